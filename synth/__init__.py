@@ -1,0 +1,129 @@
+"""Seeded synthetic inputs shared by the CPU oracle and the CUDA library.
+
+Only input generation lives here: matrices with exponential decay
+|a_ij| <= c exp(-alpha d(i,j)) (Definition 1 of the paper) on the 1-D index
+line (the model problem of Section 5.3) or on a 3-D unit lattice in Morton
+order (the stand-in for the water-cluster overlap matrices of Section 5.4).
+The element rule is in ``decaygen.h``; this module builds the host copy of it
+and wraps it with ctypes.  Nothing here computes norms, thresholds or products.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libsynth.so")
+_lib = None
+
+KIND_1D = 0
+KIND_3D = 1
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("kind", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("alpha", ctypes.c_double), ("c", ctypes.c_double), ("cutoff", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+@dataclass(frozen=True)
+class DecayParams:
+    """One synthetic decay matrix: a_ij = c u_ij exp(-alpha d(i,j)), |a|<cutoff -> 0."""
+    n: int
+    kind: int = KIND_3D
+    alpha: float = 1.0
+    seed: int = 1
+    c: float = 1.0
+    cutoff: float = 1e-16
+
+    def as_c(self) -> _Params:
+        return _Params(self.n, self.kind, 0, self.alpha, self.c, self.cutoff, self.seed)
+
+
+def build(force: bool = False) -> str:
+    """Compile libsynth.so (gcc, OpenMP, no FP contraction)."""
+    src = os.path.join(_HERE, "synth_host.c")
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "decaygen.h"))):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, src, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.POINTER(_Params)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int32)
+        lib.synth_fill_dense.argtypes = [P, dp]
+        lib.synth_fill_leaves.argtypes = [P, ctypes.c_int32, ctypes.c_int64, ip, ip, dp]
+        lib.synth_exp_nonpos_host.argtypes = [ctypes.c_double]
+        lib.synth_exp_nonpos_host.restype = ctypes.c_double
+        lib.synth_uniform_host.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64]
+        lib.synth_uniform_host.restype = ctypes.c_double
+        lib.synth_distance_host.argtypes = [P, ctypes.c_int64, ctypes.c_int64]
+        lib.synth_distance_host.restype = ctypes.c_double
+        lib.synth_lattice_point_host.argtypes = [ctypes.c_int64, ip]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def dense(p: DecayParams) -> np.ndarray:
+    """The full n x n matrix (small n only)."""
+    out = np.empty((p.n, p.n), dtype=np.float64)
+    cp = p.as_c()
+    _load().synth_fill_dense(ctypes.byref(cp), _ptr(out, ctypes.c_double))
+    return out
+
+
+def leaves(p: DecayParams, bs: int, bi, bj) -> np.ndarray:
+    """Leaf blocks (len, bs, bs): rows bi*bs.., cols bj*bs.., zero past n."""
+    bi = np.ascontiguousarray(bi, dtype=np.int32)
+    bj = np.ascontiguousarray(bj, dtype=np.int32)
+    out = np.empty((len(bi), bs, bs), dtype=np.float64)
+    cp = p.as_c()
+    _load().synth_fill_leaves(ctypes.byref(cp), bs, len(bi), _ptr(bi, ctypes.c_int32),
+                              _ptr(bj, ctypes.c_int32), _ptr(out, ctypes.c_double))
+    return out
+
+
+def exp_nonpos(x: float) -> float:
+    return _load().synth_exp_nonpos_host(float(x))
+
+
+def uniform(seed: int, i: int, j: int) -> float:
+    return _load().synth_uniform_host(seed, i, j)
+
+
+def distance(p: DecayParams, i: int, j: int) -> float:
+    cp = p.as_c()
+    return _load().synth_distance_host(ctypes.byref(cp), i, j)
+
+
+def lattice_point(i: int):
+    xyz = np.zeros(3, dtype=np.int32)
+    _load().synth_lattice_point_host(i, _ptr(xyz, ctypes.c_int32))
+    return tuple(int(v) for v in xyz)
+
+
+# The synthetic workloads (sizes and decay of the paper's model problem and
+# of the large chemical systems it stands in for).
+def model_1d(n=2048, alpha=0.05, seed=1) -> DecayParams:
+    return DecayParams(n=n, kind=KIND_1D, alpha=alpha, seed=seed)
+
+
+def lattice_3d(n=65536, alpha=1.0, seed=1) -> DecayParams:
+    return DecayParams(n=n, kind=KIND_3D, alpha=alpha, seed=seed)

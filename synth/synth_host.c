@@ -1,0 +1,28 @@
+/* Host build of the shared input generator (decaygen.h), exported for ctypes.
+ * Compiled with -ffp-contract=off so that no multiply-add is fused and the
+ * bits equal those the device build produces. */
+#include "decaygen.h"
+
+void synth_fill_dense(const synth_params* p, double* out) {
+  const int64_t n = p->n;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) out[i * n + j] = synth_element(p, i, j);
+}
+
+/* Leaf (bi, bj) of size bs x bs, row-major, rows bi*bs.., cols bj*bs.. */
+void synth_fill_leaves(const synth_params* p, int32_t bs, int64_t nleaves, const int32_t* bi,
+                       const int32_t* bj, double* out) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t m = 0; m < nleaves; ++m) {
+    double* dst = out + m * (int64_t)bs * bs;
+    for (int32_t r = 0; r < bs; ++r)
+      for (int32_t c = 0; c < bs; ++c)
+        dst[r * bs + c] = synth_element(p, (int64_t)bi[m] * bs + r, (int64_t)bj[m] * bs + c);
+  }
+}
+
+double synth_exp_nonpos_host(double x) { return synth_exp_nonpos(x); }
+double synth_uniform_host(uint64_t seed, int64_t i, int64_t j) { return synth_uniform(seed, i, j); }
+double synth_distance_host(const synth_params* p, int64_t i, int64_t j) { return synth_distance(p, i, j); }
+void synth_lattice_point_host(int64_t i, int32_t* xyz) { synth_lattice_point(i, xyz, xyz + 1, xyz + 2); }

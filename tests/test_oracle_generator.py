@@ -1,0 +1,83 @@
+"""Pins for the seeded input generator (Definitions 1-3 of the paper)."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+
+def test_exp_matches_libm_within_a_few_ulp():
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([np.linspace(-699.0, 0.0, 20001), -rng.exponential(8.0, 20000)])
+    worst = max(abs(synth.exp_nonpos(x) - math.exp(x)) / math.exp(x) for x in xs)
+    assert worst <= 4 * 2.0 ** -53
+    assert synth.exp_nonpos(0.0) == 1.0
+    assert synth.exp_nonpos(-800.0) == 0.0
+
+
+def test_uniform_range_symmetry_and_moments():
+    vals = np.array([synth.uniform(7, i, j) for i in range(60) for j in range(60)])
+    assert np.all(vals >= -1.0) and np.all(vals < 1.0)
+    assert synth.uniform(7, 3, 11) == synth.uniform(7, 11, 3)
+    assert synth.uniform(7, 3, 11) != synth.uniform(8, 3, 11)
+    assert abs(vals.mean()) < 0.05
+    assert abs(vals.var() - 1.0 / 3.0) < 0.02
+
+
+def test_lattice_is_a_box_in_morton_order():
+    pts = np.array([synth.lattice_point(i) for i in range(65536)])
+    assert pts[:, 0].max() == 63 and pts[:, 1].max() == 31 and pts[:, 2].max() == 31
+    assert len({tuple(p) for p in pts}) == 65536
+    # Morton order with x first: index 1 -> (1,0,0), 2 -> (0,1,0), 4 -> (0,0,1)
+    assert synth.lattice_point(1) == (1, 0, 0)
+    assert synth.lattice_point(2) == (0, 1, 0)
+    assert synth.lattice_point(4) == (0, 0, 1)
+    assert synth.lattice_point(7) == (1, 1, 1)
+
+
+@pytest.mark.parametrize("kind", [synth.KIND_1D, synth.KIND_3D])
+def test_distance_is_a_pseudo_metric(kind):
+    """Section 3: d >= 0, symmetric, d(i,i) = 0, triangle inequality."""
+    p = synth.DecayParams(n=4096, kind=kind)
+    rng = np.random.default_rng(1)
+    for _ in range(500):
+        i, j, k = (int(v) for v in rng.integers(0, 4096, 3))
+        dij, dji = synth.distance(p, i, j), synth.distance(p, j, i)
+        assert dij >= 0 and dij == dji and synth.distance(p, i, i) == 0.0
+        assert dij <= synth.distance(p, i, k) + synth.distance(p, k, j) + 1e-12
+    if kind == synth.KIND_1D:
+        assert synth.distance(p, 10, 3) == 7.0
+
+
+def test_finite_neighbourhood_3d():
+    """Definition 3 holds on the lattice with beta = 3: |N(i,R)| <= gamma R^3."""
+    p = synth.lattice_3d(4096)
+    for i in (0, 1000, 4095):
+        for R in (1.0, 2.0, 4.0):
+            cnt = sum(synth.distance(p, i, j) <= R for j in range(4096))
+            assert cnt <= (4.0 / 3.0 * math.pi * (R + 1.0) ** 3) * 1.0 + 1
+
+
+@pytest.mark.parametrize("params", [synth.model_1d(300, alpha=0.05), synth.lattice_3d(512, alpha=1.0)])
+def test_decay_bound_and_cutoff(params):
+    """Definition 1 with c = 1: |a_ij| <= exp(-alpha d(i,j)); |a| < cutoff is 0."""
+    A = synth.dense(params)
+    assert np.array_equal(A, A.T)
+    for i in range(0, params.n, 7):
+        for j in range(0, params.n, 5):
+            bound = math.exp(-params.alpha * synth.distance(params, i, j))
+            assert abs(A[i, j]) <= bound * (1 + 1e-14)
+    nz = A[A != 0.0]
+    assert np.all(np.abs(nz) >= params.cutoff)
+
+
+def test_leaves_match_dense_with_zero_padding():
+    p = synth.model_1d(100, alpha=0.1, seed=5)
+    A = synth.dense(p)
+    bs = 32
+    L = synth.leaves(p, bs, [0, 3, 2], [1, 3, 0])
+    assert np.array_equal(L[0], A[0:32, 32:64])
+    assert np.array_equal(L[1][:4, :4], A[96:100, 96:100])
+    assert not L[1][4:, :].any() and not L[1][:, 4:].any()
+    assert np.array_equal(L[2], A[64:96, 0:32])
