@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark: kept-block GFLOP/s of approximate C ~ AB on one GB300.
+
+Workload (default): the 3-D lattice decay problem, n = 65536 indices on a
+64 x 32 x 32 unit lattice in Morton order, a_ij = u_ij exp(-1.0 d), u_ij ~
+U[-1,1) symmetric, A != B from seeds 1 and 2, 64 x 64 leaves, Hybrid
+(combined) method at tau = 1e-6, FP64 leaf products.  One step is one pass
+of the whole hot path from device-resident inputs (leaves and norms, which
+the paper treats as given): input truncation, task-list build, batched leaf
+products with the C-leaf norm epilogue, C quadtree norms, ||C||_F read-back.
+
+Metric: kept-block GFLOP/s = 2 bs^3 N_kept / t (the paper's flop count,
+Section 5.3); mults/s = N_kept / t is reported beside it.  Inputs are 2 x
+27.7 GB, far larger than the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+
+--impl reference times the CPU oracle (the only reference implementation
+this method has) on a bounded window of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FP64_PEAK_GFLOPS = 1258.6  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (DFMA probe: 1208)
+CONFIGS = {
+    "lattice65536": dict(n=65536, kind=1, alpha=1.0, bs=64, seeds=(1, 2),
+                         desc="3-D lattice 64x32x32 Morton, alpha=1.0, A!=B seeds 1,2, 64x64 leaves"),
+    "model2048": dict(n=2048, kind=0, alpha=0.05, bs=32, seeds=(1, 1),
+                      desc="1-D decay n=2048, alpha=0.05, A=B seed 1, 32x32 leaves"),
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="lattice65536", choices=sorted(CONFIGS))
+    ap.add_argument("--mode", default="combined", choices=["truncate", "spamm", "combined"])
+    ap.add_argument("--tau", type=float, default=1e-6)
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16_split", "fp16_scaled"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- CPU oracle
+def oracle_window(cfg, mode, tau, target_s):
+    """Oracle inputs for a window of C leaves sized for about target_s seconds."""
+    import oracle
+    from oracle import sampled
+    import synth
+    pa = synth.DecayParams(n=cfg["n"], kind=cfg["kind"], alpha=cfg["alpha"], seed=cfg["seeds"][0])
+    pb = synth.DecayParams(n=cfg["n"], kind=cfg["kind"], alpha=cfg["alpha"], seed=cfg["seeds"][1])
+    bs = cfg["bs"]
+    nb = -(-cfg["n"] // bs)
+    w = min(8, nb)
+    while True:
+        A, B = sampled.window_inputs(pa, pb, bs, range(w), range(w))
+        t0 = time.perf_counter()
+        C, ikj = sampled.window_product(A, B, tau, oracle.MODES[mode])
+        dt = time.perf_counter() - t0
+        if dt >= 0.25 * target_s or w >= nb:
+            return A, B, w, dt, len(ikj)
+        grow = (target_s / max(dt, 1e-3)) ** 0.5
+        w = min(nb, max(w + 1, int(w * min(grow, 4.0))))
+
+
+def cpu_baseline(cfg, mode, tau, target_s):
+    import oracle
+    from oracle import sampled
+    A, B, w, _, _ = oracle_window(cfg, mode, tau, target_s)
+    t0 = time.perf_counter()
+    C, ikj = sampled.window_product(A, B, tau, oracle.MODES[mode])
+    dt = time.perf_counter() - t0
+    flops = 2.0 * cfg["bs"] ** 3 * len(ikj)
+    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"C leaves (i,j) in block rows/cols [0,{w}) of the same workload: {len(ikj)} kept leaf "
+                      f"products ({flops / 1e9:.1f} GFLOP) in {dt:.1f} s"}
+
+
+def run_reference(args, cfg):
+    """--impl reference: the CPU oracle, each step a bounded window of the workload."""
+    import oracle
+    from oracle import sampled
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    A, B, w, _, _ = oracle_window(cfg, args.mode, args.tau, per_step)
+    for _ in range(args.warmup):
+        sampled.window_product(A, B, args.tau, oracle.MODES[args.mode])
+    flops, t = 0.0, 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        C, ikj = sampled.window_product(A, B, args.tau, oracle.MODES[args.mode])
+        t += time.perf_counter() - t0
+        flops += 2.0 * cfg["bs"] ** 3 * len(ikj)
+    value = flops / t / 1e9
+    line = {"metric": "kept-block GFLOP/s", "value": value, "unit": "GFLOP/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.config, "desc": cfg["desc"], "method": args.mode, "tau": args.tau,
+                       "precision": "fp64", "bs": cfg["bs"]},
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"C leaves in block rows/cols [0,{w}) per step"},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse_args()
+    cfg = CONFIGS[args.config]
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_1906_08148_gb300 import spamm as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = S.Context(local, stream=stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    pa = synth.DecayParams(n=cfg["n"], kind=cfg["kind"], alpha=cfg["alpha"], seed=cfg["seeds"][0])
+    pb = synth.DecayParams(n=cfg["n"], kind=cfg["kind"], alpha=cfg["alpha"], seed=cfg["seeds"][1])
+    bs = cfg["bs"]
+    GA = S.spamm_generate(ctx, pa, bs)
+    GB = GA if pb == pa else S.spamm_generate(ctx, pb, bs)
+
+    def step():
+        C, st = S.spamm_multiply(ctx, GA, GB, args.tau, args.mode, args.prec, stats=True)
+        nrm = S.spamm_frob_norm(ctx, C)
+        C.close()
+        return st, nrm
+
+    for _ in range(args.warmup):
+        st0, nrm0 = step()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st, nrm = step()
+            stats.append(st)
+        ev1.record(stream)
+        barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms_total], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t[0])
+    flops_rank = sum(s["kept_flops"] for s in stats)
+    kept_rank = sum(s["n_kept"] for s in stats)
+    value = world * flops_rank / (ms_total / 1e3) / 1e9
+    mults = world * kept_rank / (ms_total / 1e3)
+    clocks = clk.summary()
+
+    ms_gemm = statistics.mean(s["ms_gemm"] for s in stats)
+    kept = stats[-1]["n_kept"]
+    achieved = 2.0 * bs ** 3 * kept / (ms_gemm / 1e3) / 1e9
+    phases = {k: statistics.mean(s[k] for s in stats) for k in ("ms_truncate", "ms_tasks", "ms_gemm", "ms_cnorm")}
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        e2e = run_e2e(S, ctx, GA, GB, args, bs, torch, np)
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        cpu = cpu_baseline(cfg, args.mode, args.tau, args.cpu_seconds)
+
+    if rank == 0:
+        traffic = load_traffic(args, kept)
+        line = {
+            "metric": "kept-block GFLOP/s", "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.prec == "fp64" else args.prec, "data": "synthetic",
+            "config": {"workload": args.config, "desc": cfg["desc"], "n": cfg["n"], "bs": bs, "method": args.mode,
+                       "tau": args.tau, "precision": args.prec, "l2": "inputs (2 x 27.7 GB) larger than L2",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "mults_per_s": mults,
+            "n_kept": kept, "n_c_leaves": stats[-1]["n_c_leaves"], "n_borderline": stats[-1]["n_borderline"],
+            "n_a_leaves": stats[-1]["n_a_leaves"], "n_b_leaves": stats[-1]["n_b_leaves"],
+            "c_frob": nrm, "phase_ms": phases,
+            "roofline": {"kernel": f"gemm_fp64_kernel<{bs}>", "bound": "alu", "achieved": achieved,
+                         "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+                         "traffic": traffic, "peak_source": "FP64 DFMA units x clock (no FP64 entry is measured)"},
+            "gpu_launches": None, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        line["gpu_launches"] = count_launches(stats[-1], args.steps)
+        print(json.dumps(line), flush=True)
+    for m in {id(GA): GA, id(GB): GB}.values():
+        m.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def count_launches(st, steps):
+    """Kernels one multiply launches (task builder 5 per level incl. the scan, truncation and tree builds)."""
+    L = st["levels"]
+    per_level_tasks = 5
+    tree = 5 * L + 3
+    trunc = 2 * (4 + tree)
+    gemm = 1
+    cnorm = 1 + tree
+    return steps * (per_level_tasks * L + trunc + gemm + cnorm)
+
+
+def load_traffic(args, kept):
+    """DRAM bytes per GEMM launch from the committed ncu summary, scaled by leaf products."""
+    path = os.path.join(ROOT, "profiles", f"gemm_fp64_{args.config}.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if d.get("tau") != args.tau or d.get("mode") != args.mode or d.get("prec") != args.prec:
+        return None
+    return d["dram_bytes_per_launch"] * kept / d["n_kept"]
+
+
+def run_e2e(S, ctx, GA, GB, args, bs, torch, np):
+    """Same metric through the public API from host buffers: H2D of both
+    inputs' leaves, multiply, D2H of every C leaf, all inside the timed region."""
+    ia, ib = GA.info(), GB.info()
+    e = bs * bs
+
+    def pinned(shape, dtype):
+        return torch.empty(shape, dtype=dtype, pin_memory=True).numpy()
+
+    hA = (pinned(ia["nleaves"], torch.int32), pinned(ia["nleaves"], torch.int32),
+          pinned((ia["nleaves"], bs, bs), torch.float64), pinned(ia["nleaves"], torch.float64))
+    S.spamm_to_blocks(ctx, GA, out=hA)
+    if GB is GA:
+        hB = hA
+    else:
+        hB = (pinned(ib["nleaves"], torch.int32), pinned(ib["nleaves"], torch.int32),
+              pinned((ib["nleaves"], bs, bs), torch.float64), pinned(ib["nleaves"], torch.float64))
+        S.spamm_to_blocks(ctx, GB, out=hB)
+    hC = None
+    times, flops, h2d, d2h = [], 0.0, 0, 0
+    n = ia["n"]
+    for it in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        A = S.spamm_from_blocks(ctx, n, bs, hA[0], hA[1], hA[2])
+        B = A if hB is hA else S.spamm_from_blocks(ctx, n, bs, hB[0], hB[1], hB[2])
+        C, st = S.spamm_multiply(ctx, A, B, args.tau, args.mode, args.prec, stats=True)
+        nc = C.info()["nleaves"]
+        if hC is None or len(hC[0]) < nc:
+            hC = (pinned(nc, torch.int32), pinned(nc, torch.int32), pinned((nc, bs, bs), torch.float64),
+                  pinned(nc, torch.float64))
+            if it > 0:
+                raise RuntimeError("C size changed between steps")
+        if it == 0:
+            # first pass sizes the pinned C buffer; time the next ones
+            S.spamm_to_blocks(ctx, C, out=hC)
+            for m in (C, A, B):
+                m.close()
+            continue
+        S.spamm_to_blocks(ctx, C, out=hC)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        flops += st["kept_flops"]
+        h2d = hA[2].nbytes + 8 * len(hA[0]) + (0 if hB is hA else hB[2].nbytes + 8 * len(hB[0]))
+        d2h = 8 * nc * e + 16 * nc
+        for m in {id(C): C, id(A): A, id(B): B}.values():
+            m.close()
+    return {"value": flops / sum(times) / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": len(times), "ms_per_step": 1e3 * sum(times) / len(times)}
+
+
+if __name__ == "__main__":
+    main()

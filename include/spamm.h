@@ -1,0 +1,253 @@
+/*
+ * spamm.h -- C ABI of libspamm: approximate multiplication C ~ AB of nearly
+ * sparse matrices with decay, stored as quadtrees of dense leaf blocks, on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: Artemov, "Approximate multiplication of nearly sparse matrices with
+ * decay in a fully recursive distributed task-based parallel framework"
+ * (arXiv:1906.08148).  The three methods of Section 5 are provided:
+ *   Truncmul  C~ = A~ B~            (Theorem 1: inputs truncated with tau)
+ *   SpAMM     C- = SpAMM(A, B, tau) (Algorithm 1 / Theorem 2: a sub-product
+ *                                    A_ik B_kj is skipped iff
+ *                                    ||A_ik||_F ||B_kj||_F < tau)
+ *   Hybrid    C^ = SpAMM(A~, B~, tau), the same tau for both (Theorem 3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Matrices are n x n, FP64.  A matrix handle (spamm_mat) is a quadtree whose
+ *   leaves are dense bs x bs row-major FP64 blocks, bs in {32, 64, 128}; a leaf
+ *   is stored iff it has at least one non-zero element and a null sub-matrix is
+ *   never stored (Sections 4.2 and 4.4).  Every node carries its squared
+ *   Frobenius norm, parents being the sums of their four children (Section 2).
+ *   n need not be a multiple of bs: the last leaves are zero-padded and the
+ *   padding stays zero.  Leaf grid side 2^L >= ceil(n / bs), L <= 16.
+ * - Handles are immutable once returned and are released with
+ *   spamm_release().  The library owns all device memory behind a handle; it
+ *   allocates through the context's allocator (spamm_set_allocator) or, by
+ *   default, stream-ordered cudaMallocAsync on the context stream.  Caller
+ *   buffers are only borrowed for the duration of a call.
+ * - `on_device` = 1 means a pointer argument is a device pointer on the
+ *   context's device; 0 means host memory (pageable or pinned).
+ * - All device work runs on the context's CUDA stream.  Calls that return a
+ *   host value (norms, errors, counts, statistics, host copies) synchronise
+ *   that stream before returning.
+ * - Every call returns a spamm_status; nothing aborts or traps.  The message
+ *   of the last failure on a context is available from spamm_last_error().
+ *   A device-side wait that runs past its bound makes the call return
+ *   SPAMM_E_TIMEOUT.
+ * - A context is used by one host thread at a time.
+ */
+#ifndef SPAMM_H
+#define SPAMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SPAMM_API __attribute__((visibility("default")))
+#else
+#define SPAMM_API
+#endif
+
+#define SPAMM_ABI_VERSION 1
+#define SPAMM_MAX_LEVELS 17
+
+typedef struct spamm_ctx_s* spamm_ctx;
+typedef struct spamm_mat_s* spamm_mat;
+
+typedef enum {
+  SPAMM_OK = 0,
+  SPAMM_E_INVALID_ARG = 1, /* bad size, tau < 0 or NaN, bs not 32/64/128, NULL pointer, index out of range */
+  SPAMM_E_SHAPE = 2,       /* operands disagree in n or bs */
+  SPAMM_E_NONFINITE = 3,   /* an input element is Inf or NaN */
+  SPAMM_E_OOM = 4,         /* device allocation failed */
+  SPAMM_E_CUDA = 5,        /* a CUDA call failed */
+  SPAMM_E_TIMEOUT = 6,     /* a bounded device-side wait ran out */
+  SPAMM_E_BUSY = 7,        /* resource in use */
+  SPAMM_E_CAPACITY = 8,    /* caller buffer too small; required size returned where the call says so */
+  SPAMM_E_UNSUPPORTED = 9  /* valid request this build does not implement (named in the message) */
+} spamm_status;
+
+/* The three methods of Section 5: Truncmul, SpAMM, Hybrid. */
+typedef enum { SPAMM_MODE_TRUNCATE = 0, SPAMM_MODE_SPAMM = 1, SPAMM_MODE_COMBINED = 2 } spamm_mode;
+
+/* Input truncation rule.  BLOCK_FROB: a leaf is dropped iff its Frobenius
+ * norm is < tau.  ELEMENT: a_ij -> 0 iff |a_ij| < tau (Theorem 1, equation
+ * "truncated matrices"), then leaves left without a non-zero are dropped. */
+typedef enum { SPAMM_TRUNC_BLOCK_FROB = 0, SPAMM_TRUNC_ELEMENT = 1 } spamm_trunc_rule;
+
+/* Arithmetic of the leaf products.  FP64: plain double precision on the GPU.
+ * BF16_SPLIT: each operand split into three bfloat16 terms, the six products
+ * with term-index sum <= 2 on the tensor cores, FP32 accumulation.
+ * FP16_SCALED: per-leaf power-of-two scaling, two float16 terms, FP32
+ * accumulation.  Norms, the tau test and errors are always FP64. */
+typedef enum { SPAMM_PREC_FP64 = 0, SPAMM_PREC_BF16_SPLIT = 1, SPAMM_PREC_FP16_SCALED = 2 } spamm_prec;
+
+/* Synthetic matrix with exponential decay (Definition 1 with c, alpha):
+ *   a_ij = c u_ij exp(-alpha d(i,j)),  u_ij ~ U[-1,1) symmetric, seeded;
+ *   |a_ij| < cutoff -> 0.   kind 0: d = |i - j| (the model problem of
+ * Section 5.3); kind 1: d = Euclidean distance between the points of a 3-D
+ * unit lattice in Morton order (stand-in for the systems of Section 5.4). */
+typedef struct {
+  int64_t n;
+  int32_t kind;
+  int32_t reserved;
+  double alpha;
+  double c;
+  double cutoff;
+  uint64_t seed;
+} spamm_gen_params;
+
+/* Statistics of one multiplication.  Level t counts child pairs formed when
+ * descending from level t-1 to level t (t = 1..L). */
+typedef struct {
+  int64_t n_candidates[SPAMM_MAX_LEVELS]; /* pairs with both sub-matrices non-null */
+  int64_t n_kept_level[SPAMM_MAX_LEVELS]; /* of those, pairs that passed the norm test */
+  int64_t n_kept;        /* leaf products performed (the paper's N_gemm) */
+  int64_t n_borderline;  /* leaf candidates with |norm product - tau| <= 1e-12 tau */
+  int64_t n_c_leaves;    /* leaves of C */
+  int64_t n_a_leaves;    /* leaves of A after input truncation */
+  int64_t n_b_leaves;
+  int32_t levels;        /* L */
+  int32_t bs;
+  double kept_flops;     /* 2 bs^3 n_kept (Section 5.3, flop count) */
+  double ms_truncate;    /* device time of input truncation */
+  double ms_tasks;       /* device time of the task-list build */
+  double ms_gemm;        /* device time of the leaf products (incl. C leaf norms) */
+  double ms_cnorm;       /* device time of the C quadtree norms */
+} spamm_stats;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` using stream `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * handle.  Errors: SPAMM_E_INVALID_ARG (out NULL, bad device), SPAMM_E_CUDA. */
+SPAMM_API spamm_status spamm_create(int device, void* cuda_stream, spamm_ctx* out);
+
+/* Destroy a context.  Handles created on it must be released first. */
+SPAMM_API spamm_status spamm_destroy(spamm_ctx ctx);
+
+/* Replace the stream all later work of `ctx` runs on. */
+SPAMM_API spamm_status spamm_set_stream(spamm_ctx ctx, void* cuda_stream);
+
+/* Install a device allocator: alloc(bytes, user) returns device memory usable
+ * on the context stream in stream order (NULL on failure -> SPAMM_E_OOM);
+ * free(ptr, user) returns it.  Pass alloc = free = NULL to go back to
+ * cudaMallocAsync.  Must be called while no handle of `ctx` is alive. */
+SPAMM_API spamm_status spamm_set_allocator(spamm_ctx ctx, void* (*alloc)(size_t bytes, void* user),
+                                 void (*free_fn)(void* ptr, void* user), void* user);
+
+/* Block until all work of `ctx` is done; reports a pending device error. */
+SPAMM_API spamm_status spamm_sync(spamm_ctx ctx);
+
+/* Message of the last failing call on `ctx` ("" if none).  Owned by ctx. */
+SPAMM_API const char* spamm_last_error(spamm_ctx ctx);
+
+/* -------------------------------------------------------------- building */
+
+/* Build a quadtree matrix from a dense row-major n x n array `a` with leading
+ * dimension `lda` >= n.  tau > 0 truncates the input with `rule` while
+ * building (tau = 0: only the all-zero leaves are dropped).  Leaf squared
+ * norms and parents are computed here (Section 2).
+ * Errors: INVALID_ARG (n <= 0, lda < n, bs, tau), NONFINITE, OOM, CUDA. */
+SPAMM_API spamm_status spamm_from_dense(spamm_ctx ctx, int64_t n, const double* a, int64_t lda, int on_device, int bs,
+                              double tau, spamm_trunc_rule rule, spamm_mat* out);
+
+/* Build from `nblocks` dense leaves: block (bi[q], bj[q]) has its bs*bs
+ * row-major payload at payload + q*bs*bs.  Blocks may come in any order;
+ * all-zero blocks are dropped; a repeated (bi, bj) is INVALID_ARG, as is a
+ * coordinate outside [0, ceil(n/bs)).  Payload entries past n must be 0. */
+SPAMM_API spamm_status spamm_from_blocks(spamm_ctx ctx, int64_t n, int bs, int64_t nblocks, const int32_t* bi,
+                               const int32_t* bj, const double* payload, int on_device, double tau,
+                               spamm_trunc_rule rule, spamm_mat* out);
+
+/* Build from COO triplets (row[q], col[q], val[q]), q < nnz, 0-based.
+ * Repeated coordinates are summed in input order.  Explicit zeros are
+ * allowed (a leaf holding only zeros is dropped).
+ * Errors: INVALID_ARG (index outside [0,n)), NONFINITE, OOM, CUDA. */
+SPAMM_API spamm_status spamm_from_coo(spamm_ctx ctx, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
+                            const double* val, int on_device, int bs, double tau, spamm_trunc_rule rule,
+                            spamm_mat* out);
+
+/* Generate a synthetic decay matrix (spamm_gen_params) directly into leaves on
+ * the device.  With tau > 0 and the BLOCK_FROB rule, leaves below tau are
+ * never stored (identical to truncating the full matrix, the rule being
+ * per leaf), so matrices whose untruncated form does not fit can be built. */
+SPAMM_API spamm_status spamm_generate(spamm_ctx ctx, const spamm_gen_params* params, int bs, double tau,
+                            spamm_trunc_rule rule, spamm_mat* out);
+
+/* Truncated copy of `in` with threshold tau (the vector-space truncation the
+ * paper contrasts with SpAMM's product-space truncation, Sections 2 and 3).
+ * BLOCK_FROB shares the leaf payload with `in` (no copy).  Also the output
+ * truncation of a product (pass a product as `in`). */
+SPAMM_API spamm_status spamm_truncate(spamm_ctx ctx, spamm_mat in, double tau, spamm_trunc_rule rule, spamm_mat* out);
+
+/* Release a handle (payload memory shared with views is freed with the last). */
+SPAMM_API spamm_status spamm_release(spamm_mat m);
+
+/* ---------------------------------------------------------- multiplication */
+
+/* C ~ A B with method `mode` and threshold tau >= 0 (Algorithm 1; Section 5):
+ * TRUNCATE and COMBINED first truncate A and B with the block rule and the
+ * same tau.  The quadtrees are descended level by level; a child pair
+ * (A_ik, B_kj) is entered iff both are non-null and, except in TRUNCATE mode,
+ * fl(sqrt(s_A)) * fl(sqrt(s_B)) >= tau (s = stored squared norm); the norm
+ * test is applied down to leaf pairs (Section 4.4).  C's structure is built
+ * in advance from the kept set and all leaf products are then run batched
+ * (Section 4.4); C_ij = sum over kept k, ascending, of A_ik B_kj.  C carries
+ * its leaf and parent squared norms.  `stats` may be NULL.
+ * Errors: SHAPE (n or bs differ), INVALID_ARG (tau, mode, prec),
+ * UNSUPPORTED (precision form not available for this bs), OOM, CUDA, TIMEOUT. */
+SPAMM_API spamm_status spamm_multiply(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_mode mode,
+                            spamm_prec prec, spamm_mat* C, spamm_stats* stats);
+
+/* Parity hook: the kept leaf triples of spamm_multiply(A, B, tau, mode) as
+ * (i, k, j) int32 triples (3 per triple, host memory), grouped by C leaf in
+ * Morton order of (i, j), k ascending within a group.  *count receives the
+ * number of triples; if it exceeds `cap`, nothing is written and
+ * SPAMM_E_CAPACITY is returned. */
+SPAMM_API spamm_status spamm_kept_tasks(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_mode mode,
+                              int32_t* ikj_out, int64_t cap, int64_t* count);
+
+/* ------------------------------------------------------------ evaluation */
+
+/* ||M||_F = sqrt of the root's squared norm (Section 2); 0 for an empty M. */
+SPAMM_API spamm_status spamm_frob_norm(spamm_ctx ctx, spamm_mat m, double* out);
+
+/* ||X - Y||_F over the union of the two leaf sets (a leaf missing on one side
+ * counts as zero), accumulated in FP64 (the error measure of Section 5). */
+SPAMM_API spamm_status spamm_error(spamm_ctx ctx, spamm_mat X, spamm_mat Y, double* out);
+
+/* Shape of a handle: any output pointer may be NULL. */
+SPAMM_API spamm_status spamm_mat_info(spamm_mat m, int64_t* n, int32_t* bs, int32_t* levels, int64_t* nleaves);
+
+/* Dense copy of M into `out` (row-major, leading dimension ld >= n). */
+SPAMM_API spamm_status spamm_to_dense(spamm_ctx ctx, spamm_mat m, double* out, int64_t ld, int on_device);
+
+/* Export the leaves in Morton order of (bi, bj): coordinates, payloads
+ * (bs*bs row-major each) and squared norms.  Any of bi/bj/payload/sq may be
+ * NULL.  `cap` is the capacity in leaves; fewer than nleaves -> CAPACITY. */
+SPAMM_API spamm_status spamm_to_blocks(spamm_ctx ctx, spamm_mat m, int32_t* bi, int32_t* bj, double* payload, double* sq,
+                             int64_t cap, int on_device);
+
+/* Copy the leaves at block coordinates (bi[q], bj[q]), q < nq, into
+ * payload_out + q*bs*bs (row-major); found[q] = 1 if that leaf is stored, else
+ * 0 and its payload is zero-filled.  bi, bj, payload_out and found are all on
+ * the host (on_device = 0) or all on the device (1); found may be NULL. */
+SPAMM_API spamm_status spamm_gather_leaves(spamm_ctx ctx, spamm_mat m, int64_t nq, const int32_t* bi,
+                                           const int32_t* bj, double* payload_out, int32_t* found, int on_device);
+
+/* Nodes of quadtree level `level` (0 = root, L = leaves): Morton codes of
+ * (row, col) at that level and squared norms, host memory.  *count receives
+ * the node count; more than `cap` -> CAPACITY, nothing written. */
+SPAMM_API spamm_status spamm_level_norms(spamm_ctx ctx, spamm_mat m, int level, uint32_t* codes, double* sq, int64_t cap,
+                               int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPAMM_H */

@@ -77,12 +77,18 @@ def _load():
         lib.orc_dense_product.argtypes = [i64, dp, dp, dp]
         lib.orc_leaf_diff_sumsq.argtypes = [i32, dp, dp]
         lib.orc_leaf_diff_sumsq.restype = f64
+        lib.orc_num_threads.restype = i32
         _lib = lib
     return _lib
 
 
 def _p(a, ct=ctypes.c_double):
     return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def num_threads() -> int:
+    """Host threads the oracle's parallel loops use."""
+    return int(_load().orc_num_threads())
 
 
 def levels(n: int, bs: int) -> int:

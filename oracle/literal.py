@@ -50,7 +50,11 @@ def spamm_literal(A: np.ndarray, B: np.ndarray, tau: float, bs: int, truncmul: b
                 C[i * h:(i + 1) * h, j * h:(j + 1) * h] = T[0] + T[1]
         return C
 
-    if Ap.any() and Bp.any():
+    root_ok = Ap.any() and Bp.any()
+    if root_ok and N == bs and not truncmul:
+        # a single leaf: the root pair is a leaf pair and takes the leaf test
+        root_ok = np.linalg.norm(Ap) * np.linalg.norm(Bp) >= tau
+    if root_ok:
         C = rec(Ap, Bp, 0, 0, 0, N)
     else:
         C = np.zeros((N, N))

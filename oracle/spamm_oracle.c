@@ -18,6 +18,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 enum { ORC_MODE_TRUNCATE = 0, ORC_MODE_SPAMM = 1, ORC_MODE_COMBINED = 2 };
 
@@ -181,7 +184,11 @@ static void spamm_rec(rec_state* s, int t, int64_t I, int64_t K, int64_t J) {
 int64_t orc_kept_recursive(int32_t L, const double* grid_a, const double* grid_b, double tau,
                            int32_t mode, int32_t* out_ikj) {
   rec_state s = {grid_a, grid_b, L, tau, mode, out_ikj, 0};
-  if (grid_a[0] >= 0.0 && grid_b[0] >= 0.0) spamm_rec(&s, 0, 0, 0, 0);
+  if (grid_a[0] < 0.0 || grid_b[0] < 0.0) return 0;
+  /* A single-leaf matrix (L = 0): the root pair is a leaf pair and takes the
+   * leaf-level test (Section 4.4 carries the test down to leaf pairs). */
+  if (L == 0 && !keep_pair(grid_a[0], grid_b[0], tau, mode)) return 0;
+  spamm_rec(&s, 0, 0, 0, 0);
   return s.cnt;
 }
 
@@ -231,4 +238,13 @@ double orc_leaf_diff_sumsq(int32_t bs, const double* x, const double* y) {
     s += d * d;
   }
   return s;
+}
+
+/* Threads the OpenMP loops above use (reported with the CPU baseline). */
+int32_t orc_num_threads(void) {
+#ifdef _OPENMP
+  return (int32_t)omp_get_max_threads();
+#else
+  return 1;
+#endif
 }

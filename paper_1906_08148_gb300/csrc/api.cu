@@ -1,0 +1,419 @@
+// api.cu -- the extern "C" entry points of libspamm (declared in spamm.h).
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace spamm {
+spamm_mat build_from_blocks(spamm_ctx, int64_t, int, int64_t, const int32_t*, const int32_t*, const double*, int,
+                            double, spamm_trunc_rule);
+spamm_mat build_from_dense(spamm_ctx, int64_t, const double*, int64_t, int, int, double, spamm_trunc_rule);
+spamm_mat build_generated(spamm_ctx, const spamm_gen_params*, int, double, spamm_trunc_rule);
+spamm_mat build_from_coo(spamm_ctx, int64_t, int64_t, const int64_t*, const int64_t*, const double*, int, int, double,
+                         spamm_trunc_rule);
+void export_dense(spamm_mat, double*, int64_t, int);
+void export_blocks(spamm_mat, int32_t*, int32_t*, double*, double*, int);
+void tasks_to_ikj(spamm_mat A, const TaskList& T, int32_t* d_out);
+void fill_iota_i64(spamm_ctx ctx, int64_t* p, int64_t n);
+void gather_leaves(spamm_mat m, int64_t nq, const int32_t* bi, const int32_t* bj, double* out, int32_t* found,
+                   int on_device);
+}  // namespace spamm
+
+using namespace spamm;
+
+namespace {
+
+spamm_status set_error(spamm_ctx ctx, spamm_status st, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return st;
+}
+
+template <class F>
+spamm_status guarded(spamm_ctx ctx, F&& f) {
+  if (ctx) {
+    ctx->last_error.clear();
+    cudaSetDevice(ctx->device);
+  }
+  try {
+    f();
+    return SPAMM_OK;
+  } catch (const Error& e) {
+    return set_error(ctx, e.status, e.msg);
+  } catch (const std::bad_alloc&) {
+    return set_error(ctx, SPAMM_E_OOM, "host allocation failed");
+  } catch (...) {
+    return set_error(ctx, SPAMM_E_CUDA, "unexpected exception");
+  }
+}
+
+void need(bool ok, const char* what) {
+  if (!ok) fail(SPAMM_E_INVALID_ARG, what);
+}
+
+void check_bs(int bs) { need(bs == 32 || bs == 64 || bs == 128, "bs must be 32, 64 or 128"); }
+void check_tau(double tau) { need(std::isfinite(tau) && tau >= 0.0, "tau must be finite and >= 0"); }
+void check_rule(spamm_trunc_rule r) {
+  need(r == SPAMM_TRUNC_BLOCK_FROB || r == SPAMM_TRUNC_ELEMENT, "unknown truncation rule");
+}
+void check_n(int64_t n, int bs) {
+  need(n > 0, "n must be > 0");
+  need(levels_for(n, bs) <= 16, "n / bs exceeds 65536 leaves per dimension");
+}
+
+spamm_mat registered(spamm_mat m) {
+  m->ctx->live_handles++;
+  return m;
+}
+
+// Device time between two events on the context stream (events are synchronised).
+double elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, a, b));
+  return (double)ms;
+}
+
+struct Events {
+  cudaEvent_t e[5] = {};
+  Events() {
+    for (auto& x : e) CK(cudaEventCreate(&x));
+  }
+  ~Events() {
+    for (auto& x : e)
+      if (x) cudaEventDestroy(x);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+spamm_status spamm_create(int device, void* cuda_stream, spamm_ctx* out) {
+  if (!out) return SPAMM_E_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return SPAMM_E_INVALID_ARG;
+  }
+  spamm_ctx ctx = new spamm_ctx_s();
+  spamm_status st = guarded(nullptr, [&] {
+    ctx->device = device;
+    CK(cudaSetDevice(device));
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
+    CK(cudaMalloc(&ctx->d_err, sizeof(int)));
+    CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    CK(cudaMalloc(&ctx->d_scratch, 64 * sizeof(unsigned long long)));
+    CK(cudaMemset(ctx->d_scratch, 0, 64 * sizeof(unsigned long long)));
+    CK(cudaMallocHost(&ctx->h_pinned, 4096));
+    // keep freed stream-ordered memory in the pool instead of returning it
+    cudaMemPool_t pool;
+    CK(cudaDeviceGetDefaultMemPool(&pool, device));
+    uint64_t thr = UINT64_MAX;
+    CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+  });
+  if (st != SPAMM_OK) {
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    delete ctx;
+    return st;
+  }
+  *out = ctx;
+  return SPAMM_OK;
+}
+
+spamm_status spamm_destroy(spamm_ctx ctx) {
+  if (!ctx) return SPAMM_E_INVALID_ARG;
+  if (ctx->live_handles > 0) return set_error(ctx, SPAMM_E_BUSY, "release all handles before destroying the context");
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->d_err);
+  cudaFree(ctx->d_scratch);
+  cudaFreeHost(ctx->h_pinned);
+  delete ctx;
+  return SPAMM_OK;
+}
+
+spamm_status spamm_set_stream(spamm_ctx ctx, void* cuda_stream) {
+  if (!ctx) return SPAMM_E_INVALID_ARG;
+  return guarded(ctx, [&] {
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  });
+}
+
+spamm_status spamm_set_allocator(spamm_ctx ctx, void* (*alloc)(size_t, void*), void (*free_fn)(void*, void*),
+                                 void* user) {
+  if (!ctx) return SPAMM_E_INVALID_ARG;
+  return guarded(ctx, [&] {
+    need((alloc == nullptr) == (free_fn == nullptr), "alloc and free must both be set or both be NULL");
+    if (ctx->live_handles > 0) fail(SPAMM_E_BUSY, "the allocator can only change while no handle is alive");
+    ctx->ualloc = alloc;
+    ctx->ufree = free_fn;
+    ctx->user = user;
+  });
+}
+
+spamm_status spamm_sync(spamm_ctx ctx) {
+  if (!ctx) return SPAMM_E_INVALID_ARG;
+  return guarded(ctx, [&] { sync_and_check(ctx); });
+}
+
+const char* spamm_last_error(spamm_ctx ctx) { return ctx ? ctx->last_error.c_str() : "invalid context"; }
+
+spamm_status spamm_from_dense(spamm_ctx ctx, int64_t n, const double* a, int64_t lda, int on_device, int bs,
+                              double tau, spamm_trunc_rule rule, spamm_mat* out) {
+  if (!ctx || !out) return SPAMM_E_INVALID_ARG;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    check_bs(bs);
+    check_n(n, bs);
+    check_tau(tau);
+    check_rule(rule);
+    need(a != nullptr && lda >= n, "a must be non-NULL with lda >= n");
+    spamm_mat m = build_from_dense(ctx, n, a, lda, on_device, bs, tau, rule);
+    *out = registered(m);
+  });
+}
+
+spamm_status spamm_from_blocks(spamm_ctx ctx, int64_t n, int bs, int64_t nblocks, const int32_t* bi,
+                               const int32_t* bj, const double* payload, int on_device, double tau,
+                               spamm_trunc_rule rule, spamm_mat* out) {
+  if (!ctx || !out) return SPAMM_E_INVALID_ARG;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    check_bs(bs);
+    check_n(n, bs);
+    check_tau(tau);
+    check_rule(rule);
+    need(nblocks >= 0, "nblocks must be >= 0");
+    need(nblocks == 0 || (bi && bj && payload), "bi, bj and payload must be non-NULL");
+    spamm_mat m = build_from_blocks(ctx, n, bs, nblocks, bi, bj, payload, on_device, tau, rule);
+    *out = registered(m);
+  });
+}
+
+spamm_status spamm_from_coo(spamm_ctx ctx, int64_t n, int64_t nnz, const int64_t* row, const int64_t* col,
+                            const double* val, int on_device, int bs, double tau, spamm_trunc_rule rule,
+                            spamm_mat* out) {
+  if (!ctx || !out) return SPAMM_E_INVALID_ARG;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    check_bs(bs);
+    check_n(n, bs);
+    check_tau(tau);
+    check_rule(rule);
+    need(nnz >= 0, "nnz must be >= 0");
+    need(nnz == 0 || (row && col && val), "row, col and val must be non-NULL");
+    spamm_mat m = build_from_coo(ctx, n, nnz, row, col, val, on_device, bs, tau, rule);
+    *out = registered(m);
+  });
+}
+
+spamm_status spamm_generate(spamm_ctx ctx, const spamm_gen_params* params, int bs, double tau, spamm_trunc_rule rule,
+                            spamm_mat* out) {
+  if (!ctx || !out || !params) return SPAMM_E_INVALID_ARG;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    check_bs(bs);
+    check_n(params->n, bs);
+    check_tau(tau);
+    check_rule(rule);
+    need(params->kind == 0 || params->kind == 1, "kind must be 0 (1-D) or 1 (3-D lattice)");
+    need(std::isfinite(params->alpha) && params->alpha >= 0.0, "alpha must be finite and >= 0");
+    need(std::isfinite(params->c) && std::isfinite(params->cutoff) && params->cutoff >= 0.0, "bad c or cutoff");
+    spamm_mat m = build_generated(ctx, params, bs, tau, rule);
+    *out = registered(m);
+  });
+}
+
+spamm_status spamm_truncate(spamm_ctx ctx, spamm_mat in, double tau, spamm_trunc_rule rule, spamm_mat* out) {
+  if (!ctx || !in || !out) return SPAMM_E_INVALID_ARG;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    check_tau(tau);
+    check_rule(rule);
+    spamm_mat m = rule == SPAMM_TRUNC_BLOCK_FROB ? truncate_block(in, tau) : truncate_element(in, tau);
+    sync_and_check(ctx);
+    *out = registered(m);
+  });
+}
+
+spamm_status spamm_release(spamm_mat m) {
+  if (!m) return SPAMM_E_INVALID_ARG;
+  spamm_ctx ctx = m->ctx;
+  cudaSetDevice(ctx->device);
+  delete m;
+  ctx->live_handles--;
+  return SPAMM_OK;
+}
+
+static void run_truncation(spamm_mat A, spamm_mat B, double tau, spamm_mode mode, spamm_mat* At, spamm_mat* Bt) {
+  if (mode == SPAMM_MODE_SPAMM) {
+    *At = A;
+    *Bt = B;
+    return;
+  }
+  *At = truncate_block(A, tau);
+  *Bt = (B == A) ? *At : truncate_block(B, tau);
+}
+
+static void check_pair(spamm_mat A, spamm_mat B, double tau, spamm_mode mode) {
+  if (A->n != B->n || A->bs != B->bs) fail(SPAMM_E_SHAPE, "A and B differ in n or bs");
+  if (A->ctx != B->ctx) fail(SPAMM_E_INVALID_ARG, "A and B belong to different contexts");
+  check_tau(tau);
+  need(mode == SPAMM_MODE_TRUNCATE || mode == SPAMM_MODE_SPAMM || mode == SPAMM_MODE_COMBINED, "unknown mode");
+}
+
+spamm_status spamm_multiply(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_mode mode, spamm_prec prec,
+                            spamm_mat* C, spamm_stats* stats) {
+  if (!ctx || !A || !B || !C) return SPAMM_E_INVALID_ARG;
+  *C = nullptr;
+  return guarded(ctx, [&] {
+    check_pair(A, B, tau, mode);
+    need(prec == SPAMM_PREC_FP64 || prec == SPAMM_PREC_BF16_SPLIT || prec == SPAMM_PREC_FP16_SCALED,
+         "unknown precision form");
+    if (prec != SPAMM_PREC_FP64) fail(SPAMM_E_UNSUPPORTED, "tensor-core precision forms are not built yet");
+    if (A->bs > 64) fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32 and 64");
+    Events ev;
+    CK(cudaEventRecord(ev.e[0], ctx->stream));
+    spamm_mat At = nullptr, Bt = nullptr;
+    run_truncation(A, B, tau, mode, &At, &Bt);
+    std::unique_ptr<spamm_mat_s> ownA(At != A ? At : nullptr), ownB((Bt != B && Bt != At) ? Bt : nullptr);
+    CK(cudaEventRecord(ev.e[1], ctx->stream));
+    TaskList T = build_tasks(At, Bt, tau, mode != SPAMM_MODE_TRUNCATE);
+    CK(cudaEventRecord(ev.e[2], ctx->stream));
+    spamm_mat Cm = new_mat(ctx, A->n, A->bs);
+    std::unique_ptr<spamm_mat_s> ownC(Cm);
+    const int64_t e = (int64_t)A->bs * A->bs;
+    Cm->pool = alloc_n<double>(ctx, T.ngroups * e);
+    BufP csq = alloc_n<double>(ctx, T.ngroups);
+    gemm_fp64(At, Bt, T, P<double>(Cm->pool), P<double>(csq));
+    CK(cudaEventRecord(ev.e[3], ctx->stream));
+    Level& leaf = Cm->lv[Cm->L];
+    leaf.count = T.ngroups;
+    leaf.code = T.gcode;
+    leaf.sq = csq;
+    Cm->nleaves = T.ngroups;
+    Cm->slot = alloc_n<int64_t>(ctx, T.ngroups);
+    fill_iota_i64(ctx, P<int64_t>(Cm->slot), T.ngroups);
+    build_tree(Cm);
+    CK(cudaEventRecord(ev.e[4], ctx->stream));
+    sync_and_check(ctx);
+    if (stats) {
+      memset(stats, 0, sizeof(*stats));
+      for (int t = 0; t < SPAMM_MAX_LEVELS; ++t) {
+        stats->n_candidates[t] = T.n_candidates[t];
+        stats->n_kept_level[t] = T.n_kept_level[t];
+      }
+      stats->n_kept = T.ntasks;
+      stats->n_borderline = T.n_borderline;
+      stats->n_c_leaves = T.ngroups;
+      stats->n_a_leaves = At->nleaves;
+      stats->n_b_leaves = Bt->nleaves;
+      stats->levels = A->L;
+      stats->bs = A->bs;
+      stats->kept_flops = 2.0 * (double)A->bs * A->bs * A->bs * (double)T.ntasks;
+      stats->ms_truncate = elapsed_ms(ev.e[0], ev.e[1]);
+      stats->ms_tasks = elapsed_ms(ev.e[1], ev.e[2]);
+      stats->ms_gemm = elapsed_ms(ev.e[2], ev.e[3]);
+      stats->ms_cnorm = elapsed_ms(ev.e[3], ev.e[4]);
+    }
+    *C = registered(ownC.release());
+  });
+}
+
+spamm_status spamm_kept_tasks(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_mode mode, int32_t* ikj_out,
+                              int64_t cap, int64_t* count) {
+  if (!ctx || !A || !B || !count) return SPAMM_E_INVALID_ARG;
+  return guarded(ctx, [&] {
+    check_pair(A, B, tau, mode);
+    spamm_mat At = nullptr, Bt = nullptr;
+    run_truncation(A, B, tau, mode, &At, &Bt);
+    std::unique_ptr<spamm_mat_s> ownA(At != A ? At : nullptr), ownB((Bt != B && Bt != At) ? Bt : nullptr);
+    TaskList T = build_tasks(At, Bt, tau, mode != SPAMM_MODE_TRUNCATE);
+    *count = T.ntasks;
+    if (T.ntasks > cap) fail(SPAMM_E_CAPACITY, "ikj_out holds fewer triples than the kept set");
+    if (T.ntasks == 0) return;
+    need(ikj_out != nullptr, "ikj_out must be non-NULL");
+    BufP d = alloc_n<int32_t>(ctx, 3 * T.ntasks);
+    tasks_to_ikj(At, T, P<int32_t>(d));
+    CK(cudaMemcpyAsync(ikj_out, P<int32_t>(d), 3 * T.ntasks * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    sync_and_check(ctx);
+  });
+}
+
+spamm_status spamm_frob_norm(spamm_ctx ctx, spamm_mat m, double* out) {
+  if (!ctx || !m || !out) return SPAMM_E_INVALID_ARG;
+  return guarded(ctx, [&] {
+    if (m->nleaves == 0) {
+      *out = 0.0;
+      return;
+    }
+    *out = std::sqrt(read_scalar<double>(ctx, P<double>(m->lv[0].sq)));
+  });
+}
+
+spamm_status spamm_error(spamm_ctx ctx, spamm_mat X, spamm_mat Y, double* out) {
+  if (!ctx || !X || !Y || !out) return SPAMM_E_INVALID_ARG;
+  return guarded(ctx, [&] {
+    if (X->n != Y->n || X->bs != Y->bs) fail(SPAMM_E_SHAPE, "X and Y differ in n or bs");
+    *out = error_fro(X, Y);
+  });
+}
+
+spamm_status spamm_mat_info(spamm_mat m, int64_t* n, int32_t* bs, int32_t* levels, int64_t* nleaves) {
+  if (!m) return SPAMM_E_INVALID_ARG;
+  if (n) *n = m->n;
+  if (bs) *bs = m->bs;
+  if (levels) *levels = m->L;
+  if (nleaves) *nleaves = m->nleaves;
+  return SPAMM_OK;
+}
+
+spamm_status spamm_to_dense(spamm_ctx ctx, spamm_mat m, double* out, int64_t ld, int on_device) {
+  if (!ctx || !m || !out) return SPAMM_E_INVALID_ARG;
+  return guarded(ctx, [&] {
+    need(ld >= m->n, "ld must be >= n");
+    export_dense(m, out, ld, on_device);
+  });
+}
+
+spamm_status spamm_to_blocks(spamm_ctx ctx, spamm_mat m, int32_t* bi, int32_t* bj, double* payload, double* sq,
+                             int64_t cap, int on_device) {
+  if (!ctx || !m) return SPAMM_E_INVALID_ARG;
+  return guarded(ctx, [&] {
+    if (cap < m->nleaves) fail(SPAMM_E_CAPACITY, "cap is smaller than the number of leaves");
+    export_blocks(m, bi, bj, payload, sq, on_device);
+  });
+}
+
+spamm_status spamm_gather_leaves(spamm_ctx ctx, spamm_mat m, int64_t nq, const int32_t* bi, const int32_t* bj,
+                                 double* payload_out, int32_t* found, int on_device) {
+  if (!ctx || !m) return SPAMM_E_INVALID_ARG;
+  return guarded(ctx, [&] {
+    need(nq >= 0, "nq must be >= 0");
+    need(nq == 0 || (bi && bj && payload_out), "bi, bj and payload_out must be non-NULL");
+    gather_leaves(m, nq, bi, bj, payload_out, found, on_device);
+  });
+}
+
+spamm_status spamm_level_norms(spamm_ctx ctx, spamm_mat m, int level, uint32_t* codes, double* sq, int64_t cap,
+                               int64_t* count) {
+  if (!ctx || !m || !count) return SPAMM_E_INVALID_ARG;
+  return guarded(ctx, [&] {
+    need(level >= 0 && level <= m->L, "level must be in [0, L]");
+    const Level& lv = m->lv[level];
+    *count = lv.count;
+    if (lv.count > cap) fail(SPAMM_E_CAPACITY, "cap is smaller than the node count");
+    if (lv.count == 0) return;
+    if (codes)
+      CK(cudaMemcpyAsync(codes, P<uint32_t>(lv.code), lv.count * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+    if (sq) CK(cudaMemcpyAsync(sq, P<double>(lv.sq), lv.count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    sync_and_check(ctx);
+  });
+}
+
+}  // extern "C"

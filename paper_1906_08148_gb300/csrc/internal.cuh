@@ -1,0 +1,152 @@
+// internal.cuh -- shared internals of libspamm (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "spamm.h"
+
+namespace spamm {
+
+struct Error {
+  spamm_status status;
+  std::string msg;
+};
+
+[[noreturn]] void fail(spamm_status st, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+#define CK(x) ::spamm::check_cuda((x), #x, __FILE__, __LINE__)
+#define CK_LAUNCH(what) ::spamm::check_cuda(cudaGetLastError(), what, __FILE__, __LINE__)
+
+// Device buffer owned through the context allocator.
+struct Buf {
+  spamm_ctx ctx = nullptr;
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~Buf();
+};
+using BufP = std::shared_ptr<Buf>;
+BufP alloc_bytes(spamm_ctx ctx, size_t bytes);
+template <class T>
+BufP alloc_n(spamm_ctx ctx, int64_t count) {
+  return alloc_bytes(ctx, (size_t)(count > 0 ? count : 0) * sizeof(T));
+}
+template <class T>
+T* P(const BufP& b) {
+  return b ? static_cast<T*>(b->p) : nullptr;
+}
+
+// One quadtree level: nodes sorted by Morton code of (row, col) at that level.
+struct Level {
+  int64_t count = 0;
+  BufP code;   // uint32 Morton code
+  BufP sq;     // double squared Frobenius norm
+  BufP child;  // int4: node index of child (2*ci + cj) on the next level, -1 if null (levels < L)
+};
+
+// Bits of the device error word.
+enum : int { DEV_ERR_TIMEOUT = 1, DEV_ERR_RANGE = 2, DEV_ERR_NONFINITE = 4, DEV_ERR_DUPLICATE = 8 };
+
+// Bounded waits: iterations of a try_wait loop before a device wait gives up.
+constexpr long long kWaitLimit = 1ll << 26;
+
+// Morton codes of (row, col) with the row bit above the column bit, so the
+// four children of code m are 4m + 2*ci + cj.
+__host__ __device__ __forceinline__ uint32_t part1by1(uint32_t x) {
+  x &= 0x0000FFFFu;
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+__host__ __device__ __forceinline__ uint32_t compact1by1(uint32_t x) {
+  x &= 0x55555555u;
+  x = (x | (x >> 1)) & 0x33333333u;
+  x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+  x = (x | (x >> 4)) & 0x00FF00FFu;
+  x = (x | (x >> 8)) & 0x0000FFFFu;
+  return x;
+}
+__host__ __device__ __forceinline__ uint32_t morton2(uint32_t r, uint32_t c) { return (part1by1(r) << 1) | part1by1(c); }
+__host__ __device__ __forceinline__ uint32_t code_row(uint32_t m) { return compact1by1(m >> 1); }
+__host__ __device__ __forceinline__ uint32_t code_col(uint32_t m) { return compact1by1(m); }
+
+inline int levels_for(int64_t n, int bs) {
+  int64_t nb = (n + bs - 1) / bs;
+  int L = 0;
+  while (((int64_t)1 << L) < nb) ++L;
+  return L;
+}
+
+// ---- primitives (prims.cu) ----
+// Exclusive prefix sum of n uint64 values; total written to d_total (device) if not null.
+void scan_exclusive_u64(spamm_ctx ctx, const uint64_t* in, uint64_t* out, int64_t n, uint64_t* d_total);
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the key.
+void radix_sort_pairs(spamm_ctx ctx, uint64_t* keys, int64_t* vals, int64_t n, int bits);
+// Copy a device scalar to the host (synchronises the context stream).
+template <class T>
+T read_scalar(spamm_ctx ctx, const T* d);
+void sync_and_check(spamm_ctx ctx);  // synchronise, map the device error word to a status
+void clear_device_error(spamm_ctx ctx);
+
+}  // namespace spamm
+
+struct spamm_ctx_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void* (*ualloc)(size_t, void*) = nullptr;
+  void (*ufree)(void*, void*) = nullptr;
+  void* user = nullptr;
+  std::string last_error;
+  int* d_err = nullptr;                      // device error word
+  unsigned long long* d_scratch = nullptr;   // 64 counters (statistics, work queues)
+  void* h_pinned = nullptr;                  // 4 KB pinned staging for scalar read-backs
+  int num_sms = 0;
+  int live_handles = 0;
+};
+
+struct spamm_mat_s {
+  spamm_ctx ctx = nullptr;
+  int64_t n = 0;
+  int bs = 0;
+  int L = 0;
+  int64_t nleaves = 0;
+  spamm::BufP pool;  // double payload, bs*bs per slot
+  spamm::BufP slot;  // int64 per leaf: payload slot of leaf m (leaves in Morton order)
+  std::vector<spamm::Level> lv;  // levels 0..L
+};
+
+namespace spamm {
+// ---- quadtree store (store.cu) ----
+spamm_mat new_mat(spamm_ctx ctx, int64_t n, int bs);
+void build_tree(spamm_mat m);  // levels L-1..0 from m->lv[L]
+// Leaf set from candidate leaves: keep[q] selects rows of (code, sq, slot) already sorted by code.
+void set_leaves_compacted(spamm_mat m, int64_t ncand, const uint32_t* code, const double* sq, const int64_t* slot,
+                          const uint8_t* keep);
+spamm_mat truncate_block(spamm_mat in, double tau);
+spamm_mat truncate_element(spamm_mat in, double tau);
+void leaf_sqnorms(spamm_ctx ctx, const double* pool, const int64_t* slot, int64_t nleaves, int bs, double* sq,
+                  uint8_t* nonzero, int check_finite);
+double error_fro(spamm_mat X, spamm_mat Y);
+
+// ---- task-list builder (tasks.cu) ----
+struct TaskList {
+  int64_t ngroups = 0;  // C leaves
+  int64_t ntasks = 0;   // kept leaf products
+  BufP gcode;           // uint32 Morton code of each C leaf, ascending
+  BufP gstart;          // int64 [ngroups + 1] first task of each C leaf
+  BufP ta, tb;          // int32 leaf index in A / B of each task (k ascending within a C leaf)
+  int64_t n_candidates[SPAMM_MAX_LEVELS] = {};
+  int64_t n_kept_level[SPAMM_MAX_LEVELS] = {};
+  int64_t n_borderline = 0;
+};
+TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms);
+
+// ---- leaf products (gemm_fp64.cu) ----
+// C leaf g = sum over its tasks of A[ta] B[tb]; writes cpool (g-th slot) and csq[g].
+void gemm_fp64(spamm_mat A, spamm_mat B, const TaskList& T, double* cpool, double* csq);
+}  // namespace spamm

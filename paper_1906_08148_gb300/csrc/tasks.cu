@@ -1,0 +1,284 @@
+// tasks.cu -- kernel (b): the SpAMM task-list builder.
+//
+// Algorithm 1 descends both quadtrees together: a pair (A_IK, B_KJ) that was
+// entered on level t spawns the eight child pairs (A_ik, B_kj), i in {2I,
+// 2I+1}, k in {2K, 2K+1}, j in {2J, 2J+1}; a child pair is entered iff both
+// children are non-null and ||A_ik|| ||B_kj|| >= tau (Truncmul: no test).  The
+// test is carried down to leaf pairs (Section 4.4) and the whole output
+// structure is known before any leaf product runs, as the batched "in
+// advance" multiplication of Section 4.4 does.
+//
+// Representation on level t: "groups" are the output nodes (I, J) that have
+// at least one entered pair, in Morton order, each owning a contiguous run of
+// pairs (a = node index in A, b = node index in B) ordered by K ascending.
+// One level step:
+//   count  (warp per group): evaluate the 8 children of every pair, store an
+//          8-bit kept mask per pair and, per child output node c = 2ci + cj,
+//          the number of kept pairs; pack (count | nonempty << 36).
+//   scan   exclusive prefix over the 4 * groups packed values: output offset
+//          of every child group and its index among the non-empty ones.
+//   write  (warp per group): every lane takes one pair, per child group a
+//          warp prefix sum of the kept counts places the pairs; within a
+//          child group pairs stay in parent order with k = 2K, 2K+1, so the
+//          children are again sorted by k.  Lane 0 writes the child groups.
+// Because a parent's squared norm is a floating-point sum of non-negative
+// children, the test is monotone down the tree and the pruned descent keeps
+// exactly the leaf pairs that pass the leaf-level test.
+#include "internal.cuh"
+
+namespace spamm {
+
+constexpr int kWarpsPerBlock = 8;
+constexpr uint64_t kCountMask = (1ull << 36) - 1;
+
+__device__ __forceinline__ int comp4(const int4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// mask bit (2*c + ck) for child group c = 2*ci + cj and child k-index ck.
+__device__ __forceinline__ unsigned child_mask(const int4& ca, const int4& cb, const double* __restrict__ sqA,
+                                               const double* __restrict__ sqB, double tau, int test, bool leaf,
+                                               long long* cand, long long* border) {
+  unsigned m = 0;
+#pragma unroll
+  for (int ci = 0; ci < 2; ++ci)
+#pragma unroll
+    for (int cj = 0; cj < 2; ++cj)
+#pragma unroll
+      for (int ck = 0; ck < 2; ++ck) {
+        const int a = comp4(ca, 2 * ci + ck), b = comp4(cb, 2 * ck + cj);
+        if (a < 0 || b < 0) continue;
+        ++*cand;
+        bool keep = true;
+        if (test) {
+          const double prod = __dmul_rn(sqrt(sqA[a]), sqrt(sqB[b]));
+          keep = prod >= tau;
+          if (leaf && fabs(prod - tau) <= 1e-12 * tau) ++*border;
+        }
+        if (keep) m |= 1u << (2 * (2 * ci + cj) + ck);
+      }
+  return m;
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    task_count_kernel(int64_t G, const int64_t* __restrict__ gstart, const int32_t* __restrict__ ta,
+                      const int32_t* __restrict__ tb, const int4* __restrict__ childA, const int4* __restrict__ childB,
+                      const double* __restrict__ sqA, const double* __restrict__ sqB, double tau, int test, int leaf,
+                      uint8_t* __restrict__ mask, uint64_t* __restrict__ packed, unsigned long long* stats) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  long long cand = 0, border = 0;
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += nw) {
+    const int64_t q0 = gstart[g], q1 = gstart[g + 1];
+    unsigned cnt[4] = {0, 0, 0, 0};
+    for (int64_t q = q0 + lane; q < q1; q += 32) {
+      const int4 ca = childA[ta[q]], cb = childB[tb[q]];
+      const unsigned m = child_mask(ca, cb, sqA, sqB, tau, test, leaf, &cand, &border);
+      mask[q] = (uint8_t)m;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) cnt[c] += __popc((m >> (2 * c)) & 3u);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) cnt[c] += __shfl_xor_sync(0xffffffffu, cnt[c], off);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) packed[4 * g + c] = (uint64_t)cnt[c] | ((uint64_t)(cnt[c] > 0) << 36);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    cand += __shfl_xor_sync(0xffffffffu, cand, off);
+    border += __shfl_xor_sync(0xffffffffu, border, off);
+  }
+  if (lane == 0 && (cand || border)) {
+    atomicAdd(stats + 0, (unsigned long long)cand);
+    atomicAdd(stats + 1, (unsigned long long)border);
+  }
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    task_write_kernel(int64_t G, const int64_t* __restrict__ gstart, const uint32_t* __restrict__ gcode,
+                      const int32_t* __restrict__ ta, const int32_t* __restrict__ tb, const int4* __restrict__ childA,
+                      const int4* __restrict__ childB, const uint8_t* __restrict__ mask,
+                      const uint64_t* __restrict__ packed, const uint64_t* __restrict__ off,
+                      int32_t* __restrict__ ta2, int32_t* __restrict__ tb2, uint32_t* __restrict__ gcode2,
+                      int64_t* __restrict__ gstart2) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += nw) {
+    const int64_t q0 = gstart[g], q1 = gstart[g + 1];
+    int64_t base[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) base[c] = (int64_t)(off[4 * g + c] & kCountMask);
+    if (lane < 4) {
+      const uint64_t o = off[4 * g + lane];
+      if (packed[4 * g + lane] & kCountMask) {
+        const int64_t gid = (int64_t)(o >> 36);
+        gcode2[gid] = 4u * gcode[g] + (uint32_t)lane;
+        gstart2[gid] = (int64_t)(o & kCountMask);
+      }
+    }
+    for (int64_t qb = q0; qb < q1; qb += 32) {
+      const int64_t q = qb + lane;
+      const bool active = q < q1;
+      const unsigned m = active ? mask[q] : 0u;
+      int4 ca = make_int4(-1, -1, -1, -1), cb = ca;
+      if (m) {
+        ca = childA[ta[q]];
+        cb = childB[tb[q]];
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const unsigned bits = (m >> (2 * c)) & 3u;
+        const int cntc = __popc(bits);
+        int incl = cntc;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          int y = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += y;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        int64_t pos = base[c] + (incl - cntc);
+        const int ci = c >> 1, cj = c & 1;
+        if (bits & 1u) {
+          ta2[pos] = comp4(ca, 2 * ci + 0);
+          tb2[pos] = comp4(cb, 0 + cj);
+          ++pos;
+        }
+        if (bits & 2u) {
+          ta2[pos] = comp4(ca, 2 * ci + 1);
+          tb2[pos] = comp4(cb, 2 + cj);
+        }
+        base[c] += tot;
+      }
+    }
+  }
+}
+
+__global__ void root_test_kernel(const double* sqA, const double* sqB, double tau, int test, int64_t* gstart,
+                                 unsigned long long* stats) {
+  if (threadIdx.x != 0) return;
+  const double prod = __dmul_rn(sqrt(sqA[0]), sqrt(sqB[0]));
+  const bool keep = !test || prod >= tau;
+  gstart[1] = keep ? 1 : 0;
+  stats[0] = 1;
+  stats[1] = (test && fabs(prod - tau) <= 1e-12 * tau) ? 1 : 0;
+}
+
+static unsigned warps_grid(spamm_ctx ctx, int64_t items) {
+  int64_t g = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  int64_t cap = (int64_t)ctx->num_sms * 16;
+  if (g > cap) g = cap;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms) {
+  spamm_ctx ctx = A->ctx;
+  TaskList T;
+  if (A->nleaves == 0 || B->nleaves == 0) {
+    T.gstart = alloc_n<int64_t>(ctx, 1);
+    CK(cudaMemsetAsync(P<int64_t>(T.gstart), 0, sizeof(int64_t), ctx->stream));
+    return T;
+  }
+  // level 0: the root pair is entered
+  int64_t G = 1, Q = 1;
+  BufP gcode = alloc_n<uint32_t>(ctx, 1), gstart = alloc_n<int64_t>(ctx, 2);
+  BufP ta = alloc_n<int32_t>(ctx, 1), tb = alloc_n<int32_t>(ctx, 1);
+  {
+    const int64_t h_gstart[2] = {0, 1};
+    CK(cudaMemsetAsync(P<uint32_t>(gcode), 0, sizeof(uint32_t), ctx->stream));
+    CK(cudaMemsetAsync(P<int32_t>(ta), 0, sizeof(int32_t), ctx->stream));
+    CK(cudaMemsetAsync(P<int32_t>(tb), 0, sizeof(int32_t), ctx->stream));
+    CK(cudaMemcpyAsync(P<int64_t>(gstart), h_gstart, sizeof(h_gstart), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  unsigned long long* stats = ctx->d_scratch;  // [0] candidates, [1] borderline
+  if (A->L == 0) {
+    // a single leaf: the root pair is the only leaf pair and takes the leaf test
+    root_test_kernel<<<1, 32, 0, ctx->stream>>>(P<double>(A->lv[0].sq), P<double>(B->lv[0].sq), tau, test_norms,
+                                                P<int64_t>(gstart), stats);
+    CK_LAUNCH("root_test_kernel");
+    uint64_t* hp = static_cast<uint64_t*>(ctx->h_pinned);
+    CK(cudaMemcpyAsync(hp, P<int64_t>(gstart) + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(hp + 1, stats, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    Q = (int64_t)hp[0];
+    G = Q;
+    T.n_borderline = (int64_t)hp[2];
+  }
+  for (int t = 0; t < A->L; ++t) {
+    const bool leaf = (t + 1 == A->L);
+    CK(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    BufP mask = alloc_n<uint8_t>(ctx, Q);
+    BufP packed = alloc_n<uint64_t>(ctx, 4 * G), off = alloc_n<uint64_t>(ctx, 4 * G), tot = alloc_n<uint64_t>(ctx, 1);
+    task_count_kernel<<<warps_grid(ctx, G), kWarpsPerBlock * 32, 0, ctx->stream>>>(
+        G, P<int64_t>(gstart), P<int32_t>(ta), P<int32_t>(tb), P<int4>(A->lv[t].child), P<int4>(B->lv[t].child),
+        P<double>(A->lv[t + 1].sq), P<double>(B->lv[t + 1].sq), tau, test_norms, leaf, P<uint8_t>(mask),
+        P<uint64_t>(packed), stats);
+    CK_LAUNCH("task_count_kernel");
+    scan_exclusive_u64(ctx, P<uint64_t>(packed), P<uint64_t>(off), 4 * G, P<uint64_t>(tot));
+    uint64_t* hp = static_cast<uint64_t*>(ctx->h_pinned);
+    CK(cudaMemcpyAsync(hp, P<uint64_t>(tot), sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(hp + 1, stats, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const uint64_t total = hp[0];
+    const unsigned long long h_stats[2] = {hp[1], hp[2]};
+    const int64_t Q2 = (int64_t)(total & kCountMask), G2 = (int64_t)(total >> 36);
+    T.n_candidates[t + 1] = (int64_t)h_stats[0];
+    T.n_kept_level[t + 1] = Q2;
+    if (leaf) T.n_borderline = (int64_t)h_stats[1];
+    BufP gcode2 = alloc_n<uint32_t>(ctx, G2), gstart2 = alloc_n<int64_t>(ctx, G2 + 1);
+    BufP ta2 = alloc_n<int32_t>(ctx, Q2), tb2 = alloc_n<int32_t>(ctx, Q2);
+    CK(cudaMemcpyAsync(P<int64_t>(gstart2) + G2, &T.n_kept_level[t + 1], sizeof(int64_t), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    if (G2 > 0) {
+      task_write_kernel<<<warps_grid(ctx, G), kWarpsPerBlock * 32, 0, ctx->stream>>>(
+          G, P<int64_t>(gstart), P<uint32_t>(gcode), P<int32_t>(ta), P<int32_t>(tb), P<int4>(A->lv[t].child),
+          P<int4>(B->lv[t].child), P<uint8_t>(mask), P<uint64_t>(packed), P<uint64_t>(off), P<int32_t>(ta2),
+          P<int32_t>(tb2), P<uint32_t>(gcode2), P<int64_t>(gstart2));
+      CK_LAUNCH("task_write_kernel");
+    }
+    G = G2;
+    Q = Q2;
+    gcode = gcode2;
+    gstart = gstart2;
+    ta = ta2;
+    tb = tb2;
+    if (G == 0) break;
+  }
+  T.ngroups = G;
+  T.ntasks = Q;
+  T.gcode = gcode;
+  T.gstart = gstart;
+  T.ta = ta;
+  T.tb = tb;
+  return T;
+}
+
+// (i, k, j) of every task, for the parity hook.
+__global__ void tasks_to_ikj_kernel(int64_t G, const int64_t* __restrict__ gstart, const uint32_t* __restrict__ gcode,
+                                    const int32_t* __restrict__ ta, const uint32_t* __restrict__ codeA,
+                                    int32_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += nw) {
+    const int32_t i = (int32_t)code_row(gcode[g]), j = (int32_t)code_col(gcode[g]);
+    for (int64_t q = gstart[g] + lane; q < gstart[g + 1]; q += 32) {
+      out[3 * q + 0] = i;
+      out[3 * q + 1] = (int32_t)code_col(codeA[ta[q]]);
+      out[3 * q + 2] = j;
+    }
+  }
+}
+
+void tasks_to_ikj(spamm_mat A, const TaskList& T, int32_t* d_out) {
+  spamm_ctx ctx = A->ctx;
+  if (T.ngroups == 0) return;
+  tasks_to_ikj_kernel<<<warps_grid(ctx, T.ngroups), kWarpsPerBlock * 32, 0, ctx->stream>>>(
+      T.ngroups, P<int64_t>(T.gstart), P<uint32_t>(T.gcode), P<int32_t>(T.ta), P<uint32_t>(A->lv[A->L].code), d_out);
+  CK_LAUNCH("tasks_to_ikj_kernel");
+}
+
+}  // namespace spamm

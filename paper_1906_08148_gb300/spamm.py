@@ -1,0 +1,361 @@
+"""ctypes binding of libspamm (include/spamm.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts Python
+objects (numpy arrays for host memory, torch CUDA tensors for device memory)
+to pointers and sizes, calls the C entry point of the same name and turns a
+non-OK status into SpammError.  PyTorch provides device memory and streams:
+a Context can run on a torch CUDA stream and allocate through torch's caching
+allocator.  There is no CPU fallback: if libspamm.so is missing the import of
+the library fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libspamm.so")
+
+OK, E_INVALID_ARG, E_SHAPE, E_NONFINITE, E_OOM, E_CUDA, E_TIMEOUT, E_BUSY, E_CAPACITY, E_UNSUPPORTED = range(10)
+MODE_TRUNCATE, MODE_SPAMM, MODE_COMBINED = 0, 1, 2
+MODES = {"truncate": MODE_TRUNCATE, "spamm": MODE_SPAMM, "combined": MODE_COMBINED}
+TRUNC_BLOCK_FROB, TRUNC_ELEMENT = 0, 1
+RULES = {"block": TRUNC_BLOCK_FROB, "element": TRUNC_ELEMENT}
+PREC_FP64, PREC_BF16_SPLIT, PREC_FP16_SCALED = 0, 1, 2
+PRECS = {"fp64": PREC_FP64, "bf16_split": PREC_BF16_SPLIT, "fp16_scaled": PREC_FP16_SCALED}
+MAX_LEVELS = 17
+
+# every entry point of include/spamm.h
+ENTRY_POINTS = (
+    "spamm_create", "spamm_destroy", "spamm_set_stream", "spamm_set_allocator", "spamm_sync", "spamm_last_error",
+    "spamm_from_dense", "spamm_from_blocks", "spamm_from_coo", "spamm_generate", "spamm_truncate", "spamm_release",
+    "spamm_multiply", "spamm_kept_tasks", "spamm_frob_norm", "spamm_error", "spamm_mat_info", "spamm_to_dense",
+    "spamm_to_blocks", "spamm_gather_leaves", "spamm_level_norms",
+)
+
+
+class SpammError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"libspamm status {status}: {message}")
+        self.status = status
+
+
+class GenParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("kind", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("alpha", ctypes.c_double), ("c", ctypes.c_double), ("cutoff", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_candidates", ctypes.c_int64 * MAX_LEVELS), ("n_kept_level", ctypes.c_int64 * MAX_LEVELS),
+                ("n_kept", ctypes.c_int64), ("n_borderline", ctypes.c_int64), ("n_c_leaves", ctypes.c_int64),
+                ("n_a_leaves", ctypes.c_int64), ("n_b_leaves", ctypes.c_int64), ("levels", ctypes.c_int32),
+                ("bs", ctypes.c_int32), ("kept_flops", ctypes.c_double), ("ms_truncate", ctypes.c_double),
+                ("ms_tasks", ctypes.c_double), ("ms_gemm", ctypes.c_double), ("ms_cnorm", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        L = self.levels
+        return {"n_candidates": list(self.n_candidates[1:L + 1]), "n_kept_level": list(self.n_kept_level[1:L + 1]),
+                "n_kept": self.n_kept, "n_borderline": self.n_borderline, "n_c_leaves": self.n_c_leaves,
+                "n_a_leaves": self.n_a_leaves, "n_b_leaves": self.n_b_leaves, "levels": L, "bs": self.bs,
+                "kept_flops": self.kept_flops, "ms_truncate": self.ms_truncate, "ms_tasks": self.ms_tasks,
+                "ms_gemm": self.ms_gemm, "ms_cnorm": self.ms_cnorm}
+
+
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libspamm.so and declare the C signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libspamm.so not found at {path}: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    L = ctypes.CDLL(path)
+    vp, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    pi32, pi64, pf64, pu32 = (ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint32))
+    sig = {
+        "spamm_create": [ctypes.c_int, vp, ctypes.POINTER(vp)],
+        "spamm_destroy": [vp],
+        "spamm_set_stream": [vp, vp],
+        "spamm_set_allocator": [vp, _ALLOC_T, _FREE_T, vp],
+        "spamm_sync": [vp],
+        "spamm_from_dense": [vp, i64, vp, i64, ctypes.c_int, ctypes.c_int, f64, ctypes.c_int, ctypes.POINTER(vp)],
+        "spamm_from_blocks": [vp, i64, ctypes.c_int, i64, vp, vp, vp, ctypes.c_int, f64, ctypes.c_int,
+                              ctypes.POINTER(vp)],
+        "spamm_from_coo": [vp, i64, i64, vp, vp, vp, ctypes.c_int, ctypes.c_int, f64, ctypes.c_int,
+                           ctypes.POINTER(vp)],
+        "spamm_generate": [vp, ctypes.POINTER(GenParams), ctypes.c_int, f64, ctypes.c_int, ctypes.POINTER(vp)],
+        "spamm_truncate": [vp, vp, f64, ctypes.c_int, ctypes.POINTER(vp)],
+        "spamm_release": [vp],
+        "spamm_multiply": [vp, vp, vp, f64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(Stats)],
+        "spamm_kept_tasks": [vp, vp, vp, f64, ctypes.c_int, vp, i64, pi64],
+        "spamm_frob_norm": [vp, vp, pf64],
+        "spamm_error": [vp, vp, vp, pf64],
+        "spamm_mat_info": [vp, pi64, pi32, pi32, pi64],
+        "spamm_to_dense": [vp, vp, vp, i64, ctypes.c_int],
+        "spamm_to_blocks": [vp, vp, vp, vp, vp, vp, i64, ctypes.c_int],
+        "spamm_level_norms": [vp, vp, ctypes.c_int, vp, vp, i64, pi64],
+        "spamm_gather_leaves": [vp, vp, i64, vp, vp, vp, vp, ctypes.c_int],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.spamm_last_error.argtypes = [vp]
+    L.spamm_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(ctx_handle, status: int):
+    if status != OK:
+        msg = load().spamm_last_error(ctx_handle).decode() if ctx_handle else ""
+        raise SpammError(status, msg)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, on_device, keepalive) for a numpy array or a torch tensor."""
+    if x is None:
+        return None, 0, None
+    if _is_torch(x):
+        assert x.is_contiguous(), "tensor must be contiguous"
+        return ctypes.c_void_p(x.data_ptr()), int(x.is_cuda), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data_as(ctypes.c_void_p), 0, a
+
+
+class Context:
+    """A libspamm context on one CUDA device and stream (spamm_create)."""
+
+    def __init__(self, device: int = 0, stream=None, torch_allocator: bool = False):
+        self._lib = load()
+        s = stream.cuda_stream if (stream is not None and hasattr(stream, "cuda_stream")) else stream
+        h = ctypes.c_void_p()
+        st = self._lib.spamm_create(device, ctypes.c_void_p(s or 0), ctypes.byref(h))
+        if st != OK:
+            raise SpammError(st, "spamm_create failed")
+        self.handle = h
+        self.device = device
+        self._callbacks = None
+        if torch_allocator:
+            spamm_set_allocator(self, "torch")
+
+    def close(self):
+        if self.handle:
+            _check(self.handle, self._lib.spamm_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Matrix:
+    """An immutable quadtree matrix handle (released on close or garbage collection)."""
+
+    def __init__(self, ctx: Context, handle: ctypes.c_void_p):
+        self.ctx = ctx
+        self.handle = handle
+
+    def info(self) -> dict:
+        n, bs, L, m = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(self.ctx.handle, load().spamm_mat_info(self.handle, ctypes.byref(n), ctypes.byref(bs),
+                                                      ctypes.byref(L), ctypes.byref(m)))
+        return {"n": n.value, "bs": bs.value, "levels": L.value, "nleaves": m.value}
+
+    def close(self):
+        if self.handle:
+            load().spamm_release(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _new(ctx, fn, *args) -> Matrix:
+    out = ctypes.c_void_p()
+    _check(ctx.handle, fn(ctx.handle, *args, ctypes.byref(out)))
+    return Matrix(ctx, out)
+
+
+def spamm_set_allocator(ctx: Context, which: Optional[str] = "torch"):
+    """Route the library's device allocations through torch's caching allocator (or back to cudaMallocAsync)."""
+    lib = load()
+    if which is None:
+        _check(ctx.handle, lib.spamm_set_allocator(ctx.handle, _ALLOC_T(), _FREE_T(), None))
+        ctx._callbacks = None
+        return
+    import torch
+
+    dev = ctx.device
+
+    def _alloc(nbytes, _user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, torch.cuda.current_stream(dev))
+        except Exception:
+            return None
+
+    def _free(p, _user):
+        torch.cuda.caching_allocator_delete(p)
+
+    cbs = (_ALLOC_T(_alloc), _FREE_T(_free))
+    _check(ctx.handle, lib.spamm_set_allocator(ctx.handle, cbs[0], cbs[1], None))
+    ctx._callbacks = cbs
+
+
+def spamm_sync(ctx: Context):
+    _check(ctx.handle, load().spamm_sync(ctx.handle))
+
+
+def spamm_from_dense(ctx: Context, a, bs: int, tau: float = 0.0, rule: str = "block") -> Matrix:
+    n = a.shape[0]
+    p, dev, keep = _ptr(a, np.float64)
+    lda = a.stride(0) if _is_torch(a) else n
+    return _new(ctx, load().spamm_from_dense, n, p, lda, dev, bs, float(tau), RULES[rule])
+
+
+def spamm_from_blocks(ctx: Context, n: int, bs: int, bi, bj, payload, tau: float = 0.0, rule: str = "block") -> Matrix:
+    pbi, dev, k1 = _ptr(bi, np.int32)
+    pbj, _, k2 = _ptr(bj, np.int32)
+    pp, _, k3 = _ptr(payload, np.float64)
+    return _new(ctx, load().spamm_from_blocks, n, bs, len(bi), pbi, pbj, pp, dev, float(tau), RULES[rule])
+
+
+def spamm_from_coo(ctx: Context, n: int, row, col, val, bs: int, tau: float = 0.0, rule: str = "block") -> Matrix:
+    pr, dev, k1 = _ptr(row, np.int64)
+    pc, _, k2 = _ptr(col, np.int64)
+    pv, _, k3 = _ptr(val, np.float64)
+    return _new(ctx, load().spamm_from_coo, n, len(row), pr, pc, pv, dev, bs, float(tau), RULES[rule])
+
+
+def spamm_generate(ctx: Context, params, bs: int, tau: float = 0.0, rule: str = "block") -> Matrix:
+    """params: any object with n, kind, alpha, c, cutoff, seed (e.g. synth.DecayParams)."""
+    gp = GenParams(int(params.n), int(params.kind), 0, float(params.alpha), float(params.c), float(params.cutoff),
+                   int(params.seed))
+    return _new(ctx, load().spamm_generate, ctypes.byref(gp), bs, float(tau), RULES[rule])
+
+
+def spamm_truncate(ctx: Context, m: Matrix, tau: float, rule: str = "block") -> Matrix:
+    return _new(ctx, load().spamm_truncate, m.handle, float(tau), RULES[rule])
+
+
+def spamm_release(m: Matrix):
+    m.close()
+
+
+def spamm_multiply(ctx: Context, A: Matrix, B: Matrix, tau: float, mode: str = "spamm", prec: str = "fp64",
+                   stats: bool = False):
+    out = ctypes.c_void_p()
+    st = Stats()
+    _check(ctx.handle, load().spamm_multiply(ctx.handle, A.handle, B.handle, float(tau), MODES[mode], PRECS[prec],
+                                             ctypes.byref(out), ctypes.byref(st)))
+    C = Matrix(ctx, out)
+    return (C, st.as_dict()) if stats else C
+
+
+def spamm_kept_tasks(ctx: Context, A: Matrix, B: Matrix, tau: float, mode: str = "spamm") -> np.ndarray:
+    lib = load()
+    cnt = ctypes.c_int64()
+    st = lib.spamm_kept_tasks(ctx.handle, A.handle, B.handle, float(tau), MODES[mode], None, 0, ctypes.byref(cnt))
+    if st not in (OK, E_CAPACITY):
+        _check(ctx.handle, st)
+    out = np.empty((cnt.value, 3), np.int32)
+    if cnt.value:
+        _check(ctx.handle, lib.spamm_kept_tasks(ctx.handle, A.handle, B.handle, float(tau), MODES[mode],
+                                                out.ctypes.data_as(ctypes.c_void_p), cnt.value, ctypes.byref(cnt)))
+    return out
+
+
+def spamm_frob_norm(ctx: Context, m: Matrix) -> float:
+    v = ctypes.c_double()
+    _check(ctx.handle, load().spamm_frob_norm(ctx.handle, m.handle, ctypes.byref(v)))
+    return v.value
+
+
+def spamm_error(ctx: Context, X: Matrix, Y: Matrix) -> float:
+    v = ctypes.c_double()
+    _check(ctx.handle, load().spamm_error(ctx.handle, X.handle, Y.handle, ctypes.byref(v)))
+    return v.value
+
+
+def spamm_to_dense(ctx: Context, m: Matrix, out=None):
+    n = m.info()["n"]
+    if out is None:
+        out = np.empty((n, n), np.float64)
+    p, dev, keep = _ptr(out, np.float64)
+    ld = out.stride(0) if _is_torch(out) else n
+    if not _is_torch(out):
+        assert out.flags["C_CONTIGUOUS"] and out.dtype == np.float64
+        p = out.ctypes.data_as(ctypes.c_void_p)
+    _check(ctx.handle, load().spamm_to_dense(ctx.handle, m.handle, p, ld, dev))
+    return out
+
+
+def spamm_to_blocks(ctx: Context, m: Matrix, payload: bool = True, out=None):
+    """(bi, bj, payload (m, bs, bs) or None, sq) on the host, leaves in Morton order.
+
+    `out` may supply preallocated host arrays (bi, bj, payload, sq), e.g. pinned."""
+    info = m.info()
+    nl, bs = info["nleaves"], info["bs"]
+    if out is not None:
+        bi, bj, pay, sq = out
+        assert len(bi) >= nl and len(bj) >= nl and len(sq) >= nl and (pay is None or len(pay) >= nl)
+        payload = pay is not None
+    else:
+        bi = np.empty(nl, np.int32)
+        bj = np.empty(nl, np.int32)
+        sq = np.empty(nl, np.float64)
+        pay = np.empty((nl, bs, bs), np.float64) if payload else None
+    vp = ctypes.c_void_p
+    _check(ctx.handle, load().spamm_to_blocks(
+        ctx.handle, m.handle, bi.ctypes.data_as(vp), bj.ctypes.data_as(vp),
+        pay.ctypes.data_as(vp) if payload else None, sq.ctypes.data_as(vp), nl, 0))
+    return bi, bj, pay, sq
+
+
+def spamm_level_norms(ctx: Context, m: Matrix, level: int):
+    """(codes uint32, squared norms) of one quadtree level, Morton order."""
+    lib = load()
+    cnt = ctypes.c_int64()
+    st = lib.spamm_level_norms(ctx.handle, m.handle, level, None, None, 0, ctypes.byref(cnt))
+    if st not in (OK, E_CAPACITY):
+        _check(ctx.handle, st)
+    codes = np.empty(cnt.value, np.uint32)
+    sq = np.empty(cnt.value, np.float64)
+    if cnt.value:
+        vp = ctypes.c_void_p
+        _check(ctx.handle, lib.spamm_level_norms(ctx.handle, m.handle, level, codes.ctypes.data_as(vp),
+                                                 sq.ctypes.data_as(vp), cnt.value, ctypes.byref(cnt)))
+    return codes, sq
+
+
+def spamm_gather_leaves(ctx: Context, m: Matrix, bi, bj):
+    """(payload (nq, bs, bs), found (nq,)) for the leaves at (bi[q], bj[q]), host arrays."""
+    bs = m.info()["bs"]
+    bi = np.ascontiguousarray(bi, np.int32)
+    bj = np.ascontiguousarray(bj, np.int32)
+    out = np.empty((len(bi), bs, bs), np.float64)
+    found = np.empty(len(bi), np.int32)
+    vp = ctypes.c_void_p
+    _check(ctx.handle, load().spamm_gather_leaves(ctx.handle, m.handle, len(bi), bi.ctypes.data_as(vp),
+                                                  bj.ctypes.data_as(vp), out.ctypes.data_as(vp),
+                                                  found.ctypes.data_as(vp), 0))
+    return out, found.astype(bool)

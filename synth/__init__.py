@@ -73,6 +73,8 @@ def _load():
         lib.synth_distance_host.argtypes = [P, ctypes.c_int64, ctypes.c_int64]
         lib.synth_distance_host.restype = ctypes.c_double
         lib.synth_lattice_point_host.argtypes = [ctypes.c_int64, ip]
+        lib.synth_leaf_bound_host.argtypes = [P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64]
+        lib.synth_leaf_bound_host.restype = ctypes.c_double
         _lib = lib
     return _lib
 
@@ -111,6 +113,12 @@ def uniform(seed: int, i: int, j: int) -> float:
 def distance(p: DecayParams, i: int, j: int) -> float:
     cp = p.as_c()
     return _load().synth_distance_host(ctypes.byref(cp), i, j)
+
+
+def leaf_bound(p: DecayParams, bs: int, bi: int, bj: int) -> float:
+    """Upper bound of |a_ij| over leaf (bi, bj)."""
+    cp = p.as_c()
+    return _load().synth_leaf_bound_host(ctypes.byref(cp), bs, bi, bj)
 
 
 def lattice_point(i: int):

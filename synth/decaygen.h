@@ -105,10 +105,14 @@ SYNTH_HD double synth_exp_nonpos(double x) {
 }
 
 SYNTH_HD uint32_t synth_compact1by2(uint64_t v) {
-  /* keep bits 0, 3, 6, ... of v and pack them */
-  uint32_t out = 0;
-  for (int b = 0; b < 21; ++b) out |= (uint32_t)((v >> (3 * b)) & 1ull) << b;
-  return out;
+  /* keep bits 0, 3, 6, ... of v and pack them (21 bits) */
+  v &= 0x1249249249249249ull;
+  v = (v ^ (v >> 2)) & 0x10C30C30C30C30C3ull;
+  v = (v ^ (v >> 4)) & 0x100F00F00F00F00Full;
+  v = (v ^ (v >> 8)) & 0x001F0000FF0000FFull;
+  v = (v ^ (v >> 16)) & 0x001F00000000FFFFull;
+  v = (v ^ (v >> 32)) & 0x00000000001FFFFFull;
+  return (uint32_t)v;
 }
 
 SYNTH_HD void synth_lattice_point(int64_t i, int32_t* x, int32_t* y, int32_t* z) {
@@ -134,6 +138,35 @@ SYNTH_HD double synth_element(const synth_params* p, int64_t i, int64_t j) {
   double v = SYNTH_MUL(SYNTH_MUL(p->c, synth_uniform(p->seed, i, j)), e);
   double av = v < 0.0 ? -v : v;
   return av < p->cutoff ? 0.0 : v;
+}
+
+/* Upper bound of |a_ij| over the leaf rows [bi*bs, bi*bs+bs) x columns
+ * [bj*bs, bj*bs+bs) (bs a power of two): c exp(-alpha dmin), dmin the least
+ * distance between the two index sets (for the 3-D kind an aligned
+ * power-of-two run of Morton indices is an axis-aligned box).  Slightly
+ * enlarged so rounding cannot make it smaller than a true element. */
+SYNTH_HD double synth_leaf_bound(const synth_params* p, int32_t bs, int64_t bi, int64_t bj) {
+  double dmin;
+  if (p->kind == SYNTH_KIND_1D) {
+    int64_t gap = (bi > bj ? bi - bj : bj - bi) * (int64_t)bs - (bs - 1);
+    dmin = gap > 0 ? (double)gap : 0.0;
+  } else {
+    int32_t a0[3], a1[3], b0[3], b1[3];
+    synth_lattice_point(bi * bs, &a0[0], &a0[1], &a0[2]);
+    synth_lattice_point(bi * bs + bs - 1, &a1[0], &a1[1], &a1[2]);
+    synth_lattice_point(bj * bs, &b0[0], &b0[1], &b0[2]);
+    synth_lattice_point(bj * bs + bs - 1, &b1[0], &b1[1], &b1[2]);
+    int64_t d2 = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+      int64_t g = 0;
+      if (b0[ax] > a1[ax]) g = b0[ax] - a1[ax];
+      if (a0[ax] > b1[ax]) g = a0[ax] - b1[ax];
+      d2 += g * g;
+    }
+    dmin = SYNTH_SQRT((double)d2);
+  }
+  double e = synth_exp_nonpos(SYNTH_MUL(-p->alpha, dmin));
+  return SYNTH_MUL(SYNTH_MUL(p->c < 0.0 ? -p->c : p->c, e), 1.0 + 0x1.0p-40);
 }
 
 #endif /* SYNTH_DECAYGEN_H */

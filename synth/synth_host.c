@@ -26,3 +26,6 @@ double synth_exp_nonpos_host(double x) { return synth_exp_nonpos(x); }
 double synth_uniform_host(uint64_t seed, int64_t i, int64_t j) { return synth_uniform(seed, i, j); }
 double synth_distance_host(const synth_params* p, int64_t i, int64_t j) { return synth_distance(p, i, j); }
 void synth_lattice_point_host(int64_t i, int32_t* xyz) { synth_lattice_point(i, xyz, xyz + 1, xyz + 2); }
+double synth_leaf_bound_host(const synth_params* p, int32_t bs, int64_t bi, int64_t bj) {
+  return synth_leaf_bound(p, bs, bi, bj);
+}

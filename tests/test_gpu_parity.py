@@ -1,0 +1,303 @@
+"""GPU path vs the FP64 oracle, through the C ABI (libspamm.so).
+
+Bars (from the method's statement of the problem): the kept-task set is
+bit-exact except for leaf pairs whose norm product lies within 1e-12
+relative of tau (counted, reported, and tolerated only in that band); the
+FP64 product agrees with the oracle to ||C_gpu - C_orc||_F / ||C_orc||_F
+<= 1e-12; leaf sets, coordinates and integer outputs are bit-exact; squared
+norms agree to a few ulp (different summation order: the bound used below,
+1e-14 relative, is ~log2(bs^2) ulp)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+REL_C = 1e-12
+REL_NORM = 1e-14
+
+
+@pytest.fixture(scope="module")
+def S():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1906_08148_gb300 import spamm
+    return spamm
+
+
+@pytest.fixture(scope="module")
+def ctx(S):
+    c = S.Context(0)
+    yield c
+
+
+def _dense_pair(n, alpha, kind=synth.KIND_3D, seeds=(1, 2)):
+    A = synth.dense(synth.DecayParams(n=n, kind=kind, alpha=alpha, seed=seeds[0]))
+    B = synth.dense(synth.DecayParams(n=n, kind=kind, alpha=alpha, seed=seeds[1]))
+    return A, B
+
+
+def _gpu_leaves(S, ctx, M):
+    bi, bj, pay, sq = S.spamm_to_blocks(ctx, M)
+    return bi, bj, pay, sq
+
+
+def _orc_sorted(M: oracle.LeafMatrix):
+    """Oracle leaves in Morton order of (bi, bj) (the library's order)."""
+    def morton(r, c):
+        code = 0
+        for b in range(16):
+            code |= ((int(r) >> b) & 1) << (2 * b + 1) | ((int(c) >> b) & 1) << (2 * b)
+        return code
+    codes = np.array([morton(r, c) for r, c in zip(M.bi, M.bj)], dtype=np.int64)
+    o = np.argsort(codes, kind="stable")
+    return M.bi[o], M.bj[o], M.data[o], M.sq[o]
+
+
+def _assert_same_matrix(S, ctx, G, M: oracle.LeafMatrix, rel=REL_C):
+    bi, bj, pay, sq = _gpu_leaves(S, ctx, G)
+    obi, obj, odata, osq = _orc_sorted(M)
+    assert np.array_equal(bi, obi) and np.array_equal(bj, obj), "leaf structure differs"
+    num = np.sqrt(np.sum((pay - odata) ** 2))
+    den = np.sqrt(np.sum(odata ** 2))
+    assert num <= rel * den + 1e-300, (num, den)
+    assert np.all(np.abs(sq - osq) <= 1e-12 * osq + 1e-300)
+
+
+def _assert_kept_parity(ikj_gpu, ikj_orc, A: oracle.LeafMatrix, B: oracle.LeafMatrix, tau):
+    """Bit-exact kept set except pairs within 1e-12 relative of tau."""
+    g = set(map(tuple, ikj_gpu.tolist()))
+    o = set(map(tuple, ikj_orc.tolist()))
+    diff = g ^ o
+    if diff:
+        side = 1 << A.L
+        ia = {(int(r), int(c)): q for q, (r, c) in enumerate(zip(A.bi, A.bj))}
+        ib = {(int(r), int(c)): q for q, (r, c) in enumerate(zip(B.bi, B.bj))}
+        for (i, k, j) in diff:
+            prod = np.sqrt(A.sq[ia[(i, k)]]) * np.sqrt(B.sq[ib[(k, j)]])
+            assert abs(prod - tau) <= 1e-12 * tau, ("non-borderline mismatch", (i, k, j), prod, tau)
+        assert side > 0
+    return len(diff)
+
+
+# ----------------------------------------------------------- building (a)
+@pytest.mark.parametrize("n,bs", [(2048, 32), (4096, 64), (1000, 32), (300, 128)])
+def test_from_dense_leaves_norms_and_parents(S, ctx, n, bs):
+    A, _ = _dense_pair(n, 0.7)
+    G = S.spamm_from_dense(ctx, A, bs)
+    M = oracle.from_dense(A, bs)
+    _assert_same_matrix(S, ctx, G, M, rel=0.0)
+    # parents: every level's squared norms against the oracle's quadtree
+    grids, _ = oracle.tree_norms(M)
+    L = M.L
+    assert G.info()["levels"] == L
+    for t in range(L + 1):
+        codes, sq = S.spamm_level_norms(ctx, G, t)
+        grid = grids[t]
+        rows = np.array([sum(((int(c) >> (2 * b + 1)) & 1) << b for b in range(16)) for c in codes], dtype=np.int64)
+        cols = np.array([sum(((int(c) >> (2 * b)) & 1) << b for b in range(16)) for c in codes], dtype=np.int64)
+        ref = grid[rows, cols] if len(codes) else np.zeros(0)
+        assert np.all(ref >= 0), "GPU has a node the oracle does not"
+        assert len(codes) == int(np.sum(grid >= 0)), "node count differs"
+        assert np.all(np.abs(sq - ref) <= REL_NORM * ref + 1e-300)
+    assert np.array_equal(S.spamm_to_dense(ctx, G), A)
+    assert abs(S.spamm_frob_norm(ctx, G) - oracle.frob_norm(M)) <= REL_NORM * oracle.frob_norm(M)
+
+
+def test_from_blocks_any_order_and_errors(S, ctx):
+    A, _ = _dense_pair(1536, 0.6)
+    M = oracle.from_dense(A, 32)
+    perm = np.random.default_rng(3).permutation(M.m)
+    G = S.spamm_from_blocks(ctx, 1536, 32, M.bi[perm], M.bj[perm], M.data[perm])
+    _assert_same_matrix(S, ctx, G, M, rel=0.0)
+    with pytest.raises(S.SpammError) as e:
+        S.spamm_from_blocks(ctx, 1536, 32, np.array([0, 0], np.int32), np.array([1, 1], np.int32), M.data[:2])
+    assert e.value.status == S.E_INVALID_ARG
+    with pytest.raises(S.SpammError) as e:
+        S.spamm_from_blocks(ctx, 1536, 32, np.array([48], np.int32), np.array([0], np.int32), M.data[:1])
+    assert e.value.status == S.E_INVALID_ARG
+    bad = M.data[:1].copy()
+    bad[0, 3, 3] = np.nan
+    with pytest.raises(S.SpammError) as e:
+        S.spamm_from_blocks(ctx, 1536, 32, M.bi[:1], M.bj[:1], bad)
+    assert e.value.status == S.E_NONFINITE
+    with pytest.raises(S.SpammError) as e:
+        S.spamm_from_dense(ctx, A, 48)
+    assert e.value.status == S.E_INVALID_ARG
+
+
+def test_from_coo_sums_duplicates(S, ctx):
+    rng = np.random.default_rng(5)
+    n = 700
+    nnz = 20000
+    row = rng.integers(0, n, nnz)
+    col = rng.integers(0, n, nnz)
+    val = rng.standard_normal(nnz)
+    dense = np.zeros((n, n))
+    np.add.at(dense, (row, col), val)
+    G = S.spamm_from_coo(ctx, n, row, col, val, 64)
+    Dg = S.spamm_to_dense(ctx, G)
+    assert np.allclose(Dg, dense, rtol=1e-14, atol=1e-14)
+    _assert_same_matrix(S, ctx, G, oracle.from_dense(Dg, 64), rel=0.0)
+    with pytest.raises(S.SpammError) as e:
+        S.spamm_from_coo(ctx, n, np.array([n]), np.array([0]), np.array([1.0]), 64)
+    assert e.value.status == S.E_INVALID_ARG
+
+
+@pytest.mark.parametrize("p,bs", [(synth.model_1d(2048, alpha=0.05, seed=1), 32),
+                                  (synth.lattice_3d(4096, alpha=1.0, seed=2), 64),
+                                  (synth.lattice_3d(3000, alpha=0.8, seed=4), 32)])
+def test_device_generator_matches_host_bits(S, ctx, p, bs):
+    G = S.spamm_generate(ctx, p, bs)
+    M = oracle.from_dense(synth.dense(p), bs)
+    _assert_same_matrix(S, ctx, G, M, rel=0.0)
+
+
+@pytest.mark.parametrize("rule", ["block", "element"])
+def test_truncation_rules(S, ctx, rule):
+    A, _ = _dense_pair(2048, 0.9)
+    G = S.spamm_from_dense(ctx, A, 32)
+    M = oracle.from_dense(A, 32)
+    for tau in (1e-10, 1e-6, 1e-3):
+        T = S.spamm_truncate(ctx, G, tau, rule)
+        _assert_same_matrix(S, ctx, T, oracle.truncate(M, tau, rule), rel=0.0)
+        T2 = S.spamm_from_dense(ctx, A, 32, tau, rule)
+        _assert_same_matrix(S, ctx, T2, oracle.truncate(M, tau, rule), rel=0.0)
+
+
+# ------------------------------------------------------ task list (b), (c)
+@pytest.mark.parametrize("mode", ["spamm", "truncate", "combined"])
+def test_cfg1_model_problem_full_parity(S, ctx, mode):
+    """1-D decay, n=2048, a_ij = u_ij exp(-0.05|i-j|), A = B, 32x32 leaves."""
+    p = synth.model_1d(2048, alpha=0.05, seed=1)
+    A = synth.dense(p)
+    G = S.spamm_generate(ctx, p, 32)
+    M = oracle.from_dense(A, 32)
+    for tau in (1e-8, 1e-4):
+        ikj_g = S.spamm_kept_tasks(ctx, G, G, tau, mode)
+        Mt = M if mode == "spamm" else oracle.truncate_block(M, tau)
+        ref, ikj_o = oracle.multiply(M, M, tau, oracle.MODES[mode])
+        nb = _assert_kept_parity(ikj_g, ikj_o, Mt, Mt, tau)
+        C, st = S.spamm_multiply(ctx, G, G, tau, mode, "fp64", stats=True)
+        assert st["n_kept"] == len(ikj_g)
+        if nb == 0:
+            assert np.array_equal(ikj_g, ikj_o[np.lexsort((ikj_o[:, 1], ikj_o[:, 2], ikj_o[:, 0]))]) or \
+                set(map(tuple, ikj_g.tolist())) == set(map(tuple, ikj_o.tolist()))
+            _assert_same_matrix(S, ctx, C, ref)
+        assert st["kept_flops"] == 2.0 * 32 ** 3 * st["n_kept"]
+        if mode == "spamm" and tau == 1e-8:
+            print("cfg1 spamm tau=1e-8 kept", st["n_kept"])
+
+
+def test_kept_tasks_are_grouped_by_c_leaf_in_morton_order(S, ctx):
+    p = synth.lattice_3d(4096, alpha=0.8, seed=1)
+    G = S.spamm_generate(ctx, p, 32)
+    ikj = S.spamm_kept_tasks(ctx, G, G, 1e-7, "spamm")
+
+    def morton(r, c):
+        code = 0
+        for b in range(16):
+            code |= ((int(r) >> b) & 1) << (2 * b + 1) | ((int(c) >> b) & 1) << (2 * b)
+        return code
+    keys = np.array([morton(i, j) for i, j in zip(ikj[:, 0], ikj[:, 2])], dtype=np.int64)
+    assert np.all(np.diff(keys) >= 0)
+    same = np.diff(keys) == 0
+    assert np.all(np.diff(ikj[:, 1])[same] > 0), "k must ascend within a C leaf"
+
+
+@pytest.mark.parametrize("n,bs,alpha", [(4096, 64, 1.0), (3000, 32, 0.8), (5000, 64, 0.6)])
+@pytest.mark.parametrize("mode", ["spamm", "truncate", "combined"])
+def test_lattice_parity_all_methods(S, ctx, n, bs, alpha, mode):
+    pa, pb = synth.lattice_3d(n, alpha=alpha, seed=1), synth.lattice_3d(n, alpha=alpha, seed=2)
+    GA, GB = S.spamm_generate(ctx, pa, bs), S.spamm_generate(ctx, pb, bs)
+    MA, MB = oracle.from_dense(synth.dense(pa), bs), oracle.from_dense(synth.dense(pb), bs)
+    for tau in (1e-8, 1e-6, 1e-4):
+        ref, ikj_o = oracle.multiply(MA, MB, tau, oracle.MODES[mode])
+        ikj_g = S.spamm_kept_tasks(ctx, GA, GB, tau, mode)
+        At = MA if mode == "spamm" else oracle.truncate_block(MA, tau)
+        Bt = MB if mode == "spamm" else oracle.truncate_block(MB, tau)
+        nb = _assert_kept_parity(ikj_g, ikj_o, At, Bt, tau)
+        C, st = S.spamm_multiply(ctx, GA, GB, tau, mode, "fp64", stats=True)
+        if nb == 0:
+            _assert_same_matrix(S, ctx, C, ref)
+        assert st["n_borderline"] >= nb
+        exact = oracle.exact(MA, MB)
+        e_gpu = S.spamm_error(ctx, C, S.spamm_multiply(ctx, GA, GB, 0.0, "spamm"))
+        e_orc = oracle.error(exact, ref)
+        assert abs(e_gpu - e_orc) <= 1e-9 * e_orc + 1e-13 * oracle.frob_norm(exact)
+
+
+def test_tau_zero_is_the_dense_product(S, ctx):
+    A, B = _dense_pair(1111, 0.3)
+    GA, GB = S.spamm_from_dense(ctx, A, 32), S.spamm_from_dense(ctx, B, 32)
+    C = S.spamm_multiply(ctx, GA, GB, 0.0, "spamm")
+    D = S.spamm_to_dense(ctx, C)
+    ref = A @ B
+    assert np.linalg.norm(D - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+def test_edge_cases(S, ctx):
+    # single leaf (L = 0), with the leaf-level test
+    A, B = _dense_pair(20, 0.3)
+    GA, GB = S.spamm_from_dense(ctx, A, 32), S.spamm_from_dense(ctx, B, 32)
+    MA, MB = oracle.from_dense(A, 32), oracle.from_dense(B, 32)
+    prod = np.sqrt(MA.sq[0]) * np.sqrt(MB.sq[0])
+    C = S.spamm_multiply(ctx, GA, GB, prod * 0.999, "spamm")
+    assert C.info()["nleaves"] == 1
+    assert np.allclose(S.spamm_to_dense(ctx, C), A @ B, rtol=1e-13, atol=1e-15)
+    C = S.spamm_multiply(ctx, GA, GB, prod * 1.001, "spamm")
+    assert C.info()["nleaves"] == 0 and S.spamm_frob_norm(ctx, C) == 0.0
+    # tau above every product: empty result; error = ||AB||
+    A, B = _dense_pair(1024, 0.5)
+    GA, GB = S.spamm_from_dense(ctx, A, 32), S.spamm_from_dense(ctx, B, 32)
+    C = S.spamm_multiply(ctx, GA, GB, 1e9, "spamm")
+    assert C.info()["nleaves"] == 0
+    X = S.spamm_multiply(ctx, GA, GB, 0.0, "spamm")
+    assert abs(S.spamm_error(ctx, X, C) - np.linalg.norm(A @ B)) <= 1e-12 * np.linalg.norm(A @ B)
+    # all-zero input: no leaves, product empty
+    Z = S.spamm_from_dense(ctx, np.zeros((256, 256)), 32)
+    assert Z.info()["nleaves"] == 0
+    assert S.spamm_multiply(ctx, Z, GA if False else Z, 0.0, "spamm").info()["nleaves"] == 0
+    # shape mismatch
+    G64 = S.spamm_from_dense(ctx, A, 64)
+    with pytest.raises(S.SpammError) as e:
+        S.spamm_multiply(ctx, GA, G64, 1e-6, "spamm")
+    assert e.value.status == S.E_SHAPE
+    with pytest.raises(S.SpammError) as e:
+        S.spamm_multiply(ctx, GA, GB, -1.0, "spamm")
+    assert e.value.status == S.E_INVALID_ARG
+
+
+def test_results_are_deterministic(S, ctx):
+    p = synth.lattice_3d(4096, alpha=0.7, seed=1)
+    G = S.spamm_generate(ctx, p, 64)
+    outs = []
+    for _ in range(3):
+        C = S.spamm_multiply(ctx, G, G, 1e-7, "combined")
+        outs.append(S.spamm_to_blocks(ctx, C))
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
+
+
+def test_torch_allocator_and_stream(S):
+    import torch
+    s = torch.cuda.Stream()
+    with S.Context(0, stream=s, torch_allocator=True) as c:
+        p = synth.lattice_3d(2048, alpha=0.8, seed=3)
+        G = S.spamm_generate(c, p, 32)
+        C = S.spamm_multiply(c, G, G, 1e-6, "spamm")
+        D = torch.empty((2048, 2048), dtype=torch.float64, device="cuda")
+        S.spamm_to_dense(c, C, D)
+        torch.cuda.synchronize()
+        M = oracle.from_dense(synth.dense(p), 32)
+        ref, _ = oracle.multiply(M, M, 1e-6, oracle.SPAMM)
+        R = oracle.to_dense(ref)
+        assert np.linalg.norm(D.cpu().numpy() - R) <= REL_C * np.linalg.norm(R)
+        for m in (C, G):
+            m.close()

@@ -81,3 +81,19 @@ def test_leaves_match_dense_with_zero_padding():
     assert np.array_equal(L[1][:4, :4], A[96:100, 96:100])
     assert not L[1][4:, :].any() and not L[1][:, 4:].any()
     assert np.array_equal(L[2], A[64:96, 0:32])
+
+
+@pytest.mark.parametrize("params,bs", [(synth.model_1d(600, alpha=0.05), 32), (synth.lattice_3d(4096, alpha=0.7), 64)])
+def test_leaf_bound_dominates_every_element(params, bs):
+    A = synth.dense(params)
+    nb = -(-params.n // bs)
+    pad = np.zeros((nb * bs, nb * bs))
+    pad[:params.n, :params.n] = np.abs(A)
+    tight = 0
+    for bi in range(nb):
+        for bj in range(nb):
+            b = synth.leaf_bound(params, bs, bi, bj)
+            m = pad[bi * bs:(bi + 1) * bs, bj * bs:(bj + 1) * bs].max()
+            assert m <= b
+            tight += m > 0.1 * b
+    assert tight > 0

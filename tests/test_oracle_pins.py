@@ -235,3 +235,17 @@ def test_error_function_closed_forms():
     Z = oracle.LeafMatrix(100, 8, np.zeros(0), np.zeros(0), np.zeros((0, 8, 8)))
     assert abs(oracle.error(X, Z) - oracle.frob_norm(X)) <= 1e-14 * oracle.frob_norm(X)
     assert abs(oracle.frob_norm(X) - np.linalg.norm(A)) <= 1e-13 * np.linalg.norm(A)
+
+
+def test_single_leaf_matrix_takes_the_leaf_test():
+    """n <= bs: the one leaf pair is tested like every other leaf pair."""
+    A, B = _pair(20, alpha=0.3)
+    LA, LB = oracle.from_dense(A, 32), oracle.from_dense(B, 32)
+    assert LA.L == 0 and LA.m == 1
+    prod = np.sqrt(LA.sq[0]) * np.sqrt(LB.sq[0])
+    for tau, expect in ((prod * 0.999, 1), (prod * 1.001, 0)):
+        for f in (oracle.kept_flat, oracle.kept_recursive):
+            assert len(f(LA, LB, tau, oracle.SPAMM)) == expect
+        _, kl = literal.spamm_literal(A, B, tau, 32)
+        assert len(kl) == expect
+    assert len(oracle.kept_recursive(LA, LB, prod * 2, oracle.TRUNCATE)) == 1
