@@ -37,6 +37,8 @@ FP64_PEAK_GFLOPS = 1258.6  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (DFMA 
 CONFIGS = {
     "lattice65536": dict(n=65536, kind=1, alpha=1.0, bs=64, seeds=(1, 2),
                          desc="3-D lattice 64x32x32 Morton, alpha=1.0, A!=B seeds 1,2, 64x64 leaves"),
+    "lattice16384": dict(n=16384, kind=1, alpha=1.0, bs=64, seeds=(1, 2),
+                         desc="3-D lattice 32x32x16 Morton, alpha=1.0, A!=B seeds 1,2, 64x64 leaves (profiling size)"),
     "model2048": dict(n=2048, kind=0, alpha=0.05, bs=32, seeds=(1, 1),
                       desc="1-D decay n=2048, alpha=0.05, A=B seed 1, 32x32 leaves"),
 }
@@ -248,7 +250,6 @@ def main():
 
     ms_gemm = statistics.mean(s["ms_gemm"] for s in stats)
     kept = stats[-1]["n_kept"]
-    achieved = 2.0 * bs ** 3 * kept / (ms_gemm / 1e3) / 1e9
     phases = {k: statistics.mean(s[k] for s in stats) for k in ("ms_truncate", "ms_tasks", "ms_gemm", "ms_cnorm")}
 
     e2e = None
@@ -260,7 +261,7 @@ def main():
         cpu = cpu_baseline(cfg, args.mode, args.tau, args.cpu_seconds)
 
     if rank == 0:
-        traffic = load_traffic(args, kept)
+        roof = roofline(args.prec, bs, kept, ms_gemm)
         line = {
             "metric": "kept-block GFLOP/s", "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
@@ -272,13 +273,10 @@ def main():
             "mults_per_s": mults,
             "n_kept": kept, "n_c_leaves": stats[-1]["n_c_leaves"], "n_borderline": stats[-1]["n_borderline"],
             "n_a_leaves": stats[-1]["n_a_leaves"], "n_b_leaves": stats[-1]["n_b_leaves"],
-            "c_frob": nrm, "phase_ms": phases,
-            "roofline": {"kernel": f"gemm_fp64_kernel<{bs}>", "bound": "alu", "achieved": achieved,
-                         "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
-                         "traffic": traffic, "peak_source": "FP64 DFMA units x clock (no FP64 entry is measured)"},
+            "c_frob": nrm, "phase_ms": phases, "roofline": roof,
             "gpu_launches": None, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
         }
-        line["gpu_launches"] = count_launches(stats[-1], args.steps)
+        line["gpu_launches"] = int(sum(s["n_launches"] for s in stats))
         print(json.dumps(line), flush=True)
     for m in {id(GA): GA, id(GB): GB}.values():
         m.close()
@@ -286,26 +284,49 @@ def main():
         dist.destroy_process_group()
 
 
-def count_launches(st, steps):
-    """Kernels one multiply launches (task builder 5 per level incl. the scan, truncation and tree builds)."""
-    L = st["levels"]
-    per_level_tasks = 5
-    tree = 5 * L + 3
-    trunc = 2 * (4 + tree)
-    gemm = 1
-    cnorm = 1 + tree
-    return steps * (per_level_tasks * L + trunc + gemm + cnorm)
+# executed tensor flops per kept leaf product: M=128 x N (x K=64) MMAs
+EXECUTED_PER_PRODUCT = {"bf16_split": 2.0 * 128 * (192 + 64) * 64, "fp16_scaled": 2.0 * 128 * 128 * 64}
 
 
-def load_traffic(args, kept):
-    """DRAM bytes per GEMM launch from the committed ncu summary, scaled by leaf products."""
-    path = os.path.join(ROOT, "profiles", f"gemm_fp64_{args.config}.json")
+def roofline(prec, bs, kept, ms_gemm):
+    """Roofline entry for the dominant kernel (the leaf GEMM), from the
+    CUDA-event duration of its launch inside the timed steps."""
+    import json as _json
+    algo = 2.0 * bs ** 3 * kept
+    secs = ms_gemm / 1e3
+    if prec == "fp64":
+        achieved = algo / secs / 1e9
+        kernel = f"gemm_fp64_kernel<{bs}>"
+        return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": load_traffic(kernel, kept),
+                "peak_source": "FP64 DFMA units x clock (derived; no FP64 entry in MEASURED_PEAKS.json)"}
+    peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops_sustained": 1700.0}
+    peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    achieved = algo / secs / 1e12
+    executed = EXECUTED_PER_PRODUCT[prec] * kept / secs / 1e12
+    kernel = "gemm_tc_kernel<%s>" % prec
+    return {"kernel": kernel, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "executed": executed, "executed_frac": executed / peak,
+            "traffic": load_traffic(kernel, kept),
+            "peak_source": "bf16 dense sustained, measured (fp16 dense has the same nominal rate)"}
+
+
+def load_traffic(kernel, kept):
+    """DRAM bytes per GEMM launch: the committed ncu capture's bytes per kept leaf
+    product times this launch's products; None once the kernel source has
+    changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    d = json.load(open(path))
-    if d.get("tau") != args.tau or d.get("mode") != args.mode or d.get("prec") != args.prec:
+    d = json.load(open(path)).get(kernel)
+    if not d:
         return None
-    return d["dram_bytes_per_launch"] * kept / d["n_kept"]
+    src = open(os.path.join(ROOT, d["source"]), "rb").read()
+    if hashlib.sha256(src).hexdigest()[:16] != d["source_sha256_16"]:
+        return None
+    return d["dram_bytes_per_product"] * kept
 
 
 def run_e2e(S, ctx, GA, GB, args, bs, torch, np):

@@ -119,6 +119,7 @@ typedef struct {
   double ms_tasks;       /* device time of the task-list build */
   double ms_gemm;        /* device time of the leaf products (incl. C leaf norms) */
   double ms_cnorm;       /* device time of the C quadtree norms */
+  int64_t n_launches;    /* CUDA kernels this call launched */
 } spamm_stats;
 
 /* ---------------------------------------------------------------- context */

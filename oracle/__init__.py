@@ -58,28 +58,32 @@ def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB_PATH)
-        dp = ctypes.POINTER(ctypes.c_double)
-        ip = ctypes.POINTER(ctypes.c_int32)
-        lp = ctypes.POINTER(ctypes.c_int64)
-        i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
-        lib.orc_pairwise_sumsq.argtypes = [dp, i64]
-        lib.orc_pairwise_sumsq.restype = f64
-        lib.orc_leaf_sqnorms.argtypes = [i64, i32, dp, dp]
-        lib.orc_leaves_from_dense.argtypes = [i64, i32, dp, i64, ip, ip, dp]
-        lib.orc_leaves_from_dense.restype = i64
-        lib.orc_tree_norms.argtypes = [i32, i64, ip, ip, dp, dp]
-        lib.orc_kept_flat.argtypes = [i64, ip, ip, dp, i64, ip, ip, dp, i32, f64, i32, ip]
-        lib.orc_kept_flat.restype = i64
-        lib.orc_kept_recursive.argtypes = [i32, dp, dp, f64, i32, ip]
-        lib.orc_kept_recursive.restype = i64
-        lib.orc_leaf_products.argtypes = [i32, dp, dp, i64, lp, lp, lp, dp]
-        lib.orc_dense_product.argtypes = [i64, dp, dp, dp]
-        lib.orc_leaf_diff_sumsq.argtypes = [i32, dp, dp]
-        lib.orc_leaf_diff_sumsq.restype = f64
-        lib.orc_num_threads.restype = i32
-        _lib = lib
+        _lib = _configure(ctypes.CDLL(_LIB_PATH))
     return _lib
+
+
+def _configure(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    lp = ctypes.POINTER(ctypes.c_int64)
+    i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    lib.orc_pairwise_sumsq.argtypes = [dp, i64]
+    lib.orc_pairwise_sumsq.restype = f64
+    lib.orc_leaf_sqnorms.argtypes = [i64, i32, dp, dp]
+    lib.orc_leaves_from_dense.argtypes = [i64, i32, dp, i64, ip, ip, dp]
+    lib.orc_leaves_from_dense.restype = i64
+    lib.orc_tree_norms.argtypes = [i32, i64, ip, ip, dp, dp]
+    lib.orc_kept_flat.argtypes = [i64, ip, ip, dp, i64, ip, ip, dp, i32, f64, i32, ip]
+    lib.orc_kept_flat.restype = i64
+    lib.orc_kept_recursive.argtypes = [i32, dp, dp, f64, i32, ip]
+    lib.orc_kept_recursive.restype = i64
+    lib.orc_leaf_products.argtypes = [i32, dp, dp, i64, lp, lp, lp, dp]
+    lib.orc_dense_product.argtypes = [i64, dp, dp, dp]
+    lib.orc_leaf_diff_sumsq.argtypes = [i32, dp, dp]
+    lib.orc_leaf_diff_sumsq.restype = f64
+    lib.orc_num_threads.restype = i32
+    return lib
 
 
 def _p(a, ct=ctypes.c_double):

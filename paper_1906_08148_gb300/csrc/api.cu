@@ -274,9 +274,12 @@ spamm_status spamm_multiply(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau,
     check_pair(A, B, tau, mode);
     need(prec == SPAMM_PREC_FP64 || prec == SPAMM_PREC_BF16_SPLIT || prec == SPAMM_PREC_FP16_SCALED,
          "unknown precision form");
-    if (prec != SPAMM_PREC_FP64) fail(SPAMM_E_UNSUPPORTED, "tensor-core precision forms are not built yet");
-    if (A->bs > 64) fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32 and 64");
+    if (prec == SPAMM_PREC_FP64 && A->bs > 64)
+      fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32 and 64");
+    if (prec != SPAMM_PREC_FP64 && A->bs != 64)
+      fail(SPAMM_E_UNSUPPORTED, "tensor-core precision forms are built for bs = 64");
     Events ev;
+    const unsigned long long launches0 = g_kernel_launches;
     CK(cudaEventRecord(ev.e[0], ctx->stream));
     spamm_mat At = nullptr, Bt = nullptr;
     run_truncation(A, B, tau, mode, &At, &Bt);
@@ -289,7 +292,10 @@ spamm_status spamm_multiply(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau,
     const int64_t e = (int64_t)A->bs * A->bs;
     Cm->pool = alloc_n<double>(ctx, T.ngroups * e);
     BufP csq = alloc_n<double>(ctx, T.ngroups);
-    gemm_fp64(At, Bt, T, P<double>(Cm->pool), P<double>(csq));
+    if (prec == SPAMM_PREC_FP64)
+      gemm_fp64(At, Bt, T, P<double>(Cm->pool), P<double>(csq));
+    else
+      gemm_tc(At, Bt, T, prec, P<double>(Cm->pool), P<double>(csq));
     CK(cudaEventRecord(ev.e[3], ctx->stream));
     Level& leaf = Cm->lv[Cm->L];
     leaf.count = T.ngroups;
@@ -319,6 +325,7 @@ spamm_status spamm_multiply(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau,
       stats->ms_tasks = elapsed_ms(ev.e[1], ev.e[2]);
       stats->ms_gemm = elapsed_ms(ev.e[2], ev.e[3]);
       stats->ms_cnorm = elapsed_ms(ev.e[3], ev.e[4]);
+      stats->n_launches = (int64_t)(g_kernel_launches - launches0);
     }
     *C = registered(ownC.release());
   });

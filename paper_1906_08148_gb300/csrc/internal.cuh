@@ -19,7 +19,10 @@ struct Error {
 [[noreturn]] void fail(spamm_status st, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 #define CK(x) ::spamm::check_cuda((x), #x, __FILE__, __LINE__)
-#define CK_LAUNCH(what) ::spamm::check_cuda(cudaGetLastError(), what, __FILE__, __LINE__)
+// Every kernel launch is followed by CK_LAUNCH, which also counts it.
+extern unsigned long long g_kernel_launches;
+#define CK_LAUNCH(what) \
+  (++::spamm::g_kernel_launches, ::spamm::check_cuda(cudaGetLastError(), what, __FILE__, __LINE__))
 
 // Device buffer owned through the context allocator.
 struct Buf {
@@ -149,4 +152,6 @@ TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms);
 // ---- leaf products (gemm_fp64.cu) ----
 // C leaf g = sum over its tasks of A[ta] B[tb]; writes cpool (g-th slot) and csq[g].
 void gemm_fp64(spamm_mat A, spamm_mat B, const TaskList& T, double* cpool, double* csq);
+// Tensor-core forms (gemm_tc.cu): operand split/scale pass, then the tcgen05 leaf GEMM.
+void gemm_tc(spamm_mat A, spamm_mat B, const TaskList& T, spamm_prec prec, double* cpool, double* csq);
 }  // namespace spamm

@@ -6,6 +6,8 @@
 
 namespace spamm {
 
+unsigned long long g_kernel_launches = 0;
+
 void fail(spamm_status st, const std::string& msg) { throw Error{st, msg}; }
 
 void check_cuda(cudaError_t e, const char* what, const char* file, int line) {

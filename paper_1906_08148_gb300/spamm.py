@@ -54,7 +54,8 @@ class Stats(ctypes.Structure):
                 ("n_kept", ctypes.c_int64), ("n_borderline", ctypes.c_int64), ("n_c_leaves", ctypes.c_int64),
                 ("n_a_leaves", ctypes.c_int64), ("n_b_leaves", ctypes.c_int64), ("levels", ctypes.c_int32),
                 ("bs", ctypes.c_int32), ("kept_flops", ctypes.c_double), ("ms_truncate", ctypes.c_double),
-                ("ms_tasks", ctypes.c_double), ("ms_gemm", ctypes.c_double), ("ms_cnorm", ctypes.c_double)]
+                ("ms_tasks", ctypes.c_double), ("ms_gemm", ctypes.c_double), ("ms_cnorm", ctypes.c_double),
+                ("n_launches", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         L = self.levels
@@ -62,7 +63,7 @@ class Stats(ctypes.Structure):
                 "n_kept": self.n_kept, "n_borderline": self.n_borderline, "n_c_leaves": self.n_c_leaves,
                 "n_a_leaves": self.n_a_leaves, "n_b_leaves": self.n_b_leaves, "levels": L, "bs": self.bs,
                 "kept_flops": self.kept_flops, "ms_truncate": self.ms_truncate, "ms_tasks": self.ms_tasks,
-                "ms_gemm": self.ms_gemm, "ms_cnorm": self.ms_cnorm}
+                "ms_gemm": self.ms_gemm, "ms_cnorm": self.ms_cnorm, "n_launches": self.n_launches}
 
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)

@@ -1,0 +1,95 @@
+"""Parity at the benchmark's full size (n = 65536 3-D lattice, 64x64 leaves,
+A != B), in the launch configuration bench.py times, on sampled outputs the
+oracle can compute one by one: a window of output leaves (block rows and
+columns [0, w)) plus scattered leaves, each recomputed by the oracle from
+regenerated block rows of A and block columns of B."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import sampled
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+N, BS, ALPHA = 65536, 64, 1.0
+
+
+@pytest.fixture(scope="module")
+def S():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1906_08148_gb300 import spamm
+    return spamm
+
+
+@pytest.fixture(scope="module")
+def setup(S):
+    ctx = S.Context(0)
+    pa, pb = synth.lattice_3d(N, alpha=ALPHA, seed=1), synth.lattice_3d(N, alpha=ALPHA, seed=2)
+    GA, GB = S.spamm_generate(ctx, pa, BS), S.spamm_generate(ctx, pb, BS)
+    return ctx, pa, pb, GA, GB
+
+
+def _window_check(S, ctx, C, ref, rel_tol, bound=None):
+    gpu, found = S.spamm_gather_leaves(ctx, C, ref.bi, ref.bj)
+    assert found.all(), "an oracle leaf is missing on the GPU"
+    num = float(np.sum((gpu - ref.data) ** 2))
+    den = float(np.sum(ref.data ** 2))
+    assert np.sqrt(num) <= rel_tol * np.sqrt(den), (np.sqrt(num / den))
+    return np.sqrt(num / den)
+
+
+@pytest.mark.parametrize("mode,tau", [("combined", 1e-6), ("spamm", 1e-6), ("truncate", 1e-4)])
+def test_fullsize_fp64_window(S, setup, mode, tau):
+    ctx, pa, pb, GA, GB = setup
+    C, st = S.spamm_multiply(ctx, GA, GB, tau, mode, "fp64", stats=True)
+    w = 12
+    A_rows, B_cols = sampled.window_inputs(pa, pb, BS, range(w), range(w))
+    ref, ikj = sampled.window_product(A_rows, B_cols, tau, oracle.MODES[mode])
+    # structure: the GPU's output leaves inside the window are exactly the oracle's
+    ii, jj = np.meshgrid(np.arange(w), np.arange(w), indexing="ij")
+    _, found = S.spamm_gather_leaves(ctx, C, ii.ravel(), jj.ravel())
+    want = {(int(r), int(c)) for r, c in zip(ref.bi, ref.bj)}
+    got = {(int(r), int(c)) for r, c, f in zip(ii.ravel(), jj.ravel(), found) if f}
+    assert got == want
+    rel = _window_check(S, ctx, C, ref, 1e-12)
+    # the leaf inputs themselves match the generator bit for bit
+    g, f = S.spamm_gather_leaves(ctx, GA, A_rows.bi[:64], A_rows.bj[:64])
+    assert f.all() and np.array_equal(g, A_rows.data[:64])
+    print(f"{mode} tau={tau}: kept {st['n_kept']} c_leaves {st['n_c_leaves']} window rel {rel:.2e} "
+          f"borderline {st['n_borderline']} ms_gemm {st['ms_gemm']:.1f}")
+
+
+@pytest.mark.parametrize("prec", ["bf16_split", "fp16_scaled"])
+def test_fullsize_tensor_window(S, setup, prec):
+    ctx, pa, pb, GA, GB = setup
+    tau = 1e-6
+    C = S.spamm_multiply(ctx, GA, GB, tau, "combined", prec)
+    w = 10
+    A_rows, B_cols = sampled.window_inputs(pa, pb, BS, range(w), range(w))
+    ref, ikj = sampled.window_product(A_rows, B_cols, tau, oracle.COMBINED)
+    rel = _window_check(S, ctx, C, ref, 1e-4)
+    print(f"{prec} combined tau={tau}: window rel error vs FP64 oracle {rel:.2e}")
+
+
+def test_fullsize_scattered_leaves(S, setup):
+    ctx, pa, pb, GA, GB = setup
+    tau = 1e-6
+    C = S.spamm_multiply(ctx, GA, GB, tau, "combined", "fp64")
+    rng = np.random.default_rng(4)
+    nb = N // BS
+    picks = [(int(r), int(c)) for r, c in rng.integers(0, nb, (6, 2))]
+    picks += [(r, min(nb - 1, r + int(d))) for r, d in zip(rng.integers(0, nb, 6), rng.integers(0, 3, 6))]
+    for (i, j) in picks:
+        A_rows, B_cols = sampled.window_inputs(pa, pb, BS, [i], [j])
+        ref, _ = sampled.window_product(A_rows, B_cols, tau, oracle.COMBINED)
+        g, f = S.spamm_gather_leaves(ctx, C, [i], [j])
+        if ref.m == 0:
+            assert not f[0]
+        else:
+            assert f[0]
+            assert np.linalg.norm(g[0] - ref.data[0]) <= 1e-12 * np.linalg.norm(ref.data[0])
