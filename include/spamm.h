@@ -242,6 +242,39 @@ SPAMM_API spamm_status spamm_to_blocks(spamm_ctx ctx, spamm_mat m, int32_t* bi, 
 SPAMM_API spamm_status spamm_gather_leaves(spamm_ctx ctx, spamm_mat m, int64_t nq, const int32_t* bi,
                                            const int32_t* bj, double* payload_out, int32_t* found, int on_device);
 
+/* ------------------------------------------------- allocation-free variant */
+
+/* Largest nleaves spamm_leaf_sqnorms_noalloc accepts. */
+#define SPAMM_NOALLOC_MAX_LEAVES (1 << 24)
+
+/* The paper has no counterpart of this call; it serves callers that must not
+ * allocate device memory: services that reserve all device memory up front and
+ * may not allocate on their request path (an allocation can fail there, and
+ * cudaMalloc/cudaFree can synchronise the device), and plug-ins that run inside
+ * a host framework which owns the device memory.  No context is needed.
+ *
+ * Squared Frobenius norm of each of `nleaves` dense bs x bs row-major FP64
+ * leaves stored back to back at device address `payload` (leaf q at
+ * payload + q*bs*bs) into sq_out[q], and their sum into *total_out.  payload,
+ * sq_out and total_out are caller-allocated device memory of the current CUDA
+ * device; the work is enqueued on `cuda_stream` (NULL = legacy default stream)
+ * and the call returns without waiting for it.  Per-leaf results equal, bit for
+ * bit, the leaf norms the library stores for the same payload.
+ *
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  Its scratch
+ * (one FP64 partial sum per 4096 leaves, 32 KB) is a fixed device array in this
+ * library, which every GPU that loads the library holds until the process
+ * exits.  The first call on a device looks up that array's device address with
+ * the device current (a one-time set-up); make that first call before any
+ * stream capture.  All calls on a device share the array, so calls whose work
+ * overlaps on the GPU race: order them on one stream or synchronise between
+ * them.  Each call writes every scratch entry it reads before reading it.
+ * Errors: SPAMM_E_CAPACITY if nleaves > SPAMM_NOALLOC_MAX_LEAVES,
+ * SPAMM_E_INVALID_ARG (bs not 32/64/128, nleaves < 0, NULL pointer),
+ * SPAMM_E_CUDA (set-up or launch failed). */
+SPAMM_API spamm_status spamm_leaf_sqnorms_noalloc(const double* payload, int64_t nleaves, int bs, double* sq_out,
+                                                  double* total_out, void* cuda_stream);
+
 /* Nodes of quadtree level `level` (0 = root, L = leaves): Morton codes of
  * (row, col) at that level and squared norms, host memory.  *count receives
  * the node count; more than `cap` -> CAPACITY, nothing written. */

@@ -33,8 +33,9 @@ ENTRY_POINTS = (
     "spamm_create", "spamm_destroy", "spamm_set_stream", "spamm_set_allocator", "spamm_sync", "spamm_last_error",
     "spamm_from_dense", "spamm_from_blocks", "spamm_from_coo", "spamm_generate", "spamm_truncate", "spamm_release",
     "spamm_multiply", "spamm_kept_tasks", "spamm_frob_norm", "spamm_error", "spamm_mat_info", "spamm_to_dense",
-    "spamm_to_blocks", "spamm_gather_leaves", "spamm_level_norms",
+    "spamm_to_blocks", "spamm_gather_leaves", "spamm_level_norms", "spamm_leaf_sqnorms_noalloc",
 )
+NOALLOC_MAX_LEAVES = 1 << 24
 
 
 class SpammError(RuntimeError):
@@ -106,6 +107,7 @@ def load(path: str = LIB_PATH):
         "spamm_to_blocks": [vp, vp, vp, vp, vp, vp, i64, ctypes.c_int],
         "spamm_level_norms": [vp, vp, ctypes.c_int, vp, vp, i64, pi64],
         "spamm_gather_leaves": [vp, vp, i64, vp, vp, vp, vp, ctypes.c_int],
+        "spamm_leaf_sqnorms_noalloc": [vp, i64, ctypes.c_int, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -360,3 +362,15 @@ def spamm_gather_leaves(ctx: Context, m: Matrix, bi, bj):
                                                   bj.ctypes.data_as(vp), out.ctypes.data_as(vp),
                                                   found.ctypes.data_as(vp), 0))
     return out, found.astype(bool)
+
+
+def spamm_leaf_sqnorms_noalloc(payload, nleaves: int, bs: int, sq_out, total_out, stream=None) -> int:
+    """Allocation-free leaf norms: raw device pointers (ints) or CUDA tensors in,
+    the C status code out (OK = 0).  See include/spamm.h."""
+    def addr(x):
+        if x is None:
+            return None
+        return ctypes.c_void_p(x.data_ptr() if _is_torch(x) else int(x))
+    s = stream.cuda_stream if (stream is not None and hasattr(stream, "cuda_stream")) else stream
+    return load().spamm_leaf_sqnorms_noalloc(addr(payload), int(nleaves), int(bs), addr(sq_out), addr(total_out),
+                                              ctypes.c_void_p(s or 0))
