@@ -181,6 +181,22 @@ def run_reference(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------- multi-rank timing
+def aggregate_ranks(ms_local, flops_local, kept_local, dist=None):
+    """Whole-job numbers over independent replicas (one per GPU): the timed
+    region is the slowest rank's, the work is every rank's.
+    Returns (ms, GFLOP/s, mults/s)."""
+    import torch
+    ms, flops, kept = float(ms_local), float(flops_local), float(kept_local)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        w = torch.tensor([flops, kept], dtype=torch.float64)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+        ms, flops, kept = float(t[0]), float(w[0]), float(w[1])
+    return ms, flops / (ms / 1e3) / 1e9, kept / (ms / 1e3)
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     args = parse_args()
@@ -237,15 +253,8 @@ def main():
             stats.append(st)
         ev1.record(stream)
         barrier()
-    ms_total = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms_total], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t[0])
-    flops_rank = sum(s["kept_flops"] for s in stats)
-    kept_rank = sum(s["n_kept"] for s in stats)
-    value = world * flops_rank / (ms_total / 1e3) / 1e9
-    mults = world * kept_rank / (ms_total / 1e3)
+    ms_total, value, mults = aggregate_ranks(ev0.elapsed_time(ev1), sum(s["kept_flops"] for s in stats),
+                                             sum(s["n_kept"] for s in stats), dist)
     clocks = clk.summary()
 
     ms_gemm = statistics.mean(s["ms_gemm"] for s in stats)
