@@ -120,6 +120,7 @@ typedef struct {
   double ms_gemm;        /* device time of the leaf products (incl. C leaf norms) */
   double ms_cnorm;       /* device time of the C quadtree norms */
   int64_t n_launches;    /* CUDA kernels this call launched */
+  double ms_prep;        /* device time of the tensor-form operand terms (0 for FP64) */
 } spamm_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -205,6 +206,46 @@ SPAMM_API spamm_status spamm_release(spamm_mat m);
  * UNSUPPORTED (precision form not available for this bs), OOM, CUDA, TIMEOUT. */
 SPAMM_API spamm_status spamm_multiply(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_mode mode,
                             spamm_prec prec, spamm_mat* C, spamm_stats* stats);
+
+/* ------------------------------------------------- two-phase, batched form */
+
+typedef struct spamm_plan_s* spamm_plan;
+
+/* First phase of spamm_multiply: input truncation (TRUNCATE, COMBINED), the
+ * kept task list from the quadtree descent (the output structure built in
+ * advance, Section 4.4) and, for the tensor-core forms, the operand terms.
+ * The plan holds its own references to the storage it needs, so A and B may be
+ * released afterwards; it is immutable and may be executed many times.
+ * Errors as spamm_multiply. */
+SPAMM_API spamm_status spamm_plan_create(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_mode mode,
+                                         spamm_prec prec, spamm_plan* out);
+
+/* Sizes of a plan, for admission by memory footprint: kept leaf products,
+ * output leaves, device bytes the plan holds, device bytes its execution will
+ * allocate for the output.  Any output pointer may be NULL. */
+SPAMM_API spamm_status spamm_plan_info(spamm_plan p, int64_t* n_kept, int64_t* n_c_leaves, int64_t* plan_bytes,
+                                       int64_t* exec_bytes);
+
+/* Second phase, batched: the leaf products of all `nplans` plans (one
+ * precision form and one leaf size, made on this context) run in ONE
+ * persistent kernel launch (the batched leaf multiplication of Section 4.4,
+ * across requests); then every output's leaf norms and quadtree.  C[r]
+ * receives the product of plans[r]; each output is bit-identical to executing
+ * its plan alone.  Plans may come from other contexts on the same device
+ * (e.g. planned on another stream): spamm_plan_create returns only once its
+ * work is complete, and a plan must not be released while an execute that
+ * uses it is running.  Outputs belong to `ctx`.  `stats`, if not NULL, holds
+ * nplans entries (ms_gemm is the shared launch).  Errors: INVALID_ARG (mixed
+ * forms/sizes/devices), OOM, CUDA, TIMEOUT. */
+SPAMM_API spamm_status spamm_execute(spamm_ctx ctx, int64_t nplans, const spamm_plan* plans, spamm_mat* C,
+                                     spamm_stats* stats);
+
+SPAMM_API spamm_status spamm_plan_release(spamm_plan p);
+
+/* Run the persistent leaf-product launches of `ctx` on at most `nsms` SMs
+ * (0 = all), leaving the others to kernels on other streams, e.g. planning
+ * the next requests while a batch executes. */
+SPAMM_API spamm_status spamm_set_gemm_sms(spamm_ctx ctx, int nsms);
 
 /* Parity hook: the kept leaf triples of spamm_multiply(A, B, tau, mode) as
  * (i, k, j) int32 triples (3 per triple, host memory), grouped by C leaf in

@@ -1,6 +1,8 @@
 // api.cu -- the extern "C" entry points of libspamm (declared in spamm.h).
 #include <cmath>
 #include <cstring>
+#include <memory>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -131,6 +133,7 @@ spamm_status spamm_destroy(spamm_ctx ctx) {
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_scratch);
   cudaFreeHost(ctx->h_pinned);
+  if (ctx->d_zero) cudaFree(ctx->d_zero);
   delete ctx;
   return SPAMM_OK;
 }
@@ -249,21 +252,249 @@ spamm_status spamm_release(spamm_mat m) {
   return SPAMM_OK;
 }
 
-static void run_truncation(spamm_mat A, spamm_mat B, double tau, spamm_mode mode, spamm_mat* At, spamm_mat* Bt) {
+static void run_truncation(spamm_mat A, spamm_mat B, double tau, spamm_mode mode, spamm_mat* At, spamm_mat* Bt,
+                           spamm_ctx on = nullptr) {
   if (mode == SPAMM_MODE_SPAMM) {
     *At = A;
     *Bt = B;
     return;
   }
-  *At = truncate_block(A, tau);
-  *Bt = (B == A) ? *At : truncate_block(B, tau);
+  *At = truncate_block(A, tau, on);
+  *Bt = (B == A) ? *At : truncate_block(B, tau, on);
 }
 
 static void check_pair(spamm_mat A, spamm_mat B, double tau, spamm_mode mode) {
   if (A->n != B->n || A->bs != B->bs) fail(SPAMM_E_SHAPE, "A and B differ in n or bs");
-  if (A->ctx != B->ctx) fail(SPAMM_E_INVALID_ARG, "A and B belong to different contexts");
+  if (A->ctx->device != B->ctx->device) fail(SPAMM_E_INVALID_ARG, "A and B live on different devices");
   check_tau(tau);
   need(mode == SPAMM_MODE_TRUNCATE || mode == SPAMM_MODE_SPAMM || mode == SPAMM_MODE_COMBINED, "unknown mode");
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ plan / execute
+struct spamm_plan_s {
+  spamm_ctx ctx = nullptr;
+  int64_t n = 0;
+  int bs = 0;
+  int L = 0;
+  spamm_prec prec = SPAMM_PREC_FP64;
+  TaskList T;
+  BufP poolA, slotA, poolB, slotB, termsA, termsB, expA, expB;
+  int64_t na = 0, nb = 0;
+  double ms_truncate = 0, ms_tasks = 0, ms_prep = 0;
+  int64_t launches = 0;
+};
+
+namespace {
+
+size_t held_bytes(const spamm_plan_s& p) {
+  size_t b = 0;
+  for (const BufP* x : {&p.T.gcode, &p.T.gstart, &p.T.ta, &p.T.tb, &p.T.quads, &p.slotA, &p.slotB, &p.termsA,
+                        &p.termsB, &p.expA, &p.expB})
+    if (*x) b += (*x)->bytes;
+  return b;
+}
+
+void check_form(spamm_prec prec, int bs) {
+  need(prec == SPAMM_PREC_FP64 || prec == SPAMM_PREC_BF16_SPLIT || prec == SPAMM_PREC_FP16_SCALED,
+       "unknown precision form");
+  if (prec == SPAMM_PREC_FP64 && bs > 64) fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32 and 64");
+  if (prec != SPAMM_PREC_FP64 && bs != 64)
+    fail(SPAMM_E_UNSUPPORTED, "tensor-core precision forms are built for bs = 64");
+}
+
+spamm_plan make_plan(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_mode mode, spamm_prec prec) {
+  check_pair(A, B, tau, mode);
+  check_form(prec, A->bs);
+  Events ev;
+  const unsigned long long launches0 = g_kernel_launches;
+  std::unique_ptr<spamm_plan_s> p(new spamm_plan_s());
+  p->ctx = ctx;
+  p->n = A->n;
+  p->bs = A->bs;
+  p->L = A->L;
+  p->prec = prec;
+  CK(cudaEventRecord(ev.e[0], ctx->stream));
+  spamm_mat At = nullptr, Bt = nullptr;
+  run_truncation(A, B, tau, mode, &At, &Bt, ctx);
+  std::unique_ptr<spamm_mat_s> ownA(At != A ? At : nullptr), ownB((Bt != B && Bt != At) ? Bt : nullptr);
+  CK(cudaEventRecord(ev.e[1], ctx->stream));
+  p->T = build_tasks(At, Bt, tau, mode != SPAMM_MODE_TRUNCATE, ctx);
+  CK(cudaEventRecord(ev.e[2], ctx->stream));
+  p->na = At->nleaves;
+  p->nb = Bt->nleaves;
+  if (prec == SPAMM_PREC_FP64) {
+    p->poolA = At->pool;
+    p->slotA = At->slot;
+    p->poolB = Bt->pool;
+    p->slotB = Bt->slot;
+  } else {
+    prep_terms(At, prec, 0, &p->termsA, &p->expA, ctx);
+    prep_terms(Bt, prec, 1, &p->termsB, &p->expB, ctx);
+  }
+  CK(cudaEventRecord(ev.e[3], ctx->stream));
+  sync_and_check(ctx);
+  p->ms_truncate = elapsed_ms(ev.e[0], ev.e[1]);
+  p->ms_tasks = elapsed_ms(ev.e[1], ev.e[2]);
+  p->ms_prep = elapsed_ms(ev.e[2], ev.e[3]);
+  p->launches = (int64_t)(g_kernel_launches - launches0);
+  ctx->live_handles++;
+  return p.release();
+}
+
+void fill_stats(const spamm_plan_s& p, spamm_stats* st) {
+  memset(st, 0, sizeof(*st));
+  for (int t = 0; t < SPAMM_MAX_LEVELS; ++t) {
+    st->n_candidates[t] = p.T.n_candidates[t];
+    st->n_kept_level[t] = p.T.n_kept_level[t];
+  }
+  st->n_kept = p.T.ntasks;
+  st->n_borderline = p.T.n_borderline;
+  st->n_c_leaves = p.T.ngroups;
+  st->n_a_leaves = p.na;
+  st->n_b_leaves = p.nb;
+  st->levels = p.L;
+  st->bs = p.bs;
+  st->kept_flops = 2.0 * (double)p.bs * p.bs * p.bs * (double)p.T.ntasks;
+  st->ms_truncate = p.ms_truncate;
+  st->ms_tasks = p.ms_tasks;
+  st->ms_prep = p.ms_prep;
+}
+
+// One persistent launch over all plans, then each output's norms and quadtree.
+std::vector<spamm_mat> execute_plans(spamm_ctx ctx, const std::vector<spamm_plan>& plans, double* ms_gemm,
+                                     double* ms_cnorm, int64_t* launches) {
+  const int64_t np = (int64_t)plans.size();
+  const spamm_prec prec = plans[0]->prec;
+  const int bs = plans[0]->bs;
+  for (spamm_plan p : plans)
+    if (p->ctx->device != ctx->device || p->prec != prec || p->bs != bs)
+      fail(SPAMM_E_INVALID_ARG, "a batch needs one device, one precision form and one leaf size");
+  Events ev;
+  const unsigned long long launches0 = g_kernel_launches;
+  const int64_t e = (int64_t)bs * bs;
+  std::vector<std::unique_ptr<spamm_mat_s>> outs;
+  std::vector<BufP> csq(np);
+  std::vector<PlanDev> host(np);
+  std::vector<int64_t> ubegin(np + 1, 0);
+  for (int64_t r = 0; r < np; ++r) {
+    const spamm_plan_s& p = *plans[r];
+    outs.emplace_back(new_mat(ctx, p.n, bs));
+    spamm_mat Cm = outs.back().get();
+    Cm->pool = alloc_n<double>(ctx, p.T.ngroups * e);
+    csq[r] = alloc_n<double>(ctx, p.T.ngroups);
+    PlanDev& d = host[r];
+    d.gstart = P<int64_t>(p.T.gstart);
+    d.ta = P<int32_t>(p.T.ta);
+    d.tb = P<int32_t>(p.T.tb);
+    d.quads = P<int32_t>(p.T.quads);
+    d.poolA = P<double>(p.poolA);
+    d.slotA = P<int64_t>(p.slotA);
+    d.poolB = P<double>(p.poolB);
+    d.slotB = P<int64_t>(p.slotB);
+    d.termsA = P<uint8_t>(p.termsA);
+    d.termsB = P<uint8_t>(p.termsB);
+    d.expA = P<int32_t>(p.expA);
+    d.expB = P<int32_t>(p.expB);
+    d.cpool = P<double>(Cm->pool);
+    d.csq = P<double>(csq[r]);
+    // work units: output leaves for the FP64 kernel, quads of output leaves for the tensor-core kernel
+    const int64_t units = p.T.ngroups == 0 ? 0 : (prec == SPAMM_PREC_FP64 ? p.T.ngroups : p.T.nquads);
+    ubegin[r + 1] = ubegin[r] + units;
+  }
+  BufP dplans = alloc_n<PlanDev>(ctx, np), dub = alloc_n<int64_t>(ctx, np + 1);
+  CK(cudaMemcpyAsync(P<PlanDev>(dplans), host.data(), np * sizeof(PlanDev), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(P<int64_t>(dub), ubegin.data(), (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  BatchDev batch{P<PlanDev>(dplans), P<int64_t>(dub), (int)np, ubegin[np]};
+  CK(cudaEventRecord(ev.e[0], ctx->stream));
+  if (prec == SPAMM_PREC_FP64)
+    gemm_fp64_batch(ctx, bs, batch);
+  else if (prec == SPAMM_PREC_BF16_SPLIT)
+    gemm_bf16_batch(ctx, batch);
+  else
+    gemm_fp16_batch(ctx, batch);
+  CK(cudaEventRecord(ev.e[1], ctx->stream));
+  for (int64_t r = 0; r < np; ++r) {
+    const spamm_plan_s& p = *plans[r];
+    spamm_mat Cm = outs[r].get();
+    Level& leaf = Cm->lv[Cm->L];
+    leaf.count = p.T.ngroups;
+    leaf.code = p.T.gcode;
+    leaf.sq = csq[r];
+    Cm->nleaves = p.T.ngroups;
+    Cm->slot = alloc_n<int64_t>(ctx, p.T.ngroups);
+    fill_iota_i64(ctx, P<int64_t>(Cm->slot), p.T.ngroups);
+    build_tree(Cm);
+  }
+  CK(cudaEventRecord(ev.e[2], ctx->stream));
+  sync_and_check(ctx);
+  *ms_gemm = elapsed_ms(ev.e[0], ev.e[1]);
+  *ms_cnorm = elapsed_ms(ev.e[1], ev.e[2]);
+  *launches = (int64_t)(g_kernel_launches - launches0);
+  std::vector<spamm_mat> res;
+  for (auto& o : outs) res.push_back(o.release());
+  return res;
+}
+
+}  // namespace
+
+extern "C" {
+
+spamm_status spamm_plan_create(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_mode mode, spamm_prec prec,
+                               spamm_plan* out) {
+  if (!ctx || !A || !B || !out) return SPAMM_E_INVALID_ARG;
+  *out = nullptr;
+  return guarded(ctx, [&] { *out = make_plan(ctx, A, B, tau, mode, prec); });
+}
+
+spamm_status spamm_plan_info(spamm_plan p, int64_t* n_kept, int64_t* n_c_leaves, int64_t* plan_bytes,
+                             int64_t* exec_bytes) {
+  if (!p) return SPAMM_E_INVALID_ARG;
+  if (n_kept) *n_kept = p->T.ntasks;
+  if (n_c_leaves) *n_c_leaves = p->T.ngroups;
+  if (plan_bytes) *plan_bytes = (int64_t)held_bytes(*p);
+  if (exec_bytes) *exec_bytes = p->T.ngroups * ((int64_t)p->bs * p->bs * 8 + 8 + 8) + 4096;
+  return SPAMM_OK;
+}
+
+spamm_status spamm_plan_release(spamm_plan p) {
+  if (!p) return SPAMM_E_INVALID_ARG;
+  spamm_ctx ctx = p->ctx;
+  cudaSetDevice(ctx->device);
+  delete p;
+  ctx->live_handles--;
+  return SPAMM_OK;
+}
+
+spamm_status spamm_set_gemm_sms(spamm_ctx ctx, int nsms) {
+  if (!ctx) return SPAMM_E_INVALID_ARG;
+  return guarded(ctx, [&] {
+    need(nsms >= 0 && nsms <= ctx->num_sms, "nsms must be in [0, number of SMs]");
+    ctx->gemm_sm_limit = nsms;
+  });
+}
+
+spamm_status spamm_execute(spamm_ctx ctx, int64_t nplans, const spamm_plan* plans, spamm_mat* C, spamm_stats* stats) {
+  if (!ctx || nplans <= 0 || !plans || !C) return SPAMM_E_INVALID_ARG;
+  for (int64_t r = 0; r < nplans; ++r) C[r] = nullptr;
+  return guarded(ctx, [&] {
+    std::vector<spamm_plan> v(plans, plans + nplans);
+    for (spamm_plan p : v) need(p != nullptr, "NULL plan");
+    double ms_gemm = 0, ms_cnorm = 0;
+    int64_t launches = 0;
+    std::vector<spamm_mat> out = execute_plans(ctx, v, &ms_gemm, &ms_cnorm, &launches);
+    for (int64_t r = 0; r < nplans; ++r) {
+      C[r] = registered(out[r]);
+      if (stats) {
+        fill_stats(*v[r], &stats[r]);
+        stats[r].ms_gemm = ms_gemm;
+        stats[r].ms_cnorm = ms_cnorm;
+        stats[r].n_launches = launches;
+      }
+    }
+  });
 }
 
 spamm_status spamm_multiply(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_mode mode, spamm_prec prec,
@@ -271,63 +502,18 @@ spamm_status spamm_multiply(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau,
   if (!ctx || !A || !B || !C) return SPAMM_E_INVALID_ARG;
   *C = nullptr;
   return guarded(ctx, [&] {
-    check_pair(A, B, tau, mode);
-    need(prec == SPAMM_PREC_FP64 || prec == SPAMM_PREC_BF16_SPLIT || prec == SPAMM_PREC_FP16_SCALED,
-         "unknown precision form");
-    if (prec == SPAMM_PREC_FP64 && A->bs > 64)
-      fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32 and 64");
-    if (prec != SPAMM_PREC_FP64 && A->bs != 64)
-      fail(SPAMM_E_UNSUPPORTED, "tensor-core precision forms are built for bs = 64");
-    Events ev;
-    const unsigned long long launches0 = g_kernel_launches;
-    CK(cudaEventRecord(ev.e[0], ctx->stream));
-    spamm_mat At = nullptr, Bt = nullptr;
-    run_truncation(A, B, tau, mode, &At, &Bt);
-    std::unique_ptr<spamm_mat_s> ownA(At != A ? At : nullptr), ownB((Bt != B && Bt != At) ? Bt : nullptr);
-    CK(cudaEventRecord(ev.e[1], ctx->stream));
-    TaskList T = build_tasks(At, Bt, tau, mode != SPAMM_MODE_TRUNCATE);
-    CK(cudaEventRecord(ev.e[2], ctx->stream));
-    spamm_mat Cm = new_mat(ctx, A->n, A->bs);
-    std::unique_ptr<spamm_mat_s> ownC(Cm);
-    const int64_t e = (int64_t)A->bs * A->bs;
-    Cm->pool = alloc_n<double>(ctx, T.ngroups * e);
-    BufP csq = alloc_n<double>(ctx, T.ngroups);
-    if (prec == SPAMM_PREC_FP64)
-      gemm_fp64(At, Bt, T, P<double>(Cm->pool), P<double>(csq));
-    else
-      gemm_tc(At, Bt, T, prec, P<double>(Cm->pool), P<double>(csq));
-    CK(cudaEventRecord(ev.e[3], ctx->stream));
-    Level& leaf = Cm->lv[Cm->L];
-    leaf.count = T.ngroups;
-    leaf.code = T.gcode;
-    leaf.sq = csq;
-    Cm->nleaves = T.ngroups;
-    Cm->slot = alloc_n<int64_t>(ctx, T.ngroups);
-    fill_iota_i64(ctx, P<int64_t>(Cm->slot), T.ngroups);
-    build_tree(Cm);
-    CK(cudaEventRecord(ev.e[4], ctx->stream));
-    sync_and_check(ctx);
+    std::unique_ptr<spamm_plan_s> p(make_plan(ctx, A, B, tau, mode, prec));
+    ctx->live_handles--;  // the plan is internal to this call
+    double ms_gemm = 0, ms_cnorm = 0;
+    int64_t launches = 0;
+    std::vector<spamm_mat> out = execute_plans(ctx, {p.get()}, &ms_gemm, &ms_cnorm, &launches);
     if (stats) {
-      memset(stats, 0, sizeof(*stats));
-      for (int t = 0; t < SPAMM_MAX_LEVELS; ++t) {
-        stats->n_candidates[t] = T.n_candidates[t];
-        stats->n_kept_level[t] = T.n_kept_level[t];
-      }
-      stats->n_kept = T.ntasks;
-      stats->n_borderline = T.n_borderline;
-      stats->n_c_leaves = T.ngroups;
-      stats->n_a_leaves = At->nleaves;
-      stats->n_b_leaves = Bt->nleaves;
-      stats->levels = A->L;
-      stats->bs = A->bs;
-      stats->kept_flops = 2.0 * (double)A->bs * A->bs * A->bs * (double)T.ntasks;
-      stats->ms_truncate = elapsed_ms(ev.e[0], ev.e[1]);
-      stats->ms_tasks = elapsed_ms(ev.e[1], ev.e[2]);
-      stats->ms_gemm = elapsed_ms(ev.e[2], ev.e[3]);
-      stats->ms_cnorm = elapsed_ms(ev.e[3], ev.e[4]);
-      stats->n_launches = (int64_t)(g_kernel_launches - launches0);
+      fill_stats(*p, stats);
+      stats->ms_gemm = ms_gemm;
+      stats->ms_cnorm = ms_cnorm;
+      stats->n_launches = p->launches + launches;
     }
-    *C = registered(ownC.release());
+    *C = registered(out[0]);
   });
 }
 

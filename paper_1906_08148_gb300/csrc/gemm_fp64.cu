@@ -3,13 +3,14 @@
 //
 // C_ij = sum over the kept k (ascending) of A_ik B_kj, one output leaf per
 // work item (Algorithm 1, "C = AB" at the lowest level, run batched over the
-// task list as Section 4.4 describes).  Persistent CTAs claim output leaves
-// from an atomic counter; every output leaf is owned by one CTA, so there are
-// no atomics on C and the k order is fixed (results do not depend on the
-// schedule).  Operand leaves are contiguous bs*bs FP64 blocks and are staged
-// in shared memory by 1-D TMA bulk copies, double-buffered on mbarriers; the
-// product is register-tiled DFMA (FP64 has no tcgen05 kind; DFMA measures
-// faster than the FP64 mma.sync path on this part).
+// task list as Section 4.4 describes).  The output leaves of every plan in a
+// batch form one work list; persistent CTAs claim them from an atomic
+// counter.  Every output leaf is owned by one CTA, so there are no atomics on
+// C and the k order is fixed (results do not depend on the schedule or on the
+// batch).  Operand leaves are contiguous bs*bs FP64 blocks staged in shared
+// memory by 1-D TMA bulk copies, double-buffered on mbarriers; the product is
+// register-tiled DFMA (FP64 has no tcgen05 kind; DFMA measures faster than the
+// FP64 mma.sync path on this part).
 #include "internal.cuh"
 #include "ptx.cuh"
 
@@ -18,11 +19,8 @@ namespace spamm {
 constexpr int kGemmThreads = 256;
 
 template <int BS>
-__global__ void __launch_bounds__(kGemmThreads) gemm_fp64_kernel(
-    int64_t G, const int64_t* __restrict__ gstart, const int32_t* __restrict__ ta, const int32_t* __restrict__ tb,
-    const int64_t* __restrict__ slotA, const int64_t* __restrict__ slotB, const double* __restrict__ poolA,
-    const double* __restrict__ poolB, double* __restrict__ cpool, double* __restrict__ csq,
-    unsigned long long* __restrict__ work, int* __restrict__ err) {
+__global__ void __launch_bounds__(kGemmThreads)
+    gemm_fp64_kernel(BatchDev batch, unsigned long long* __restrict__ work, int* __restrict__ err) {
   constexpr int LEAF = BS * BS;
   constexpr uint32_t LEAF_BYTES = LEAF * sizeof(double);
   constexpr int TM = BS / 16;  // per-thread tile TM x TM: rows tr + 16 i, cols tc + 16 j
@@ -30,7 +28,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_fp64_kernel(
   double* sA[2] = {reinterpret_cast<double*>(smem_raw), reinterpret_cast<double*>(smem_raw) + 2 * LEAF};
   double* sB[2] = {reinterpret_cast<double*>(smem_raw) + LEAF, reinterpret_cast<double*>(smem_raw) + 3 * LEAF};
   __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int64_t s_g;
+  __shared__ int64_t s_u;
   __shared__ int s_abort;
   __shared__ double s_red[kGemmThreads / 32];
 
@@ -46,19 +44,21 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_fp64_kernel(
   uint32_t phase[2] = {0u, 0u};
   uint32_t inflight = 0;  // bit s: stage s has a copy that nobody waited for
 
-  auto issue = [&](int64_t q, int s) {
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&bar[s], 2 * LEAF_BYTES);
-    bulk_g2s(sA[s], poolA + slotA[ta[q]] * LEAF, LEAF_BYTES, &bar[s]);
-    bulk_g2s(sB[s], poolB + slotB[tb[q]] * LEAF, LEAF_BYTES, &bar[s]);
-  };
-
   for (;;) {
-    if (tid == 0) s_g = (int64_t)atomicAdd(work, 1ull);
+    if (tid == 0) s_u = (int64_t)atomicAdd(work, 1ull);
     __syncthreads();
-    const int64_t g = s_g;
-    if (g >= G || s_abort) break;
-    const int64_t q0 = gstart[g], q1 = gstart[g + 1];
+    const int64_t u = s_u;
+    if (u >= batch.nunits || s_abort) break;
+    const int r = plan_of(batch.ubegin, batch.nplans, u);
+    const PlanDev& pl = batch.plans[r];
+    const int64_t g = u - batch.ubegin[r];
+    const int64_t q0 = pl.gstart[g], q1 = pl.gstart[g + 1];
+    auto issue = [&](int64_t q, int s) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bar[s], 2 * LEAF_BYTES);
+      bulk_g2s(sA[s], pl.poolA + pl.slotA[pl.ta[q]] * LEAF, LEAF_BYTES, &bar[s]);
+      bulk_g2s(sB[s], pl.poolB + pl.slotB[pl.tb[q]] * LEAF, LEAF_BYTES, &bar[s]);
+    };
     double acc[TM][TM];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_fp64_kernel(
     if (q0 >= q1) inflight &= ~1u;
     if (s_abort) break;
     // epilogue: write C leaf g and its squared Frobenius norm (kernel (d))
-    double* C = cpool + g * LEAF;
+    double* C = pl.cpool + g * LEAF;
     double s2 = 0.0;
 #pragma unroll
     for (int i = 0; i < TM; ++i)
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_fp64_kernel(
     if (tid == 0) {
       double t = 0.0;
       for (int w = 0; w < kGemmThreads / 32; ++w) t += s_red[w];
-      csq[g] = t;
+      pl.csq[g] = t;
     }
   }
   // leave no bulk copy in flight into this CTA's shared memory
@@ -128,28 +128,26 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_fp64_kernel(
 }
 
 template <int BS>
-static void launch_fp64(spamm_mat A, spamm_mat B, const TaskList& T, double* cpool, double* csq) {
-  spamm_ctx ctx = A->ctx;
+static void launch_fp64(spamm_ctx ctx, const BatchDev& b) {
   const size_t smem = 4 * (size_t)BS * BS * sizeof(double);
   CK(cudaFuncSetAttribute(gemm_fp64_kernel<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_fp64_kernel<BS>, kGemmThreads, smem));
   if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)ctx->num_sms * per_sm;
-  if (grid > T.ngroups) grid = T.ngroups;
+  const int sms = ctx->gemm_sm_limit > 0 ? ctx->gemm_sm_limit : ctx->num_sms;
+  int64_t grid = (int64_t)sms * per_sm;
+  if (grid > b.nunits) grid = b.nunits;
   unsigned long long* work = ctx->d_scratch + 8;
   CK(cudaMemsetAsync(work, 0, sizeof(unsigned long long), ctx->stream));
-  gemm_fp64_kernel<BS><<<(unsigned)grid, kGemmThreads, smem, ctx->stream>>>(
-      T.ngroups, P<int64_t>(T.gstart), P<int32_t>(T.ta), P<int32_t>(T.tb), P<int64_t>(A->slot), P<int64_t>(B->slot),
-      P<double>(A->pool), P<double>(B->pool), cpool, csq, work, ctx->d_err);
+  gemm_fp64_kernel<BS><<<(unsigned)grid, kGemmThreads, smem, ctx->stream>>>(b, work, ctx->d_err);
   CK_LAUNCH("gemm_fp64_kernel");
 }
 
-void gemm_fp64(spamm_mat A, spamm_mat B, const TaskList& T, double* cpool, double* csq) {
-  if (T.ngroups == 0) return;
-  switch (A->bs) {
-    case 32: launch_fp64<32>(A, B, T, cpool, csq); break;
-    case 64: launch_fp64<64>(A, B, T, cpool, csq); break;
+void gemm_fp64_batch(spamm_ctx ctx, int bs, const BatchDev& b) {
+  if (b.nunits == 0) return;
+  switch (bs) {
+    case 32: launch_fp64<32>(ctx, b); break;
+    case 64: launch_fp64<64>(ctx, b); break;
     default: fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32 and 64");
   }
 }

@@ -20,7 +20,7 @@ struct Error {
 void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 #define CK(x) ::spamm::check_cuda((x), #x, __FILE__, __LINE__)
 // Every kernel launch is followed by CK_LAUNCH, which also counts it.
-extern unsigned long long g_kernel_launches;
+extern thread_local unsigned long long g_kernel_launches;
 #define CK_LAUNCH(what) \
   (++::spamm::g_kernel_launches, ::spamm::check_cuda(cudaGetLastError(), what, __FILE__, __LINE__))
 
@@ -108,7 +108,9 @@ struct spamm_ctx_s {
   int* d_err = nullptr;                      // device error word
   unsigned long long* d_scratch = nullptr;   // 64 counters (statistics, work queues)
   void* h_pinned = nullptr;                  // 4 KB pinned staging for scalar read-backs
+  void* d_zero = nullptr;                    // 8 KB of zeros (tensor-form padding operand)
   int num_sms = 0;
+  int gemm_sm_limit = 0;                     // 0: leaf GEMM may use every SM
   int live_handles = 0;
 };
 
@@ -130,7 +132,7 @@ void build_tree(spamm_mat m);  // levels L-1..0 from m->lv[L]
 // Leaf set from candidate leaves: keep[q] selects rows of (code, sq, slot) already sorted by code.
 void set_leaves_compacted(spamm_mat m, int64_t ncand, const uint32_t* code, const double* sq, const int64_t* slot,
                           const uint8_t* keep);
-spamm_mat truncate_block(spamm_mat in, double tau);
+spamm_mat truncate_block(spamm_mat in, double tau, spamm_ctx on = nullptr);  // work on `on` (default: in's context)
 spamm_mat truncate_element(spamm_mat in, double tau);
 void leaf_sqnorms(spamm_ctx ctx, const double* pool, const int64_t* slot, int64_t nleaves, int bs, double* sq,
                   uint8_t* nonzero, int check_finite);
@@ -143,15 +145,58 @@ struct TaskList {
   BufP gcode;           // uint32 Morton code of each C leaf, ascending
   BufP gstart;          // int64 [ngroups + 1] first task of each C leaf
   BufP ta, tb;          // int32 leaf index in A / B of each task (k ascending within a C leaf)
+  int64_t nquads = 0;   // output nodes one level above the leaves
+  BufP quads;           // int32 [4 * nquads]: C leaf (group) index of child 2*ci + cj, -1 if absent
   int64_t n_candidates[SPAMM_MAX_LEVELS] = {};
   int64_t n_kept_level[SPAMM_MAX_LEVELS] = {};
   int64_t n_borderline = 0;
 };
-TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms);
+TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm_ctx on = nullptr);
 
-// ---- leaf products (gemm_fp64.cu) ----
-// C leaf g = sum over its tasks of A[ta] B[tb]; writes cpool (g-th slot) and csq[g].
-void gemm_fp64(spamm_mat A, spamm_mat B, const TaskList& T, double* cpool, double* csq);
-// Tensor-core forms (gemm_tc.cu): operand split/scale pass, then the tcgen05 leaf GEMM.
-void gemm_tc(spamm_mat A, spamm_mat B, const TaskList& T, spamm_prec prec, double* cpool, double* csq);
+// ---- batched leaf products (gemm_fp64.cu, gemm_tc.cu) ----
+// Device view of one planned multiplication.  A batch is an array of these;
+// its work units (output leaves, or quads of output leaves for the BF16
+// kernel) are numbered consecutively across plans: plan r owns units
+// [ubegin[r], ubegin[r+1]).  Output leaf g of plan r is the sum over its
+// tasks of A[ta] B[tb], written to cpool + g*bs*bs with its squared norm in csq[g].
+struct PlanDev {
+  const int64_t* gstart;
+  const int32_t* ta;
+  const int32_t* tb;
+  const int32_t* quads;
+  const double* poolA;
+  const int64_t* slotA;
+  const double* poolB;
+  const int64_t* slotB;
+  const uint8_t* termsA;  // tensor forms: operand terms per leaf
+  const uint8_t* termsB;
+  const int32_t* expA;    // FP16 form: per-leaf scale exponents
+  const int32_t* expB;
+  double* cpool;
+  double* csq;
+};
+struct BatchDev {
+  const PlanDev* plans;
+  const int64_t* ubegin;  // nplans + 1 entries
+  int nplans;
+  int64_t nunits;
+};
+// Plan owning unit u (the last r with ubegin[r] <= u).
+__device__ __forceinline__ int plan_of(const int64_t* __restrict__ ubegin, int nplans, int64_t u) {
+  int lo = 0, hi = nplans - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ubegin[mid] <= u)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+void gemm_fp64_batch(spamm_ctx ctx, int bs, const BatchDev& b);
+void gemm_fp16_batch(spamm_ctx ctx, const BatchDev& b);
+void gemm_bf16_batch(spamm_ctx ctx, const BatchDev& b);
+// Operand terms of a leaf set for a tensor form (role 0: used as A, 1: as B).
+void prep_terms(spamm_mat M, spamm_prec prec, int role, BufP* terms, BufP* expo, spamm_ctx on = nullptr);
+const uint8_t* zero_term(spamm_ctx ctx);  // 8 KB of zeros, allocated once per context
 }  // namespace spamm

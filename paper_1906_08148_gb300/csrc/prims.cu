@@ -6,7 +6,7 @@
 
 namespace spamm {
 
-unsigned long long g_kernel_launches = 0;
+thread_local unsigned long long g_kernel_launches = 0;  // per host thread: a context is used by one thread
 
 void fail(spamm_status st, const std::string& msg) { throw Error{st, msg}; }
 

@@ -211,8 +211,8 @@ __global__ void block_keep_kernel(const double* __restrict__ sq, int64_t n, doub
     keep[q] = !(sqrt(sq[q]) < tau);
 }
 
-spamm_mat truncate_block(spamm_mat in, double tau) {
-  spamm_ctx ctx = in->ctx;
+spamm_mat truncate_block(spamm_mat in, double tau, spamm_ctx on) {
+  spamm_ctx ctx = on ? on : in->ctx;
   spamm_mat out = new_mat(ctx, in->n, in->bs);
   out->pool = in->pool;
   const int64_t n = in->nleaves;

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                       const int4* __restrict__ childB, const uint8_t* __restrict__ mask,
                       const uint64_t* __restrict__ packed, const uint64_t* __restrict__ off,
                       int32_t* __restrict__ ta2, int32_t* __restrict__ tb2, uint32_t* __restrict__ gcode2,
-                      int64_t* __restrict__ gstart2) {
+                      int64_t* __restrict__ gstart2, int32_t* __restrict__ quad) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += nw) {
@@ -115,11 +115,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     for (int c = 0; c < 4; ++c) base[c] = (int64_t)(off[4 * g + c] & kCountMask);
     if (lane < 4) {
       const uint64_t o = off[4 * g + lane];
-      if (packed[4 * g + lane] & kCountMask) {
+      const bool present = (packed[4 * g + lane] & kCountMask) != 0;
+      if (present) {
         const int64_t gid = (int64_t)(o >> 36);
         gcode2[gid] = 4u * gcode[g] + (uint32_t)lane;
         gstart2[gid] = (int64_t)(o & kCountMask);
       }
+      if (quad) quad[4 * g + lane] = present ? (int32_t)(o >> 36) : -1;
     }
     for (int64_t qb = q0; qb < q1; qb += 32) {
       const int64_t q = qb + lane;
@@ -175,8 +177,8 @@ static unsigned warps_grid(spamm_ctx ctx, int64_t items) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
-TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms) {
-  spamm_ctx ctx = A->ctx;
+TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm_ctx on) {
+  spamm_ctx ctx = on ? on : A->ctx;
   TaskList T;
   if (A->nleaves == 0 || B->nleaves == 0) {
     T.gstart = alloc_n<int64_t>(ctx, 1);
@@ -207,6 +209,13 @@ TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms) {
     Q = (int64_t)hp[0];
     G = Q;
     T.n_borderline = (int64_t)hp[2];
+    if (G > 0) {
+      // one output leaf: a quad holding only child 0
+      const int32_t q4[4] = {0, -1, -1, -1};
+      T.nquads = 1;
+      T.quads = alloc_n<int32_t>(ctx, 4);
+      CK(cudaMemcpyAsync(P<int32_t>(T.quads), q4, sizeof(q4), cudaMemcpyHostToDevice, ctx->stream));
+    }
   }
   for (int t = 0; t < A->L; ++t) {
     const bool leaf = (t + 1 == A->L);
@@ -230,6 +239,11 @@ TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms) {
     T.n_kept_level[t + 1] = Q2;
     if (leaf) T.n_borderline = (int64_t)h_stats[1];
     BufP gcode2 = alloc_n<uint32_t>(ctx, G2), gstart2 = alloc_n<int64_t>(ctx, G2 + 1);
+    if (leaf) {
+      // the parents of the C leaves: their four children form the quads
+      T.nquads = G;
+      T.quads = alloc_n<int32_t>(ctx, 4 * G);
+    }
     BufP ta2 = alloc_n<int32_t>(ctx, Q2), tb2 = alloc_n<int32_t>(ctx, Q2);
     CK(cudaMemcpyAsync(P<int64_t>(gstart2) + G2, &T.n_kept_level[t + 1], sizeof(int64_t), cudaMemcpyHostToDevice,
                        ctx->stream));
@@ -237,7 +251,7 @@ TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms) {
       task_write_kernel<<<warps_grid(ctx, G), kWarpsPerBlock * 32, 0, ctx->stream>>>(
           G, P<int64_t>(gstart), P<uint32_t>(gcode), P<int32_t>(ta), P<int32_t>(tb), P<int4>(A->lv[t].child),
           P<int4>(B->lv[t].child), P<uint8_t>(mask), P<uint64_t>(packed), P<uint64_t>(off), P<int32_t>(ta2),
-          P<int32_t>(tb2), P<uint32_t>(gcode2), P<int64_t>(gstart2));
+          P<int32_t>(tb2), P<uint32_t>(gcode2), P<int64_t>(gstart2), leaf ? P<int32_t>(T.quads) : nullptr);
       CK_LAUNCH("task_write_kernel");
     }
     G = G2;

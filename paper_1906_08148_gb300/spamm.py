@@ -34,6 +34,7 @@ ENTRY_POINTS = (
     "spamm_from_dense", "spamm_from_blocks", "spamm_from_coo", "spamm_generate", "spamm_truncate", "spamm_release",
     "spamm_multiply", "spamm_kept_tasks", "spamm_frob_norm", "spamm_error", "spamm_mat_info", "spamm_to_dense",
     "spamm_to_blocks", "spamm_gather_leaves", "spamm_level_norms", "spamm_leaf_sqnorms_noalloc",
+    "spamm_plan_create", "spamm_plan_info", "spamm_execute", "spamm_plan_release", "spamm_set_gemm_sms",
 )
 NOALLOC_MAX_LEAVES = 1 << 24
 
@@ -56,7 +57,7 @@ class Stats(ctypes.Structure):
                 ("n_a_leaves", ctypes.c_int64), ("n_b_leaves", ctypes.c_int64), ("levels", ctypes.c_int32),
                 ("bs", ctypes.c_int32), ("kept_flops", ctypes.c_double), ("ms_truncate", ctypes.c_double),
                 ("ms_tasks", ctypes.c_double), ("ms_gemm", ctypes.c_double), ("ms_cnorm", ctypes.c_double),
-                ("n_launches", ctypes.c_int64)]
+                ("n_launches", ctypes.c_int64), ("ms_prep", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         L = self.levels
@@ -64,7 +65,8 @@ class Stats(ctypes.Structure):
                 "n_kept": self.n_kept, "n_borderline": self.n_borderline, "n_c_leaves": self.n_c_leaves,
                 "n_a_leaves": self.n_a_leaves, "n_b_leaves": self.n_b_leaves, "levels": L, "bs": self.bs,
                 "kept_flops": self.kept_flops, "ms_truncate": self.ms_truncate, "ms_tasks": self.ms_tasks,
-                "ms_gemm": self.ms_gemm, "ms_cnorm": self.ms_cnorm, "n_launches": self.n_launches}
+                "ms_gemm": self.ms_gemm, "ms_cnorm": self.ms_cnorm, "n_launches": self.n_launches,
+                "ms_prep": self.ms_prep}
 
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -108,6 +110,11 @@ def load(path: str = LIB_PATH):
         "spamm_level_norms": [vp, vp, ctypes.c_int, vp, vp, i64, pi64],
         "spamm_gather_leaves": [vp, vp, i64, vp, vp, vp, vp, ctypes.c_int],
         "spamm_leaf_sqnorms_noalloc": [vp, i64, ctypes.c_int, vp, vp, vp],
+        "spamm_plan_create": [vp, vp, vp, f64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)],
+        "spamm_plan_info": [vp, pi64, pi64, pi64, pi64],
+        "spamm_execute": [vp, i64, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(Stats)],
+        "spamm_plan_release": [vp],
+        "spamm_set_gemm_sms": [vp, ctypes.c_int],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -374,3 +381,59 @@ def spamm_leaf_sqnorms_noalloc(payload, nleaves: int, bs: int, sq_out, total_out
     s = stream.cuda_stream if (stream is not None and hasattr(stream, "cuda_stream")) else stream
     return load().spamm_leaf_sqnorms_noalloc(addr(payload), int(nleaves), int(bs), addr(sq_out), addr(total_out),
                                               ctypes.c_void_p(s or 0))
+
+
+class Plan:
+    """First phase of a multiplication (spamm_plan_create): truncation, task list, operand terms."""
+
+    def __init__(self, ctx: Context, handle: ctypes.c_void_p):
+        self.ctx = ctx
+        self.handle = handle
+
+    def info(self) -> dict:
+        k, c, pb, eb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(self.ctx.handle, load().spamm_plan_info(self.handle, ctypes.byref(k), ctypes.byref(c),
+                                                       ctypes.byref(pb), ctypes.byref(eb)))
+        return {"n_kept": k.value, "n_c_leaves": c.value, "plan_bytes": pb.value, "exec_bytes": eb.value}
+
+    def close(self):
+        if self.handle:
+            load().spamm_plan_release(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spamm_plan_create(ctx: Context, A: Matrix, B: Matrix, tau: float, mode: str = "spamm",
+                      prec: str = "fp64") -> Plan:
+    out = ctypes.c_void_p()
+    _check(ctx.handle, load().spamm_plan_create(ctx.handle, A.handle, B.handle, float(tau), MODES[mode],
+                                                PRECS[prec], ctypes.byref(out)))
+    return Plan(ctx, out)
+
+
+def spamm_plan_info(plan: Plan) -> dict:
+    return plan.info()
+
+
+def spamm_plan_release(plan: Plan):
+    plan.close()
+
+
+def spamm_execute(ctx: Context, plans, stats: bool = False):
+    """Run the leaf products of all plans in one persistent launch; returns the outputs (and stats)."""
+    n = len(plans)
+    arr = (ctypes.c_void_p * n)(*[p.handle for p in plans])
+    outs = (ctypes.c_void_p * n)()
+    sts = (Stats * n)()
+    _check(ctx.handle, load().spamm_execute(ctx.handle, n, arr, outs, sts))
+    Cs = [Matrix(ctx, ctypes.c_void_p(outs[i])) for i in range(n)]
+    return (Cs, [s.as_dict() for s in sts]) if stats else Cs
+
+
+def spamm_set_gemm_sms(ctx: Context, nsms: int):
+    _check(ctx.handle, load().spamm_set_gemm_sms(ctx.handle, int(nsms)))

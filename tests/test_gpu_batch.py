@@ -1,0 +1,99 @@
+"""Two-phase, batched multiplication: plans of different sizes, tau and methods
+run in one persistent launch; every output is bit-identical to the same
+plan executed alone and matches the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1906_08148_gb300 import spamm
+    return spamm
+
+
+@pytest.fixture(scope="module")
+def ctx(S):
+    return S.Context(0)
+
+
+REQUESTS = [(4096, 0.9, 1e-6, "combined"), (2048, 0.7, 1e-4, "spamm"), (8192, 1.1, 1e-8, "truncate"),
+            (1000, 0.8, 1e-5, "combined"), (4096, 0.6, 1e-6, "spamm")]
+
+
+def _inputs(S, ctx, n, alpha, bs):
+    GA = S.spamm_generate(ctx, synth.lattice_3d(n, alpha=alpha, seed=1), bs)
+    GB = S.spamm_generate(ctx, synth.lattice_3d(n, alpha=alpha, seed=2), bs)
+    return GA, GB
+
+
+@pytest.mark.parametrize("prec,bs", [("fp64", 64), ("fp64", 32), ("bf16_split", 64), ("fp16_scaled", 64)])
+def test_batch_equals_alone_bitwise(S, ctx, prec, bs):
+    plans, alone, inputs = [], [], []
+    for n, alpha, tau, mode in REQUESTS:
+        GA, GB = _inputs(S, ctx, n, alpha, bs)
+        inputs.append((GA, GB))
+        p = S.spamm_plan_create(ctx, GA, GB, tau, mode, prec)
+        plans.append(p)
+        alone.append(S.spamm_to_blocks(ctx, S.spamm_execute(ctx, [p])[0]))
+    Cs, st = S.spamm_execute(ctx, plans, stats=True)
+    for r, C in enumerate(Cs):
+        got = S.spamm_to_blocks(ctx, C)
+        for a, b in zip(alone[r], got):
+            assert np.array_equal(a, b), (prec, r)
+        assert st[r]["n_kept"] == plans[r].info()["n_kept"]
+    # the plans are reusable and independent of their inputs' handles
+    for GA, GB in inputs:
+        GA.close()
+        GB.close()
+    again = S.spamm_execute(ctx, plans[::-1])[::-1]
+    for r, C in enumerate(again):
+        assert np.array_equal(S.spamm_to_blocks(ctx, C)[2], alone[r][2])
+
+
+def test_batch_matches_oracle_fp64(S, ctx):
+    plans, refs = [], []
+    for n, alpha, tau, mode in REQUESTS[:3]:
+        pa, pb = synth.lattice_3d(n, alpha=alpha, seed=1), synth.lattice_3d(n, alpha=alpha, seed=2)
+        GA, GB = S.spamm_generate(ctx, pa, 64), S.spamm_generate(ctx, pb, 64)
+        plans.append(S.spamm_plan_create(ctx, GA, GB, tau, mode, "fp64"))
+        ref, _ = oracle.multiply(oracle.from_dense(synth.dense(pa), 64), oracle.from_dense(synth.dense(pb), 64),
+                                 tau, oracle.MODES[mode])
+        refs.append(ref)
+    for C, ref in zip(S.spamm_execute(ctx, plans), refs):
+        D = S.spamm_to_dense(ctx, C)
+        R = oracle.to_dense(ref)
+        assert np.linalg.norm(D - R) <= 1e-12 * np.linalg.norm(R)
+
+
+def test_batch_rejects_mixed_forms_and_reports_footprint(S, ctx):
+    GA, GB = _inputs(S, ctx, 2048, 0.8, 64)
+    p1 = S.spamm_plan_create(ctx, GA, GB, 1e-6, "spamm", "fp64")
+    p2 = S.spamm_plan_create(ctx, GA, GB, 1e-6, "spamm", "bf16_split")
+    with pytest.raises(S.SpammError) as e:
+        S.spamm_execute(ctx, [p1, p2])
+    assert e.value.status == S.E_INVALID_ARG
+    info = p2.info()
+    assert info["plan_bytes"] > 0 and info["exec_bytes"] >= info["n_c_leaves"] * 64 * 64 * 8
+    C, st = S.spamm_multiply(ctx, GA, GB, 1e-6, "spamm", "bf16_split", stats=True)
+    assert st["n_kept"] == info["n_kept"] and st["ms_prep"] > 0
+
+
+def test_gemm_sm_limit_keeps_results(S, ctx):
+    GA, GB = _inputs(S, ctx, 4096, 0.8, 64)
+    ref = S.spamm_to_blocks(ctx, S.spamm_multiply(ctx, GA, GB, 1e-6, "combined", "bf16_split"))
+    S.spamm_set_gemm_sms(ctx, 16)
+    try:
+        got = S.spamm_to_blocks(ctx, S.spamm_multiply(ctx, GA, GB, 1e-6, "combined", "bf16_split"))
+    finally:
+        S.spamm_set_gemm_sms(ctx, 0)
+    assert np.array_equal(ref[2], got[2])
