@@ -63,6 +63,20 @@ def parse_args():
     ap.add_argument("--serve-inputs", type=int, default=8)
     ap.add_argument("--serve-nmax", type=int, default=32768)
     ap.add_argument("--serve-batch", type=int, default=32)
+    ap.add_argument("--model-problem", action="store_true", help="the paper's 1-D model problem sweep")
+    ap.add_argument("--sweep", action="store_true", help="the three methods at equal accuracy on --config")
+    ap.add_argument("--sweep-taus", type=float, nargs="+", default=[1e-4, 1e-6, 1e-8])
+    ap.add_argument("--sigmas", type=float, nargs="+", default=[1e-2, 1e-4, 1e-6])
+    ap.add_argument("--block-sparse", action="store_true", help="random block-sparse sweep over fill-in")
+    ap.add_argument("--bsp-n", type=int, default=2048)
+    ap.add_argument("--bsp-bs", type=int, nargs="+", default=[32, 64])
+    ap.add_argument("--bsp-fills", type=float, nargs="+", default=[0.05, 0.1, 0.2, 0.3, 0.5, 0.7, 0.9])
+    ap.add_argument("--bsp-repeats", type=int, default=20)
+    ap.add_argument("--mp-n", type=int, default=40000)
+    ap.add_argument("--mp-bs", type=int, nargs="+", default=[64])
+    ap.add_argument("--mp-sigma", type=float, default=1e-6)
+    ap.add_argument("--mp-tau-lo", type=int, default=4, help="largest tau = 10^-lo")
+    ap.add_argument("--mp-tau-hi", type=int, default=12, help="smallest tau = 10^-hi")
     return ap.parse_args()
 
 
@@ -250,6 +264,134 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------ methods at equal accuracy
+def tau_sweep(S, ctx, GA, GB, taus, sigmas, prec="fp64"):
+    """The paper's comparison of the three methods (Section 5.3): multiply with
+    each method over a tau grid, measure ||AB - C||_F against the exact product
+    (tau = 0, no truncation, FP64), and for each target accuracy sigma take,
+    per method, the largest tau whose error is <= sigma.  Times are wall time
+    of the synchronous multiply (truncation + task list + leaf GEMM + C norms)."""
+    X, xs = S.spamm_multiply(ctx, GA, GB, 0.0, "spamm", "fp64", stats=True)
+    exact = {"n_kept": xs["n_kept"], "frob": S.spamm_frob_norm(ctx, X), "ms_gemm": xs["ms_gemm"]}
+    rows = {}
+    for mode in ("truncate", "spamm", "combined"):
+        rows[mode] = []
+        for tau in taus:
+            t0 = time.perf_counter()
+            C, st = S.spamm_multiply(ctx, GA, GB, tau, mode, prec, stats=True)
+            ms = 1e3 * (time.perf_counter() - t0)
+            err = S.spamm_error(ctx, X, C)
+            rows[mode].append({"tau": tau, "n_kept": st["n_kept"], "error": err, "ms": ms,
+                               "ms_gemm": st["ms_gemm"], "gflops": st["kept_flops"] / ms / 1e6,
+                               "mults_per_s": st["n_kept"] / ms * 1e3})
+            C.close()
+    X.close()
+    chosen = {}
+    for sigma in sigmas:
+        pick = {}
+        for mode, rs in rows.items():
+            ok = [r for r in rs if r["error"] <= sigma]
+            pick[mode] = max(ok, key=lambda r: r["tau"]) if ok else None
+        base = pick["truncate"]
+        chosen["%g" % sigma] = {
+            m: (c and {"tau": c["tau"], "n_kept": c["n_kept"], "error": c["error"], "ms": c["ms"],
+                       "gemm_vs_truncmul": c["n_kept"] / base["n_kept"] if base else None,
+                       "time_vs_truncmul": c["ms"] / base["ms"] if base else None})
+            for m, c in pick.items()}
+    return {"exact": exact, "chosen": chosen, "sweep": rows}
+
+
+def run_sweep(args, cfg):
+    """Equal-accuracy comparison on a bench workload (default: the 3-D lattice,
+    tau in {1e-4, 1e-6, 1e-8}, sigma in {1e-2, 1e-4, 1e-6})."""
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_1906_08148_gb300 import spamm as S
+
+    ctx = S.Context(0)
+    pa = synth.DecayParams(n=cfg["n"], kind=cfg["kind"], alpha=cfg["alpha"], seed=cfg["seeds"][0])
+    pb = synth.DecayParams(n=cfg["n"], kind=cfg["kind"], alpha=cfg["alpha"], seed=cfg["seeds"][1])
+    GA = S.spamm_generate(ctx, pa, cfg["bs"])
+    GB = GA if pb == pa else S.spamm_generate(ctx, pb, cfg["bs"])
+    res = tau_sweep(S, ctx, GA, GB, args.sweep_taus, args.sigmas, args.prec)
+    print(json.dumps({"metric": "methods at equal accuracy", "unit": "ms", "data": "synthetic",
+                      "config": {"workload": args.config, "desc": cfg["desc"], "bs": cfg["bs"],
+                                 "taus": args.sweep_taus, "sigmas": args.sigmas, "precision": args.prec},
+                      **res}), flush=True)
+    for m in {id(GA): GA, id(GB): GB}.values():
+        m.close()
+
+
+def run_model_problem(args):
+    """The paper's single-node model problem (Section 5.3): a 1-D decay matrix,
+    a_ij = u_ij exp(-0.005 |i-j|) (|a_ij| <= exp(-0.005 |i-j|)), elements below
+    1e-16 set to zero, n = 40000, multiplied by itself with the three methods,
+    tau = 1e-4 ... 1e-12, target accuracy sigma = 1e-6; per leaf size the
+    chosen tau of each method and its leaf products (gemm calls) and time
+    relative to Truncmul."""
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_1906_08148_gb300 import spamm as S
+
+    ctx = S.Context(0)
+    p = synth.model_1d(args.mp_n, alpha=0.005, seed=1)
+    taus = [10.0 ** -e for e in range(args.mp_tau_lo, args.mp_tau_hi + 1)]
+    out = {"metric": "model problem: methods at equal accuracy", "unit": "ms", "data": "synthetic",
+           "config": {"workload": "model_problem_1d", "n": args.mp_n, "alpha": 0.005, "cutoff": 1e-16,
+                      "sigma": args.mp_sigma, "taus": taus, "precision": "fp64"}, "by_bs": {}}
+    for bs in args.mp_bs:
+        G = S.spamm_generate(ctx, p, bs)
+        out["by_bs"][str(bs)] = tau_sweep(S, ctx, G, G, taus, [args.mp_sigma])
+        G.close()
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------ random block-sparse inputs
+def run_block_sparse(args):
+    """Section 5.2's leaf-library benchmark: two n x n matrices (n = 2048)
+    whose non-zero blocks are placed uniformly at random with fill-in factor
+    f, multiplied at tau = 0 (every non-null pair is a product; FP64).  Per
+    (bs, f): kept-block GFLOP/s (2 bs^3 x products / time of the whole
+    multiply), and the time of the quadtree task-list build (the predictor)
+    relative to the leaf products, the ratio the paper reports as ~1e-4 on
+    its CPU cluster."""
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_1906_08148_gb300 import spamm as S
+
+    ctx = S.Context(0)
+    rows = []
+    for bs in args.bsp_bs:
+        for fill in args.bsp_fills:
+            A = S.spamm_from_blocks(ctx, args.bsp_n, bs, *synth.block_sparse(args.bsp_n, bs, fill, seed=1))
+            B = S.spamm_from_blocks(ctx, args.bsp_n, bs, *synth.block_sparse(args.bsp_n, bs, fill, seed=2))
+            for _ in range(2):
+                S.spamm_multiply(ctx, A, B, 0.0, "spamm", args.prec).close()
+            ms, sts = [], []
+            for _ in range(args.bsp_repeats):
+                t0 = time.perf_counter()
+                C, st = S.spamm_multiply(ctx, A, B, 0.0, "spamm", args.prec, stats=True)
+                ms.append(1e3 * (time.perf_counter() - t0))
+                sts.append(st)
+                C.close()
+            med = statistics.median(ms)
+            tasks = statistics.median(s["ms_tasks"] for s in sts)
+            gemm = statistics.median(s["ms_gemm"] for s in sts)
+            rows.append({"bs": bs, "fill": fill, "a_blocks": A.info()["nleaves"], "n_kept": sts[0]["n_kept"],
+                         "ms": med, "gflops": sts[0]["kept_flops"] / med / 1e6,
+                         "gemm_gflops": sts[0]["kept_flops"] / gemm / 1e6, "ms_tasks": tasks, "ms_gemm": gemm,
+                         "predictor_over_multiply": tasks / gemm})
+            A.close()
+            B.close()
+    print(json.dumps({"metric": "random block-sparse multiply, tau = 0", "unit": "GFLOP/s", "data": "synthetic",
+                      "config": {"workload": "block_sparse", "n": args.bsp_n, "precision": args.prec,
+                                 "repeats": args.bsp_repeats, "timing": "median wall time of the synchronous call"},
+                      "rows": rows}), flush=True)
+
+
 # ---------------------------------------------------------- multi-rank timing
 def aggregate_ranks(ms_local, flops_local, kept_local, dist=None):
     """Whole-job numbers over independent replicas (one per GPU): the timed
@@ -276,6 +418,12 @@ def main():
         if args.prec == "fp64":
             args.prec = "bf16_split"
         return run_served(args)
+    if args.model_problem:
+        return run_model_problem(args)
+    if args.sweep:
+        return run_sweep(args, cfg)
+    if args.block_sparse:
+        return run_block_sparse(args)
 
     import numpy as np
     import torch
@@ -332,7 +480,8 @@ def main():
 
     ms_gemm = statistics.mean(s["ms_gemm"] for s in stats)
     kept = stats[-1]["n_kept"]
-    phases = {k: statistics.mean(s[k] for s in stats) for k in ("ms_truncate", "ms_tasks", "ms_gemm", "ms_cnorm")}
+    phases = {k: statistics.mean(s[k] for s in stats)
+              for k in ("ms_truncate", "ms_tasks", "ms_prep", "ms_gemm", "ms_cnorm")}
 
     e2e = None
     if not args.no_e2e and rank == 0:
@@ -343,17 +492,18 @@ def main():
         cpu = cpu_baseline(cfg, args.mode, args.tau, args.cpu_seconds)
 
     if rank == 0:
-        roof = roofline(args.prec, bs, kept, ms_gemm)
+        roof = roofline(args.prec, bs, kept, ms_gemm, statistics.mean(s["executed_flops"] for s in stats))
+        in_gb = (GA.info()["nleaves"] + (0 if GB is GA else GB.info()["nleaves"])) * bs * bs * 8 / 1e9
         line = {
             "metric": "kept-block GFLOP/s", "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.prec == "fp64" else args.prec, "data": "synthetic",
             "config": {"workload": args.config, "desc": cfg["desc"], "n": cfg["n"], "bs": bs, "method": args.mode,
-                       "tau": args.tau, "precision": args.prec, "l2": "inputs (2 x 27.7 GB) larger than L2",
+                       "tau": args.tau, "precision": args.prec, "l2": "inputs (%.1f GB of leaves) larger than L2" % in_gb,
                        "parallelism": "replicas" if world > 1 else "single"},
             "mults_per_s": mults,
-            "n_kept": kept, "n_c_leaves": stats[-1]["n_c_leaves"], "n_borderline": stats[-1]["n_borderline"],
+            "n_kept": kept, "n_steps": stats[-1]["n_steps"], "n_c_leaves": stats[-1]["n_c_leaves"], "n_borderline": stats[-1]["n_borderline"],
             "n_a_leaves": stats[-1]["n_a_leaves"], "n_b_leaves": stats[-1]["n_b_leaves"],
             "c_frob": nrm, "phase_ms": phases, "roofline": roof,
             "gpu_launches": None, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
@@ -366,13 +516,11 @@ def main():
         dist.destroy_process_group()
 
 
-# executed tensor flops per kept leaf product: M=128 x N (x K=64) MMAs
-EXECUTED_PER_PRODUCT = {"bf16_split": 2.0 * 128 * (192 + 64) * 64, "fp16_scaled": 2.0 * 128 * 128 * 64}
-
-
-def roofline(prec, bs, kept, ms_gemm):
+def roofline(prec, bs, kept, ms_gemm, executed_flops):
     """Roofline entry for the dominant kernel (the leaf GEMM), from the
-    CUDA-event duration of its launch inside the timed steps."""
+    CUDA-event duration of its launch inside the timed steps.  executed_flops:
+    what the kernel runs (tensor forms: every term product of every quad step
+    over the full 128 x 128 x 64 tile, counted by the library)."""
     import json as _json
     algo = 2.0 * bs ** 3 * kept
     secs = ms_gemm / 1e3
@@ -386,8 +534,8 @@ def roofline(prec, bs, kept, ms_gemm):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops_sustained": 1700.0}
     peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
     achieved = algo / secs / 1e12
-    executed = EXECUTED_PER_PRODUCT[prec] * kept / secs / 1e12
-    kernel = "gemm_tc_kernel<%s>" % prec
+    executed = executed_flops / secs / 1e12
+    kernel = "gemm_quad_kernel<%s>" % prec
     return {"kernel": kernel, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "executed": executed, "executed_frac": executed / peak,
             "traffic": load_traffic(kernel, kept),

@@ -120,7 +120,10 @@ typedef struct {
   double ms_gemm;        /* device time of the leaf products (incl. C leaf norms) */
   double ms_cnorm;       /* device time of the C quadtree norms */
   int64_t n_launches;    /* CUDA kernels this call launched */
-  double ms_prep;        /* device time of the tensor-form operand terms (0 for FP64) */
+  double ms_prep;        /* device time of the tensor-form operand terms and quad step list (0 for FP64) */
+  int64_t n_steps;       /* leaf-GEMM steps: FP64 = n_kept; tensor forms = k steps of output quads */
+  double executed_flops; /* flops the leaf-GEMM kernel executes: FP64 = kept_flops; tensor forms =
+                            n_steps x every term product over a 128 x 128 x 64 tile */
 } spamm_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -246,6 +249,14 @@ SPAMM_API spamm_status spamm_plan_release(spamm_plan p);
  * (0 = all), leaving the others to kernels on other streams, e.g. planning
  * the next requests while a batch executes. */
 SPAMM_API spamm_status spamm_set_gemm_sms(spamm_ctx ctx, int nsms);
+
+/* enable != 0: spamm_execute / spamm_multiply run their execute phase (the
+ * persistent leaf-product launch of every plan in the batch, then the output
+ * quadtrees' parent norms, one launch per level for the whole batch) as one
+ * captured CUDA graph.  Output buffers are allocated and the batch tables
+ * uploaded before the capture, so the captured sequence holds kernels and
+ * timing events only.  Results are identical either way.  Default 0. */
+SPAMM_API spamm_status spamm_set_exec_graph(spamm_ctx ctx, int enable);
 
 /* Parity hook: the kept leaf triples of spamm_multiply(A, B, tau, mode) as
  * (i, k, j) int32 triples (3 per triple, host memory), grouped by C leaf in

@@ -133,7 +133,7 @@ spamm_status spamm_destroy(spamm_ctx ctx) {
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_scratch);
   cudaFreeHost(ctx->h_pinned);
-  if (ctx->d_zero) cudaFree(ctx->d_zero);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   delete ctx;
   return SPAMM_OK;
 }
@@ -281,6 +281,9 @@ struct spamm_plan_s {
   spamm_prec prec = SPAMM_PREC_FP64;
   TaskList T;
   BufP poolA, slotA, poolB, slotB, termsA, termsB, expA, expB;
+  BufP qstart, qsteps;  // tensor forms: the quad step list
+  int64_t nsteps = 0;
+  std::vector<Level> cskel;  // output quadtree structure (codes, child links; no norms)
   int64_t na = 0, nb = 0;
   double ms_truncate = 0, ms_tasks = 0, ms_prep = 0;
   int64_t launches = 0;
@@ -290,7 +293,7 @@ namespace {
 
 size_t held_bytes(const spamm_plan_s& p) {
   size_t b = 0;
-  for (const BufP* x : {&p.T.gcode, &p.T.gstart, &p.T.ta, &p.T.tb, &p.T.quads, &p.slotA, &p.slotB, &p.termsA,
+  for (const BufP* x : {&p.T.gcode, &p.T.gstart, &p.T.ta, &p.T.tb, &p.T.quads, &p.qstart, &p.qsteps, &p.slotA, &p.slotB, &p.termsA,
                         &p.termsB, &p.expA, &p.expB})
     if (*x) b += (*x)->bytes;
   return b;
@@ -321,6 +324,14 @@ spamm_plan make_plan(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_
   std::unique_ptr<spamm_mat_s> ownA(At != A ? At : nullptr), ownB((Bt != B && Bt != At) ? Bt : nullptr);
   CK(cudaEventRecord(ev.e[1], ctx->stream));
   p->T = build_tasks(At, Bt, tau, mode != SPAMM_MODE_TRUNCATE, ctx);
+  {
+    // the output structure is fixed by the kept set (Section 4.4): build it now
+    std::unique_ptr<spamm_mat_s> sk(new_mat(ctx, A->n, A->bs));
+    sk->lv[sk->L].count = p->T.ngroups;
+    sk->lv[sk->L].code = p->T.gcode;
+    build_skeleton(sk.get());
+    p->cskel = sk->lv;
+  }
   CK(cudaEventRecord(ev.e[2], ctx->stream));
   p->na = At->nleaves;
   p->nb = Bt->nleaves;
@@ -332,6 +343,8 @@ spamm_plan make_plan(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_
   } else {
     prep_terms(At, prec, 0, &p->termsA, &p->expA, ctx);
     prep_terms(Bt, prec, 1, &p->termsB, &p->expB, ctx);
+    p->nsteps = build_quad_steps(ctx, p->T, P<uint32_t>(At->lv[At->L].code), P<int32_t>(p->expA),
+                                 P<int32_t>(p->expB), &p->qstart, &p->qsteps);
   }
   CK(cudaEventRecord(ev.e[3], ctx->stream));
   sync_and_check(ctx);
@@ -357,12 +370,17 @@ void fill_stats(const spamm_plan_s& p, spamm_stats* st) {
   st->levels = p.L;
   st->bs = p.bs;
   st->kept_flops = 2.0 * (double)p.bs * p.bs * p.bs * (double)p.T.ntasks;
+  st->n_steps = p.prec == SPAMM_PREC_FP64 ? p.T.ntasks : p.nsteps;
+  st->executed_flops = p.prec == SPAMM_PREC_FP64 ? st->kept_flops : (double)p.nsteps * quad_step_flops(p.prec);
   st->ms_truncate = p.ms_truncate;
   st->ms_tasks = p.ms_tasks;
   st->ms_prep = p.ms_prep;
 }
 
-// One persistent launch over all plans, then each output's norms and quadtree.
+// One persistent launch over all plans, then every output's parent norms (one
+// launch per level for the whole batch).  Buffers are allocated and the plan
+// table uploaded first, so the launch sequence has no host synchronisation;
+// with ctx->exec_graph it is captured and run as one CUDA graph.
 std::vector<spamm_mat> execute_plans(spamm_ctx ctx, const std::vector<spamm_plan>& plans, double* ms_gemm,
                                      double* ms_cnorm, int64_t* launches) {
   const int64_t np = (int64_t)plans.size();
@@ -375,15 +393,20 @@ std::vector<spamm_mat> execute_plans(spamm_ctx ctx, const std::vector<spamm_plan
   const unsigned long long launches0 = g_kernel_launches;
   const int64_t e = (int64_t)bs * bs;
   std::vector<std::unique_ptr<spamm_mat_s>> outs;
-  std::vector<BufP> csq(np);
+  std::vector<spamm_mat> outp;
   std::vector<PlanDev> host(np);
   std::vector<int64_t> ubegin(np + 1, 0);
   for (int64_t r = 0; r < np; ++r) {
     const spamm_plan_s& p = *plans[r];
     outs.emplace_back(new_mat(ctx, p.n, bs));
     spamm_mat Cm = outs.back().get();
+    outp.push_back(Cm);
+    Cm->lv = p.cskel;
+    Cm->nleaves = p.T.ngroups;
     Cm->pool = alloc_n<double>(ctx, p.T.ngroups * e);
-    csq[r] = alloc_n<double>(ctx, p.T.ngroups);
+    Cm->slot = alloc_n<int64_t>(ctx, p.T.ngroups);
+    Cm->lv[Cm->L].sq = alloc_n<double>(ctx, p.T.ngroups);
+    alloc_level_norms(Cm);
     PlanDev& d = host[r];
     d.gstart = P<int64_t>(p.T.gstart);
     d.ta = P<int32_t>(p.T.ta);
@@ -395,10 +418,10 @@ std::vector<spamm_mat> execute_plans(spamm_ctx ctx, const std::vector<spamm_plan
     d.slotB = P<int64_t>(p.slotB);
     d.termsA = P<uint8_t>(p.termsA);
     d.termsB = P<uint8_t>(p.termsB);
-    d.expA = P<int32_t>(p.expA);
-    d.expB = P<int32_t>(p.expB);
+    d.qstart = P<int64_t>(p.qstart);
+    d.qsteps = P<QuadStep>(p.qsteps);
     d.cpool = P<double>(Cm->pool);
-    d.csq = P<double>(csq[r]);
+    d.csq = P<double>(Cm->lv[Cm->L].sq);
     // work units: output leaves for the FP64 kernel, quads of output leaves for the tensor-core kernel
     const int64_t units = p.T.ngroups == 0 ? 0 : (prec == SPAMM_PREC_FP64 ? p.T.ngroups : p.T.nquads);
     ubegin[r + 1] = ubegin[r] + units;
@@ -407,28 +430,55 @@ std::vector<spamm_mat> execute_plans(spamm_ctx ctx, const std::vector<spamm_plan
   CK(cudaMemcpyAsync(P<PlanDev>(dplans), host.data(), np * sizeof(PlanDev), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(P<int64_t>(dub), ubegin.data(), (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
                      ctx->stream));
+  std::vector<NormBatchLevel> nlv;
+  BufP ntab = norm_batch_tables(ctx, outp, &nlv);
   BatchDev batch{P<PlanDev>(dplans), P<int64_t>(dub), (int)np, ubegin[np]};
-  CK(cudaEventRecord(ev.e[0], ctx->stream));
-  if (prec == SPAMM_PREC_FP64)
-    gemm_fp64_batch(ctx, bs, batch);
-  else if (prec == SPAMM_PREC_BF16_SPLIT)
-    gemm_bf16_batch(ctx, batch);
-  else
-    gemm_fp16_batch(ctx, batch);
-  CK(cudaEventRecord(ev.e[1], ctx->stream));
-  for (int64_t r = 0; r < np; ++r) {
-    const spamm_plan_s& p = *plans[r];
-    spamm_mat Cm = outs[r].get();
-    Level& leaf = Cm->lv[Cm->L];
-    leaf.count = p.T.ngroups;
-    leaf.code = p.T.gcode;
-    leaf.sq = csq[r];
-    Cm->nleaves = p.T.ngroups;
-    Cm->slot = alloc_n<int64_t>(ctx, p.T.ngroups);
-    fill_iota_i64(ctx, P<int64_t>(Cm->slot), p.T.ngroups);
-    build_tree(Cm);
+
+  auto sequence = [&](unsigned evflags) {
+    CK(cudaEventRecordWithFlags(ev.e[0], ctx->stream, evflags));
+    if (prec == SPAMM_PREC_FP64)
+      gemm_fp64_batch(ctx, bs, batch);
+    else if (prec == SPAMM_PREC_BF16_SPLIT)
+      gemm_bf16_batch(ctx, batch);
+    else
+      gemm_fp16_batch(ctx, batch);
+    CK(cudaEventRecordWithFlags(ev.e[1], ctx->stream, evflags));
+    for (int64_t r = 0; r < np; ++r) fill_iota_i64(ctx, P<int64_t>(outp[r]->slot), outp[r]->nleaves);
+    propagate_norms_batch(ctx, nlv);
+    CK(cudaEventRecordWithFlags(ev.e[2], ctx->stream, evflags));
+  };
+  if (ctx->exec_graph) {
+    // capture on the context's capture stream (the legacy stream cannot be captured), run on its stream
+    if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t run = ctx->stream;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    ctx->stream = ctx->capture_stream;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed));
+    try {
+      sequence(cudaEventRecordExternal);
+    } catch (...) {
+      cudaStreamEndCapture(ctx->stream, &g);
+      if (g) cudaGraphDestroy(g);
+      ctx->stream = run;
+      throw;
+    }
+    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+    ctx->stream = run;
+    CK(ce);
+    const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    CK(ie);
+    const cudaError_t le = cudaGraphLaunch(ge, ctx->stream);
+    if (le != cudaSuccess) cudaGraphExecDestroy(ge);
+    CK(le);
+    ++g_kernel_launches;  // the graph launch itself; its kernels were counted at capture
+    const cudaError_t se = cudaStreamSynchronize(ctx->stream);
+    cudaGraphExecDestroy(ge);
+    CK(se);
+  } else {
+    sequence(cudaEventRecordDefault);
   }
-  CK(cudaEventRecord(ev.e[2], ctx->stream));
   sync_and_check(ctx);
   *ms_gemm = elapsed_ms(ev.e[0], ev.e[1]);
   *ms_cnorm = elapsed_ms(ev.e[1], ev.e[2]);
@@ -474,6 +524,12 @@ spamm_status spamm_set_gemm_sms(spamm_ctx ctx, int nsms) {
     need(nsms >= 0 && nsms <= ctx->num_sms, "nsms must be in [0, number of SMs]");
     ctx->gemm_sm_limit = nsms;
   });
+}
+
+spamm_status spamm_set_exec_graph(spamm_ctx ctx, int enable) {
+  if (!ctx) return SPAMM_E_INVALID_ARG;
+  ctx->exec_graph = enable != 0;
+  return SPAMM_OK;
 }
 
 spamm_status spamm_execute(spamm_ctx ctx, int64_t nplans, const spamm_plan* plans, spamm_mat* C, spamm_stats* stats) {

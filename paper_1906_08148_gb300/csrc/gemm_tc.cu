@@ -11,67 +11,62 @@
 //                a' = h0 + h1 (f16), likewise b'; products h0 g0, h0 g1, h1 g0,
 //                scaled back by 2^-(eA + eB).
 //
-// Column pairs.  The two output leaves (2I, j) and (2I+1, j) of a quadtree
-// quad share every B leaf (k, j).  Their A terms are stacked in M: for term s
-// the 128-row operand is [A(2I,k)_s; A(2I+1,k)_s] (a zero tile where that leaf
-// has no kept product for this k), so one B tile serves both and the
-// accumulator holds the two output leaves in its row halves.  With
-// B = [b0^T; b1^T; b2^T] (BF16) or [g0^T; g1^T] (FP16) one k step issues
-//   BF16: a0 x [b0|b1|b2] (N=192), a1 x [b0|b1] (N=128), a2 x b0 (N=64)
-//   FP16: h0 x [g0|g1]    (N=128), h1 x g0      (N=64)
-// into a fresh TMEM accumulator, whose 64-column blocks add up to the step's
-// contribution.  Accumulators are double-buffered: while the tensor cores run
-// step t+1, the epilogue drains step t into FP32 registers with round-to-
-// nearest adds (one output row per thread, per-leaf FP16 scales applied per
-// row), which keeps the error of long k runs at the level of one leaf product.
-// The two pairs of a quad run back to back on one CTA, so their shared A
-// leaves are still in L2.
+// Quads.  The four output leaves (2I + h, 2J + c) of a quadtree node one level
+// above the leaves are computed together: at each k the A operand of term s is
+// [A(2I,k)_s; A(2I+1,k)_s] (M = 128) and the B operand of term t is
+// [B(k,2J)_t | B(k,2J+1)_t] (N = 128), so one step loads two A and two B leaves
+// for up to four leaf products.  The steps of each quad (the four kept-product
+// runs merged by k, with the leaves to load and each child's scale) are listed
+// at plan time, so the kernel reads them sequentially.  A product whose norm
+// test failed (or whose leaf is absent) is still formed by the MMA over the
+// whole tile, but its quadrant is discarded by the epilogue; an operand leaf no
+// kept product of the step needs is not loaded (its stale contents reach only
+// discarded quadrants: each output element depends on one A row and one B
+// column).  All term products of a step accumulate, smallest first, into one
+// fresh 128 x 128 TMEM accumulator; four accumulators rotate, and the epilogue
+// drains each step into FP32 registers with round-to-nearest adds (scale
+// applied per step), which keeps the error of long k runs at the level of one
+// step.
 //
-// Warp roles (one CTA per SM, persistent, quads statically interleaved in
-// Morton order so concurrently running CTAs share A rows and B columns in L2):
-//   warp 0     TMA producer: ring of NS stages (two A leaves' terms + one B
-//              leaf's terms), 1-D bulk copies of pre-swizzled tiles, mbarriers.
+// Warp roles (one CTA per SM, persistent; quads are claimed one at a time
+// from a global counter in Morton order, so the quads in flight on all SMs
+// form one narrow window whose A rows and B columns are shared in L2):
+//   warp 0     TMA producer: claims the next quad for all roles (a ring of 4
+//              in shared memory), ring of NS stages, 8 KB 1-D bulk copies of
+//              pre-swizzled term tiles, mbarriers.
 //   warp 1     allocates 512 TMEM columns and issues the MMAs of each step.
-//   warps 2-5  epilogue: TMEM lane = accumulator row, drain per step, write
-//              the FP64 output leaves and their squared norms.
-// No atomics on C: one CTA owns each output leaf; k runs in ascending order.
+//   warps 2-9  epilogue: warps 2-5 column 0, warps 6-9 column 1; TMEM lane =
+//              output row; writes the FP64 output leaves and their squared norms.
+// No atomics on C: one CTA owns each output quad; k runs in ascending order.
 // Every wait is bounded; on timeout the CTA sets the error word and leaves.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "fbits.cuh"
 #include "internal.cuh"
 #include "ptx.cuh"
 
 namespace spamm {
 
-constexpr int kTcThreads = 192;
 constexpr uint32_t kTerm = 64 * 64 * 2;  // one 64 x 64 two-byte term tile: 8 KB
 
 template <int PREC>
-struct PairCfg;
+struct FormCfg;
 template <>
-struct PairCfg<SPAMM_PREC_BF16_SPLIT> {
+struct FormCfg<SPAMM_PREC_BF16_SPLIT> {
   static constexpr int TERMS = 3;  // terms per operand
-  static constexpr int NS = 3;     // pipeline stages
-  static constexpr bool SCALED = false;
+  static constexpr int NS = 2;     // pipeline stages of 96 KB
+  static constexpr uint32_t AB = 1u;  // operand format bf16
 };
 template <>
-struct PairCfg<SPAMM_PREC_FP16_SCALED> {
+struct FormCfg<SPAMM_PREC_FP16_SCALED> {
   static constexpr int TERMS = 2;
-  static constexpr int NS = 4;
-  static constexpr bool SCALED = true;
+  static constexpr int NS = 3;     // stages of 64 KB
+  static constexpr uint32_t AB = 0u;  // f16
 };
 template <int PREC>
 __host__ __device__ constexpr uint32_t leaf_bytes() {
-  return PairCfg<PREC>::TERMS * kTerm;
-}
-template <int PREC>
-__host__ __device__ constexpr uint32_t stage_bytes() {
-  return 3 * leaf_bytes<PREC>();  // two A leaves (stacked per term) + one B leaf
-}
-template <int PREC>
-constexpr size_t pair_smem_bytes() {
-  return 1024 + (size_t)PairCfg<PREC>::NS * stage_bytes<PREC>();
+  return FormCfg<PREC>::TERMS * kTerm;
 }
 
 // Byte offset of element (row, k) in a 128-byte-swizzled K-major tile of
@@ -81,124 +76,243 @@ __device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
 }
 
 // ---------------------------------------------------------------- operand prep
-// Terms of one leaf as 16-byte swizzled chunks: chunk (row, c8) holds 8
-// consecutive k of one tile row.  role 0 (A): term s is a 64-row tile at
+// Terms of one leaf as 16-byte swizzled chunks: chunk (row, c8) holds k =
+// 8 c8 .. 8 c8 + 7 of one tile row.  role 0 (A): term s is a 64-row tile at
 // s * 8 KB, tile row = leaf row, k = leaf column.  role 1 (B): term s occupies
 // tile rows 64 s .. 64 s + 63 (row = leaf column n), k = leaf row.
-__global__ void prep_bf16_terms_kernel(const double* __restrict__ pool, const int64_t* __restrict__ slot,
-                                       int64_t nleaves, int role, uint8_t* __restrict__ out) {
-  constexpr uint32_t LEAF = leaf_bytes<SPAMM_PREC_BF16_SPLIT>();
+//
+// One CTA of 256 threads per leaf; a thread owns two chunks and loads their 16
+// elements first (A: 8 consecutive doubles of a row; B: one column, so the
+// lanes of a warp read consecutive doubles of each leaf row).  Each element is
+// rounded once to FP32 on its bits (fbits.cuh; the FP16 form's per-leaf scale
+// 2^e folded in), then split in FP32:
+//   BF16: b0 = bf16(a), b1 = bf16(a - b0), b2 = bf16(a - b0 - b1)
+//   FP16: h0 = f16(a 2^e), h1 = f16(a 2^e - h0), max|a 2^e| in [2^14, 2^15)
+// (each residual is exact in FP32).
+template <int PREC>
+__global__ void __launch_bounds__(256) prep_terms_kernel(const double* __restrict__ pool,
+                                                         const int64_t* __restrict__ slot, int64_t nleaves, int role,
+                                                         uint8_t* __restrict__ out, int32_t* __restrict__ expo) {
+  constexpr int TERMS = FormCfg<PREC>::TERMS;
+  constexpr uint32_t LEAF = leaf_bytes<PREC>();
+  __shared__ unsigned long long smax[8];
+  __shared__ int s_shift;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int64_t m = blockIdx.x; m < nleaves; m += gridDim.x) {
-    const double* src = pool + slot[m] * 4096;
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(pool + slot[m] * 4096);
+    unsigned long long v[2][8];
+    int row[2], c8[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (role == 0) {
+        row[j] = (t >> 3) + 32 * j;
+        c8[j] = t & 7;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[j][e] = __ldg(src + row[j] * 64 + 8 * c8[j] + e);
+      } else {
+        row[j] = t & 63;
+        c8[j] = (t >> 6) + 4 * j;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[j][e] = __ldg(src + (8 * c8[j] + e) * 64 + row[j]);
+      }
+    }
+    int shift = 0;
+    if constexpr (PREC == SPAMM_PREC_FP16_SCALED) {
+      // largest |a| of the leaf: |x| of doubles orders like their bits without the sign
+      unsigned long long mx = 0;
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const unsigned long long a = v[j][e] & 0x7FFFFFFFFFFFFFFFull;
+          mx = a > mx ? a : mx;
+        }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+        mx = o > mx ? o : mx;
+      }
+      if (lane == 0) smax[warp] = mx;
+      __syncthreads();
+      if (t == 0) {
+        unsigned long long g = 0;
+        for (int w = 0; w < 8; ++w) g = smax[w] > g ? smax[w] : g;
+        s_shift = fp16_leaf_shift(g);
+        expo[m] = s_shift;
+      }
+      __syncthreads();
+      shift = s_shift;
+    }
     uint8_t* dst = out + m * (int64_t)LEAF;
-    for (int ch = threadIdx.x; ch < 512; ch += blockDim.x) {
-      const int row = ch >> 3, c8 = ch & 7;
-      __align__(16) __nv_bfloat16 t[3][8];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      __align__(16) uint16_t term[TERMS][8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        const int k = 8 * c8 + e;
-        double rest = role == 0 ? src[row * 64 + k] : src[k * 64 + row];
+        float a = __uint_as_float(fbits_from_double_rn(v[j][e], shift));
 #pragma unroll
-        for (int s = 0; s < 3; ++s) {
-          t[s][e] = __double2bfloat16(rest);
-          rest -= (double)__bfloat162float(t[s][e]);
+        for (int s = 0; s < TERMS; ++s) {
+          if constexpr (PREC == SPAMM_PREC_FP16_SCALED) {
+            const __half h = __float2half_rn(a);
+            term[s][e] = __half_as_ushort(h);
+            a -= __half2float(h);
+          } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(a);
+            term[s][e] = __bfloat16_as_ushort(h);
+            a -= __bfloat162float(h);
+          }
         }
       }
 #pragma unroll
-      for (int s = 0; s < 3; ++s) {
-        const uint32_t off = role == 0 ? s * kTerm + sw128_offset(row, 8 * c8) : sw128_offset(64 * s + row, 8 * c8);
-        *reinterpret_cast<uint4*>(dst + off) = *reinterpret_cast<const uint4*>(t[s]);
+      for (int s = 0; s < TERMS; ++s) {
+        const uint32_t off = role == 0 ? s * kTerm + sw128_offset(row[j], 8 * c8[j])
+                                       : sw128_offset(64 * s + row[j], 8 * c8[j]);
+        *reinterpret_cast<uint4*>(dst + off) = *reinterpret_cast<const uint4*>(term[s]);
       }
     }
+    if constexpr (PREC == SPAMM_PREC_FP16_SCALED) __syncthreads();  // smax / s_shift are reused
   }
 }
 
-// FP16: per-leaf exponent e with max|a| 2^e in [2^14, 2^15), then two terms.
-__global__ void prep_fp16_terms_kernel(const double* __restrict__ pool, const int64_t* __restrict__ slot,
-                                       int64_t nleaves, int role, uint8_t* __restrict__ out,
-                                       int32_t* __restrict__ expo) {
-  constexpr uint32_t LEAF = leaf_bytes<SPAMM_PREC_FP16_SCALED>();
-  __shared__ double smax[8];
-  __shared__ int s_e;
-  for (int64_t m = blockIdx.x; m < nleaves; m += gridDim.x) {
-    const double* src = pool + slot[m] * 4096;
-    uint8_t* dst = out + m * (int64_t)LEAF;
-    double mx = 0.0;
-    for (int e = threadIdx.x; e < 4096; e += blockDim.x) mx = fmax(mx, fabs(src[e]));
+// ------------------------------------------------------------- quad steps
+// The four kept-product runs of a quad (child c = 2h + cj, tasks of one C leaf
+// in ascending k) merged by k.
+struct QuadMerge {
+  int64_t p[4], e[4];
+  __device__ QuadMerge(const int32_t* g, const int64_t* gstart) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, smax[w]);
-      int x = 0;
-      if (t > 0.0) frexp(t, &x);  // t = f 2^x, f in [0.5, 1)
-      int ex = t > 0.0 ? 15 - x : 0;
-      ex = ex > 120 ? 120 : (ex < -120 ? -120 : ex);
-      s_e = ex;
-      expo[m] = ex;
+    for (int c = 0; c < 4; ++c) {
+      p[c] = g[c] >= 0 ? gstart[g[c]] : 0;
+      e[c] = g[c] >= 0 ? gstart[g[c] + 1] : 0;
     }
-    __syncthreads();
-    const int e2 = s_e;
-    for (int ch = threadIdx.x; ch < 512; ch += blockDim.x) {
-      const int row = ch >> 3, c8 = ch & 7;
-      __align__(16) __half t[2][8];
+  }
+  __device__ bool more() const { return p[0] < e[0] || p[1] < e[1] || p[2] < e[2] || p[3] < e[3]; }
+  // advance past the next k; bit c of the result: child c has a kept product there, task q[c]
+  __device__ unsigned next(const int32_t* ta, const uint32_t* codeA, int64_t* q) {
+    uint32_t k[4];
+    uint32_t kmin = 0xFFFFFFFFu;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int k = 8 * c8 + e;
-        const double a = ldexp(role == 0 ? src[row * 64 + k] : src[k * 64 + row], e2);
-        t[0][e] = __double2half(a);
-        t[1][e] = __double2half(a - (double)__half2float(t[0][e]));
-      }
+    for (int c = 0; c < 4; ++c) {
+      k[c] = p[c] < e[c] ? code_col(codeA[ta[p[c]]]) : 0xFFFFFFFFu;
+      kmin = k[c] < kmin ? k[c] : kmin;
+    }
+    unsigned has = 0;
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const uint32_t off = role == 0 ? s * kTerm + sw128_offset(row, 8 * c8) : sw128_offset(64 * s + row, 8 * c8);
-        *reinterpret_cast<uint4*>(dst + off) = *reinterpret_cast<const uint4*>(t[s]);
+    for (int c = 0; c < 4; ++c) {
+      q[c] = p[c];
+      if (k[c] == kmin) {
+        has |= 1u << c;
+        ++p[c];
       }
     }
-    __syncthreads();
-  }
-}
-
-// Kept-product runs of the pair (g0 on top, g1 below) merged by k: B leaf
-// indices of one column ascend with k and are equal iff k is.
-struct PairCursor {
-  int64_t p0, e0, p1, e1;
-  __device__ void init(const int64_t* gstart, int g0, int g1) {
-    p0 = g0 >= 0 ? gstart[g0] : 0;
-    e0 = g0 >= 0 ? gstart[g0 + 1] : 0;
-    p1 = g1 >= 0 ? gstart[g1] : 0;
-    e1 = g1 >= 0 ? gstart[g1 + 1] : 0;
-  }
-  __device__ bool more() const { return p0 < e0 || p1 < e1; }
-  // advance past the next k; reports which rows have a product there
-  __device__ void next(const int32_t* tb, bool* u0, bool* u1, int32_t* kb, int64_t* q0, int64_t* q1) {
-    const int32_t k0 = p0 < e0 ? tb[p0] : INT32_MAX, k1 = p1 < e1 ? tb[p1] : INT32_MAX;
-    *kb = k0 < k1 ? k0 : k1;
-    *u0 = k0 == *kb;
-    *u1 = k1 == *kb;
-    *q0 = p0;
-    *q1 = p1;
-    p0 += *u0;
-    p1 += *u1;
+    return has;
   }
 };
 
+// One thread per quad.  Count pass (out == null): count[Q] = its steps.
+// Write pass: its steps at out[qstart[Q] ...].
+__global__ void quad_steps_kernel(int64_t nquads, const int32_t* __restrict__ quads, const int64_t* __restrict__ gstart,
+                                  const int32_t* __restrict__ ta, const int32_t* __restrict__ tb,
+                                  const uint32_t* __restrict__ codeA, const int32_t* __restrict__ expA,
+                                  const int32_t* __restrict__ expB, uint64_t* __restrict__ count,
+                                  const uint64_t* __restrict__ qstart, QuadStep* __restrict__ out) {
+  for (int64_t Q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; Q < nquads; Q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t g[4] = {quads[4 * Q], quads[4 * Q + 1], quads[4 * Q + 2], quads[4 * Q + 3]};
+    QuadMerge m(g, gstart);
+    QuadStep* o = out ? out + qstart[Q] : nullptr;
+    int64_t s = 0;
+    while (m.more()) {
+      int64_t q[4];
+      const unsigned has = m.next(ta, codeA, q);
+      if (o) {
+        QuadStep st;
+        // children 0/1 share the A leaf of row half 0, 2/3 that of half 1; 0/2 and 1/3 share B leaves
+        st.a[0] = (has & 1u) ? ta[q[0]] : ((has & 2u) ? ta[q[1]] : -1);
+        st.a[1] = (has & 4u) ? ta[q[2]] : ((has & 8u) ? ta[q[3]] : -1);
+        st.b[0] = (has & 1u) ? tb[q[0]] : ((has & 4u) ? tb[q[2]] : -1);
+        st.b[1] = (has & 2u) ? tb[q[1]] : ((has & 8u) ? tb[q[3]] : -1);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float sc = 0.f;
+          if (has & (1u << c)) {
+            sc = 1.f;
+            if (expA) {
+              // 2^-(eA + eB) as a product of two normal powers of two (|e| <= 120)
+              const int ea = expA[ta[q[c]]], eb = expB[tb[q[c]]];
+              sc = __int_as_float((127 - ea) << 23) * __int_as_float((127 - eb) << 23);
+            }
+          }
+          st.scale[c] = sc;
+        }
+        o[s] = st;
+      }
+      ++s;
+    }
+    if (count) count[Q] = (uint64_t)s;
+  }
+}
+
+int64_t build_quad_steps(spamm_ctx ctx, const TaskList& T, const uint32_t* codeA, const int32_t* expA,
+                         const int32_t* expB, BufP* qstart, BufP* qsteps) {
+  const int64_t nq = T.ngroups > 0 ? T.nquads : 0;
+  *qstart = alloc_n<uint64_t>(ctx, nq + 1);
+  *qsteps = nullptr;
+  if (nq == 0) {
+    CK(cudaMemsetAsync(P<uint64_t>(*qstart), 0, sizeof(uint64_t), ctx->stream));
+    return 0;
+  }
+  BufP cnt = alloc_n<uint64_t>(ctx, nq);
+  const int64_t want = (nq + 255) / 256, cap = (int64_t)ctx->num_sms * 16;
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  quad_steps_kernel<<<grid, 256, 0, ctx->stream>>>(nq, P<int32_t>(T.quads), P<int64_t>(T.gstart), P<int32_t>(T.ta),
+                                                   P<int32_t>(T.tb), codeA, expA, expB, P<uint64_t>(cnt), nullptr,
+                                                   nullptr);
+  CK_LAUNCH("quad_steps_kernel(count)");
+  scan_exclusive_u64(ctx, P<uint64_t>(cnt), P<uint64_t>(*qstart), nq, P<uint64_t>(*qstart) + nq);
+  const int64_t total = (int64_t)read_scalar(ctx, P<uint64_t>(*qstart) + nq);
+  *qsteps = alloc_n<QuadStep>(ctx, total);
+  quad_steps_kernel<<<grid, 256, 0, ctx->stream>>>(nq, P<int32_t>(T.quads), P<int64_t>(T.gstart), P<int32_t>(T.ta),
+                                                   P<int32_t>(T.tb), codeA, expA, expB, nullptr,
+                                                   P<uint64_t>(*qstart), P<QuadStep>(*qsteps));
+  CK_LAUNCH("quad_steps_kernel(write)");
+  return total;
+}
+
 // ------------------------------------------------------------------- GEMM
+constexpr int kQuadThreads = 320;
+constexpr int kQuadBufs = 4;  // rotating TMEM accumulators of 128 FP32 columns
+constexpr int kQuadQ = 4;     // ring of claimed quads shared by the three roles
 template <int PREC>
-__global__ void __launch_bounds__(kTcThreads, 1)
-    gemm_pair_kernel(BatchDev batch, const uint8_t* __restrict__ zero_term, int* __restrict__ err) {
-  using Cfg = PairCfg<PREC>;
-  constexpr int NS = Cfg::NS, TERMS = Cfg::TERMS;
-  constexpr uint32_t LEAF = leaf_bytes<PREC>(), STAGE = stage_bytes<PREC>();
-  constexpr uint32_t AB = PREC == SPAMM_PREC_BF16_SPLIT ? 1u : 0u;  // operand format: bf16 or f16
+__host__ __device__ constexpr uint32_t quad_stage_bytes() {
+  return 4 * leaf_bytes<PREC>();  // two A and two B leaves, every term
+}
+template <int PREC>
+constexpr size_t quad_smem_bytes() {
+  return 1024 + (size_t)FormCfg<PREC>::NS * quad_stage_bytes<PREC>();
+}
+
+double quad_step_flops(spamm_prec prec) {
+  const int terms = prec == SPAMM_PREC_BF16_SPLIT ? 3 : 2;
+  return (double)(terms * (terms + 1) / 2) * 2.0 * 128.0 * 128.0 * 64.0;
+}
+
+// Stage layout: A region, term s at s * 16 KB = [A(2I,k)_s; A(2I+1,k)_s]
+// (128 rows of 64 k); B region at TERMS * 16 KB, term t at t * 16 KB =
+// [B(k,2J)_t; B(k,2J+1)_t] (128 rows n of 64 k).  Both are 128-row K-major
+// SW128 operands.
+template <int PREC>
+__global__ void __launch_bounds__(kQuadThreads, 1)
+    gemm_quad_kernel(BatchDev batch, unsigned long long* __restrict__ work, int* __restrict__ err) {
+  using Cfg = FormCfg<PREC>;
+  constexpr int NS = Cfg::NS, TERMS = Cfg::TERMS, NB = kQuadBufs;
+  constexpr uint32_t LEAF = leaf_bytes<PREC>(), STAGE = quad_stage_bytes<PREC>(), BREG = 2 * LEAF;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full[NS], empty[NS], tfull[2], tempty[2];
+  __shared__ __align__(8) uint64_t full[NS], empty[NS], tfull[NB], tempty[NB], qfull[kQuadQ], qempty[kQuadQ];
+  __shared__ int64_t qid[kQuadQ], epi_un;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, epi_stop;
-  __shared__ double red[4];
+  __shared__ double red[2][4];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -206,9 +320,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NB; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
+      mbar_init(&tempty[b], 256);
+    }
+    for (int q = 0; q < kQuadQ; ++q) {
+      mbar_init(&qfull[q], 1);
+      mbar_init(&qempty[q], 2);  // the MMA issuer and the epilogue's first thread
     }
     fence_mbar_init();
     abort_flag = 0;
@@ -224,191 +342,199 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   volatile int* abortp = &abort_flag;
 
   if (warp == 0) {
-    // ---------------- TMA producer
+    // ---------------- TMA producer; claims the quads (Morton order, first come first served) for all roles
     if (lane == 0) {
       int64_t t = 0;
       bool stop = false;
-      for (int64_t un = blockIdx.x; un < batch.nunits && !stop; un += gridDim.x) {
+      for (int64_t c = 0; !stop; ++c) {
+        const int qs = (int)(c % kQuadQ);
+        if (c >= kQuadQ && !mbar_wait_or_abort(&qempty[qs], (uint32_t)(((c / kQuadQ) - 1) & 1), abortp)) {
+          atomicOr(err, DEV_ERR_TIMEOUT);
+          *abortp = 1;
+          break;
+        }
+        const int64_t claimed = (int64_t)atomicAdd(work, 1ull);
+        const int64_t un = claimed < batch.nunits ? claimed : -1;
+        qid[qs] = un;
+        mbar_arrive(&qfull[qs]);
+        if (un < 0) break;
         const int r = plan_of(batch.ubegin, batch.nplans, un);
         const PlanDev& pl = batch.plans[r];
         const int64_t Q = un - batch.ubegin[r];
-        for (int pr = 0; pr < 2 && !stop; ++pr) {
-          const int g0 = pl.quads[4 * Q + pr], g1 = pl.quads[4 * Q + 2 + pr];
-          if (g0 < 0 && g1 < 0) continue;
-          PairCursor cur;
-          cur.init(pl.gstart, g0, g1);
-          while (cur.more()) {
-            bool u0, u1;
-            int32_t kb;
-            int64_t q0, q1;
-            cur.next(pl.tb, &u0, &u1, &kb, &q0, &q1);
-            const int s = (int)(t % NS);
-            if (t >= NS && !mbar_wait_or_abort(&empty[s], (uint32_t)(((t / NS) - 1) & 1), abortp)) {
-              atomicOr(err, DEV_ERR_TIMEOUT);
-              *abortp = 1;
-              stop = true;
-              break;
-            }
-            uint8_t* st = smem + s * STAGE;
-            const uint8_t* a0 = u0 ? pl.termsA + (int64_t)pl.ta[q0] * LEAF : nullptr;
-            const uint8_t* a1 = u1 ? pl.termsA + (int64_t)pl.ta[q1] * LEAF : nullptr;
-            mbar_arrive_expect_tx(&full[s], STAGE);
-#pragma unroll
-            for (int term = 0; term < TERMS; ++term) {
-              bulk_g2s(st + term * 2 * kTerm, a0 ? a0 + term * kTerm : zero_term, kTerm, &full[s]);
-              bulk_g2s(st + term * 2 * kTerm + kTerm, a1 ? a1 + term * kTerm : zero_term, kTerm, &full[s]);
-            }
-            bulk_g2s(st + 2 * LEAF, pl.termsB + (int64_t)kb * LEAF, LEAF, &full[s]);
-            ++t;
+        const int64_t j1 = pl.qstart[Q + 1];
+        int64_t j = pl.qstart[Q];
+        const int4* rec = reinterpret_cast<const int4*>(pl.qsteps);  // word 2j: a0, a1, b0, b1 of step j
+        int4 nx = j < j1 ? __ldg(rec + 2 * j) : make_int4(-1, -1, -1, -1);
+        for (; j < j1; ++j) {
+          const int4 ab = nx;
+          if (j + 1 < j1) nx = __ldg(rec + 2 * (j + 1));  // next step's leaves, in flight during the wait
+          const int s = (int)(t % NS);
+          if (t >= NS && !mbar_wait_or_abort(&empty[s], (uint32_t)(((t / NS) - 1) & 1), abortp)) {
+            atomicOr(err, DEV_ERR_TIMEOUT);
+            *abortp = 1;
+            stop = true;
+            break;
           }
+          uint8_t* st = smem + s * STAGE;
+          const uint32_t nload = (uint32_t)((ab.x >= 0) + (ab.y >= 0) + (ab.z >= 0) + (ab.w >= 0));
+          mbar_arrive_expect_tx(&full[s], nload * LEAF);
+#pragma unroll
+          for (int term = 0; term < TERMS; ++term) {
+            uint8_t* sa = st + term * 2 * kTerm;
+            uint8_t* sb = st + BREG + term * 2 * kTerm;
+            if (ab.x >= 0) bulk_g2s(sa, pl.termsA + (int64_t)ab.x * LEAF + term * kTerm, kTerm, &full[s]);
+            if (ab.y >= 0) bulk_g2s(sa + kTerm, pl.termsA + (int64_t)ab.y * LEAF + term * kTerm, kTerm, &full[s]);
+            if (ab.z >= 0) bulk_g2s(sb, pl.termsB + (int64_t)ab.z * LEAF + term * kTerm, kTerm, &full[s]);
+            if (ab.w >= 0) bulk_g2s(sb + kTerm, pl.termsB + (int64_t)ab.w * LEAF + term * kTerm, kTerm, &full[s]);
+          }
+          ++t;
         }
       }
       // leave no bulk copy in flight: the last fill of every stage has landed
       for (int64_t k = (t > NS ? t - NS : 0); k < t; ++k) mbar_wait_bounded(&full[k % NS], (uint32_t)((k / NS) & 1));
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer: one k step into accumulator t & 1
+    // ---------------- MMA issuer: every term product of a step into accumulator t % NB
     if (lane == 0) {
+      constexpr uint32_t idesc = umma_idesc_f16(Cfg::AB, 128, 128);
       int64_t t = 0;
       bool stop = false;
-      for (int64_t un = blockIdx.x; un < batch.nunits && !stop; un += gridDim.x) {
+      for (int64_t c = 0; !stop; ++c) {
+        const int qs = (int)(c % kQuadQ);
+        if (!mbar_wait_or_abort(&qfull[qs], (uint32_t)((c / kQuadQ) & 1), abortp)) {
+          atomicOr(err, DEV_ERR_TIMEOUT);
+          *abortp = 1;
+          break;
+        }
+        const int64_t un = qid[qs];
+        mbar_arrive(&qempty[qs]);
+        if (un < 0) break;
         const int r = plan_of(batch.ubegin, batch.nplans, un);
         const PlanDev& pl = batch.plans[r];
         const int64_t Q = un - batch.ubegin[r];
-        for (int pr = 0; pr < 2 && !stop; ++pr) {
-          const int g0 = pl.quads[4 * Q + pr], g1 = pl.quads[4 * Q + 2 + pr];
-          if (g0 < 0 && g1 < 0) continue;
-          PairCursor cur;
-          cur.init(pl.gstart, g0, g1);
-          while (cur.more()) {
-            bool u0, u1;
-            int32_t kb;
-            int64_t q0, q1;
-            cur.next(pl.tb, &u0, &u1, &kb, &q0, &q1);
-            const int s = (int)(t % NS);
-            const int b = (int)(t & 1);
-            if (!mbar_wait_or_abort(&full[s], (uint32_t)((t / NS) & 1), abortp) ||
-                (t >= 2 && !mbar_wait_or_abort(&tempty[b], (uint32_t)(((t >> 1) - 1) & 1), abortp))) {
-              atomicOr(err, DEV_ERR_TIMEOUT);
-              *abortp = 1;
-              stop = true;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t d = tbase + (uint32_t)b * 256u;
-            const uint32_t a_s = smem_u32(smem + s * STAGE), b_s = a_s + 2 * LEAF;
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              const uint64_t bd = sw128_kmajor_desc(b_s + 32 * ks);
-              // term i of A meets terms 0 .. TERMS-1-i of B: N = 64 (TERMS - i)
-#pragma unroll
-              for (int i = 0; i < TERMS; ++i)
-                umma_f16(d, sw128_kmajor_desc(a_s + i * 2 * kTerm + 32 * ks), bd,
-                         umma_idesc_f16(AB, 128, 64 * (TERMS - i)), (ks == 0 && i == 0) ? 0u : 1u);
-            }
-            umma_commit(&empty[s]);
-            umma_commit(&tfull[b]);
-            ++t;
-          }
-        }
-      }
-      // leave no MMA in flight: the last accumulator has been written
-      if (t > 0) mbar_wait_bounded(&tfull[(t - 1) & 1], (uint32_t)(((t - 1) >> 1) & 1));
-    }
-  } else {
-    // ---------------- epilogue: warps 2..5; TMEM lane = accumulator row
-    const int quarter = warp & 3;
-    const int lrow = 32 * quarter + lane;
-    const int half = lrow >> 6, row = lrow & 63;
-    const int te = threadIdx.x - 64;
-    int64_t t = 0;
-    float acc[64];
-    for (int64_t un = blockIdx.x; un < batch.nunits; un += gridDim.x) {
-      const int r = plan_of(batch.ubegin, batch.nplans, un);
-      const PlanDev& pl = batch.plans[r];
-      const int64_t Q = un - batch.ubegin[r];
-      bool stop = false;
-      for (int pr = 0; pr < 2; ++pr) {
-        const int g0 = pl.quads[4 * Q + pr], g1 = pl.quads[4 * Q + 2 + pr];
-        if (g0 < 0 && g1 < 0) continue;
-        const int g = half ? g1 : g0;
-#pragma unroll
-        for (int c = 0; c < 64; ++c) acc[c] = 0.f;
-        PairCursor cur;
-        cur.init(pl.gstart, g0, g1);
-        while (cur.more()) {
-          bool u0, u1;
-          int32_t kb;
-          int64_t q0, q1;
-          cur.next(pl.tb, &u0, &u1, &kb, &q0, &q1);
-          const int b = (int)(t & 1);
-          bool ok = true;
-          if (lane == 0) ok = mbar_wait_or_abort(&tfull[b], (uint32_t)((t >> 1) & 1), abortp);
-          ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-          ++t;
-          if (!ok) {
-            // the epilogue still runs the barrier sequence below, then stops together
+        const int64_t nstep = pl.qstart[Q + 1] - pl.qstart[Q];
+        for (int64_t j = 0; j < nstep; ++j) {
+          const int s = (int)(t % NS);
+          const int b = (int)(t % NB);
+          if (!mbar_wait_or_abort(&full[s], (uint32_t)((t / NS) & 1), abortp) ||
+              (t >= NB && !mbar_wait_or_abort(&tempty[b], (uint32_t)(((t / NB) - 1) & 1), abortp))) {
             atomicOr(err, DEV_ERR_TIMEOUT);
             *abortp = 1;
+            stop = true;
             break;
           }
           tc_fence_after();
-          float scale = 1.f;
-          if constexpr (Cfg::SCALED) {
-            const bool mine = half ? u1 : u0;
-            if (mine) {
-              const int ea = pl.expA[pl.ta[half ? q1 : q0]], eb = pl.expB[kb];
-              // 2^-(ea + eb) as a product of two normal powers of two
-              scale = __int_as_float((127 - ea) << 23) * __int_as_float((127 - eb) << 23);
+          const uint32_t d = tbase + (uint32_t)b * 128u;
+          const uint32_t a_s = smem_u32(smem + s * STAGE), b_s = a_s + BREG;
+          uint32_t accumulate = 0u;
+          // term products (i, sum - i), smallest term-index sum first
+#pragma unroll
+          for (int sum = TERMS - 1; sum >= 0; --sum) {
+#pragma unroll
+            for (int i = sum; i >= 0; --i) {
+#pragma unroll
+              for (int ks = 0; ks < 4; ++ks) {
+                umma_f16(d, sw128_kmajor_desc(a_s + i * 2 * kTerm + 32 * ks),
+                         sw128_kmajor_desc(b_s + (sum - i) * 2 * kTerm + 32 * ks), idesc, accumulate);
+                accumulate = 1u;
+              }
             }
           }
-          const uint32_t tl = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)b * 256u;
-#pragma unroll
-          for (int c0 = 0; c0 < 64; c0 += 32) {
-            float v[32], w[32];
-            tmem_ld32(tl + 64 * (TERMS - 1) + c0, v);
-#pragma unroll
-            for (int blk = TERMS - 2; blk >= 0; --blk) {
-              tmem_ld32(tl + 64 * blk + c0, w);
-#pragma unroll
-              for (int i = 0; i < 32; ++i) v[i] += w[i];
-            }
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              if constexpr (Cfg::SCALED)
-                acc[c0 + i] = fmaf(v[i], scale, acc[c0 + i]);
-              else
-                acc[c0 + i] += v[i];
-            }
-          }
-          tc_fence_before();
-          mbar_arrive(&tempty[b]);
+          umma_commit(&empty[s]);
+          umma_commit(&tfull[b]);
+          ++t;
         }
-        // output row `row` of leaf g: FP64, and its squared norm
-        double s2 = 0.0;
-        if (g >= 0) {
-          double2* out = reinterpret_cast<double2*>(pl.cpool + (int64_t)g * 4096 + row * 64);
-#pragma unroll
-          for (int c = 0; c < 64; c += 2) {
-            const double x = (double)acc[c], y = (double)acc[c + 1];
-            out[c >> 1] = make_double2(x, y);
-            s2 = __fma_rn(x, x, s2);
-            s2 = __fma_rn(y, y, s2);
-          }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-        if (lane == 0) red[quarter] = s2;
-        if (te == 0) epi_stop = *abortp;
-        named_barrier(1, 128);
-        if (te == 0) {
-          if (g0 >= 0) pl.csq[g0] = red[0] + red[1];
-          if (g1 >= 0) pl.csq[g1] = red[2] + red[3];
-        }
-        stop = epi_stop != 0;
-        named_barrier(1, 128);
-        if (stop) break;
       }
+      // leave no MMA in flight: the last accumulator has been written
+      if (t > 0) mbar_wait_bounded(&tfull[(t - 1) % NB], (uint32_t)(((t - 1) / NB) & 1));
+    }
+  } else {
+    // ---------------- epilogue: warps 2..9; column c = (warp - 2) / 4; TMEM lane = output row
+    const int col = (warp - 2) >> 2;
+    const int quarter = warp & 3;
+    const int lrow = 32 * quarter + lane;
+    const int half = lrow >> 6, row = lrow & 63;
+    const int child = 2 * half + col;  // warp-uniform
+    const int te = threadIdx.x - 64;   // 0..255
+    int64_t t = 0;
+    float acc[64];
+    for (int64_t c = 0;; ++c) {
+      // one thread takes the next claimed quad for all 256 (-2: the wait gave up)
+      if (te == 0) {
+        const int qs = (int)(c % kQuadQ);
+        if (mbar_wait_or_abort(&qfull[qs], (uint32_t)((c / kQuadQ) & 1), abortp)) {
+          epi_un = qid[qs];
+          mbar_arrive(&qempty[qs]);
+        } else {
+          epi_un = -2;
+        }
+      }
+      named_barrier(2, 256);
+      const int64_t un = epi_un;  // rewritten only after the two barriers that end this quad
+      if (un < 0) {
+        if (un == -2 && te == 0) {
+          atomicOr(err, DEV_ERR_TIMEOUT);
+          *abortp = 1;
+        }
+        break;
+      }
+      const int r = plan_of(batch.ubegin, batch.nplans, un);
+      const PlanDev& pl = batch.plans[r];
+      const int64_t Q = un - batch.ubegin[r];
+      const int32_t g[4] = {pl.quads[4 * Q], pl.quads[4 * Q + 1], pl.quads[4 * Q + 2], pl.quads[4 * Q + 3]};
+#pragma unroll
+      for (int c = 0; c < 64; ++c) acc[c] = 0.f;
+      const int64_t j1 = pl.qstart[Q + 1];
+      int64_t j = pl.qstart[Q];
+      float sc_next = j < j1 ? __ldg(&pl.qsteps[j].scale[child]) : 0.f;
+      for (; j < j1; ++j) {
+        const float sc = sc_next;
+        if (j + 1 < j1) sc_next = __ldg(&pl.qsteps[j + 1].scale[child]);
+        const int b = (int)(t % NB);
+        bool ok = true;
+        if (lane == 0) ok = mbar_wait_or_abort(&tfull[b], (uint32_t)((t / NB) & 1), abortp);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        ++t;
+        if (!ok) {
+          // the epilogue still runs the barrier sequence below, then stops together
+          atomicOr(err, DEV_ERR_TIMEOUT);
+          *abortp = 1;
+          break;
+        }
+        tc_fence_after();
+        if (sc != 0.f) {  // this warp's child has a kept product at this k
+          float v[64];
+          tmem_ld64(tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)b * 128u + 64u * (uint32_t)col, v);
+#pragma unroll
+          for (int i = 0; i < 64; ++i) acc[i] = fmaf(v[i], sc, acc[i]);
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[b]);
+      }
+      // output row `row` of leaf g[child]: FP64, and its squared norm
+      const int gl = g[child];
+      double s2 = 0.0;
+      if (gl >= 0) {
+        double2* out = reinterpret_cast<double2*>(pl.cpool + (int64_t)gl * 4096 + row * 64);
+#pragma unroll
+        for (int c = 0; c < 64; c += 2) {
+          const double x = (double)acc[c], y = (double)acc[c + 1];
+          out[c >> 1] = make_double2(x, y);
+          s2 = __fma_rn(x, x, s2);
+          s2 = __fma_rn(y, y, s2);
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+      if (lane == 0) red[col][quarter] = s2;
+      if (te == 0) epi_stop = *abortp;
+      named_barrier(1, 256);
+      if (te < 4) {
+        const int cc = te & 1, hh = te >> 1;  // child 2 hh + cc: its rows are quarters 2 hh, 2 hh + 1
+        if (g[2 * hh + cc] >= 0) pl.csq[g[2 * hh + cc]] = red[cc][2 * hh] + red[cc][2 * hh + 1];
+      }
+      const bool stop = epi_stop != 0;
+      named_barrier(1, 256);
       if (stop) break;
     }
   }
@@ -427,46 +553,41 @@ static unsigned gemm_grid(spamm_ctx ctx, int64_t nunits) {
   return (unsigned)(grid < 1 ? 1 : grid);
 }
 
-const uint8_t* zero_term(spamm_ctx ctx) {
-  if (!ctx->d_zero) {
-    CK(cudaMalloc(&ctx->d_zero, kTerm));
-    CK(cudaMemset(ctx->d_zero, 0, kTerm));
-  }
-  return static_cast<const uint8_t*>(ctx->d_zero);
-}
-
 void prep_terms(spamm_mat M, spamm_prec prec, int role, BufP* terms, BufP* expo, spamm_ctx on) {
   spamm_ctx ctx = on ? on : M->ctx;
   if (M->bs != 64) fail(SPAMM_E_UNSUPPORTED, "tensor-core precision forms are built for bs = 64");
-  const unsigned pg = (unsigned)(ctx->num_sms * 8);
+  const int64_t want = M->nleaves, cap = (int64_t)ctx->num_sms * 8;
+  const unsigned grid = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
   if (prec == SPAMM_PREC_BF16_SPLIT) {
     *terms = alloc_n<uint8_t>(ctx, M->nleaves * (int64_t)leaf_bytes<SPAMM_PREC_BF16_SPLIT>());
     if (M->nleaves > 0) {
-      prep_bf16_terms_kernel<<<pg, 256, 0, ctx->stream>>>(P<double>(M->pool), P<int64_t>(M->slot), M->nleaves, role,
-                                                          P<uint8_t>(*terms));
-      CK_LAUNCH("prep_bf16_terms_kernel");
+      prep_terms_kernel<SPAMM_PREC_BF16_SPLIT><<<grid, 256, 0, ctx->stream>>>(
+          P<double>(M->pool), P<int64_t>(M->slot), M->nleaves, role, P<uint8_t>(*terms), nullptr);
+      CK_LAUNCH("prep_terms_kernel<bf16>");
     }
   } else {
     *terms = alloc_n<uint8_t>(ctx, M->nleaves * (int64_t)leaf_bytes<SPAMM_PREC_FP16_SCALED>());
     *expo = alloc_n<int32_t>(ctx, M->nleaves);
     if (M->nleaves > 0) {
-      prep_fp16_terms_kernel<<<pg, 256, 0, ctx->stream>>>(P<double>(M->pool), P<int64_t>(M->slot), M->nleaves, role,
-                                                          P<uint8_t>(*terms), P<int32_t>(*expo));
-      CK_LAUNCH("prep_fp16_terms_kernel");
+      prep_terms_kernel<SPAMM_PREC_FP16_SCALED><<<grid, 256, 0, ctx->stream>>>(
+          P<double>(M->pool), P<int64_t>(M->slot), M->nleaves, role, P<uint8_t>(*terms), P<int32_t>(*expo));
+      CK_LAUNCH("prep_terms_kernel<fp16>");
     }
   }
 }
 
 template <int PREC>
-static void launch_pairs(spamm_ctx ctx, const BatchDev& b) {
+static void launch_quads(spamm_ctx ctx, const BatchDev& b) {
   if (b.nunits == 0) return;
-  const size_t smem = pair_smem_bytes<PREC>();
-  CK(cudaFuncSetAttribute(gemm_pair_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  gemm_pair_kernel<PREC><<<gemm_grid(ctx, b.nunits), kTcThreads, smem, ctx->stream>>>(b, zero_term(ctx), ctx->d_err);
-  CK_LAUNCH("gemm_pair_kernel");
+  const size_t smem = quad_smem_bytes<PREC>();
+  CK(cudaFuncSetAttribute(gemm_quad_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  unsigned long long* work = ctx->d_scratch + 9;  // quad claim counter
+  CK(cudaMemsetAsync(work, 0, sizeof(unsigned long long), ctx->stream));
+  gemm_quad_kernel<PREC><<<gemm_grid(ctx, b.nunits), kQuadThreads, smem, ctx->stream>>>(b, work, ctx->d_err);
+  CK_LAUNCH("gemm_quad_kernel");
 }
 
-void gemm_bf16_batch(spamm_ctx ctx, const BatchDev& b) { launch_pairs<SPAMM_PREC_BF16_SPLIT>(ctx, b); }
-void gemm_fp16_batch(spamm_ctx ctx, const BatchDev& b) { launch_pairs<SPAMM_PREC_FP16_SCALED>(ctx, b); }
+void gemm_bf16_batch(spamm_ctx ctx, const BatchDev& b) { launch_quads<SPAMM_PREC_BF16_SPLIT>(ctx, b); }
+void gemm_fp16_batch(spamm_ctx ctx, const BatchDev& b) { launch_quads<SPAMM_PREC_FP16_SCALED>(ctx, b); }
 
 }  // namespace spamm

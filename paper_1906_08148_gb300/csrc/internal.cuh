@@ -108,9 +108,10 @@ struct spamm_ctx_s {
   int* d_err = nullptr;                      // device error word
   unsigned long long* d_scratch = nullptr;   // 64 counters (statistics, work queues)
   void* h_pinned = nullptr;                  // 4 KB pinned staging for scalar read-backs
-  void* d_zero = nullptr;                    // 8 KB of zeros (tensor-form padding operand)
   int num_sms = 0;
   int gemm_sm_limit = 0;                     // 0: leaf GEMM may use every SM
+  int exec_graph = 0;                        // run the execute phase as a captured CUDA graph
+  cudaStream_t capture_stream = nullptr;     // created on first graph capture
   int live_handles = 0;
 };
 
@@ -129,6 +130,23 @@ namespace spamm {
 // ---- quadtree store (store.cu) ----
 spamm_mat new_mat(spamm_ctx ctx, int64_t n, int bs);
 void build_tree(spamm_mat m);  // levels L-1..0 from m->lv[L]
+// build_tree in parts: the structure (codes, child links; synchronises per
+// level for the counts), then norm buffers, then the norms (no host sync, so
+// it can be captured in a CUDA graph).  The addition order is build_tree's.
+void build_skeleton(spamm_mat m);
+void alloc_level_norms(spamm_mat m);
+void propagate_norms(spamm_mat m);
+// propagate_norms of several matrices at once: one launch per height above the
+// leaves.  norm_batch_tables uploads the per-height segment tables (norm
+// buffers must already exist); propagate_norms_batch launches (no host sync).
+struct NormBatchLevel {
+  const void* seg = nullptr;       // device segment table of this height
+  const int64_t* begin = nullptr;  // device: first parent of each segment
+  int first = 0, nseg = 0;
+  int64_t total = 0;
+};
+BufP norm_batch_tables(spamm_ctx ctx, const std::vector<spamm_mat>& ms, std::vector<NormBatchLevel>* levels);
+void propagate_norms_batch(spamm_ctx ctx, const std::vector<NormBatchLevel>& levels);
 // Leaf set from candidate leaves: keep[q] selects rows of (code, sq, slot) already sorted by code.
 void set_leaves_compacted(spamm_mat m, int64_t ncand, const uint32_t* code, const double* sq, const int64_t* slot,
                           const uint8_t* keep);
@@ -154,10 +172,19 @@ struct TaskList {
 TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm_ctx on = nullptr);
 
 // ---- batched leaf products (gemm_fp64.cu, gemm_tc.cu) ----
+// One k step of a quad of output leaves (2I + h, 2J + c) in the tensor-core
+// kernel: the four kept-product runs of the quad merged by k.
+struct __align__(16) QuadStep {
+  int32_t a[2];    // A leaf (2I + h, k), -1 where no kept product of row half h uses k
+  int32_t b[2];    // B leaf (k, 2J + c), -1 where no kept product of column c uses k
+  float scale[4];  // child 2h + c: its operand scale factor if the product (2I+h, k, 2J+c) is kept, else 0
+};
+static_assert(sizeof(QuadStep) == 32, "QuadStep is two 16-byte words");
+
 // Device view of one planned multiplication.  A batch is an array of these;
-// its work units (output leaves, or quads of output leaves for the BF16
-// kernel) are numbered consecutively across plans: plan r owns units
-// [ubegin[r], ubegin[r+1]).  Output leaf g of plan r is the sum over its
+// its work units (output leaves, or quads of output leaves for the
+// tensor-core kernel) are numbered consecutively across plans: plan r owns
+// units [ubegin[r], ubegin[r+1]).  Output leaf g of plan r is the sum over its
 // tasks of A[ta] B[tb], written to cpool + g*bs*bs with its squared norm in csq[g].
 struct PlanDev {
   const int64_t* gstart;
@@ -170,8 +197,8 @@ struct PlanDev {
   const int64_t* slotB;
   const uint8_t* termsA;  // tensor forms: operand terms per leaf
   const uint8_t* termsB;
-  const int32_t* expA;    // FP16 form: per-leaf scale exponents
-  const int32_t* expB;
+  const int64_t* qstart;    // tensor forms: steps of quad Q are qsteps[qstart[Q] .. qstart[Q+1])
+  const QuadStep* qsteps;
   double* cpool;
   double* csq;
 };
@@ -198,5 +225,11 @@ void gemm_fp16_batch(spamm_ctx ctx, const BatchDev& b);
 void gemm_bf16_batch(spamm_ctx ctx, const BatchDev& b);
 // Operand terms of a leaf set for a tensor form (role 0: used as A, 1: as B).
 void prep_terms(spamm_mat M, spamm_prec prec, int role, BufP* terms, BufP* expo, spamm_ctx on = nullptr);
-const uint8_t* zero_term(spamm_ctx ctx);  // 8 KB of zeros, allocated once per context
+// Step list of every quad of T for the tensor-core kernel; returns the step count.
+// codeA: Morton codes of A's leaves (the k of a task is the column of its A
+// leaf); expA/expB: FP16 scale exponents (null: no scaling).
+int64_t build_quad_steps(spamm_ctx ctx, const TaskList& T, const uint32_t* codeA, const int32_t* expA,
+                         const int32_t* expB, BufP* qstart, BufP* qsteps);
+// Tensor-core flops one quad step executes (every term product over the full 128 x 128 tile).
+double quad_step_flops(spamm_prec prec);
 }  // namespace spamm

@@ -171,7 +171,7 @@ __global__ void parent_sum_kernel(int64_t np, const int4* __restrict__ child, co
   }
 }
 
-void build_tree(spamm_mat m) {
+void build_skeleton(spamm_mat m) {
   spamm_ctx ctx = m->ctx;
   for (int t = m->L; t >= 1; --t) {
     Level& ch = m->lv[t];
@@ -192,16 +192,111 @@ void build_tree(spamm_mat m) {
     const int64_t np = (int64_t)read_scalar<uint64_t>(ctx, P<uint64_t>(tot));
     pa.count = np;
     pa.code = alloc_n<uint32_t>(ctx, np);
-    pa.sq = alloc_n<double>(ctx, np);
+    pa.sq.reset();
     pa.child = alloc_n<int4>(ctx, np);
     CK(cudaMemsetAsync(P<int4>(pa.child), 0xFF, np * sizeof(int4), ctx->stream));
     parent_link_kernel<<<grid_for(ctx, n, kThreads), kThreads, 0, ctx->stream>>>(
         P<uint32_t>(ch.code), n, P<uint64_t>(flags), P<uint64_t>(excl), P<uint32_t>(pa.code), P<int4>(pa.child));
     CK_LAUNCH("parent_link_kernel");
-    parent_sum_kernel<<<grid_for(ctx, np, kThreads), kThreads, 0, ctx->stream>>>(np, P<int4>(pa.child),
-                                                                                P<double>(ch.sq), P<double>(pa.sq));
+  }
+}
+
+void alloc_level_norms(spamm_mat m) {
+  for (int t = 0; t < m->L; ++t)
+    if (m->lv[t].count > 0) m->lv[t].sq = alloc_n<double>(m->ctx, m->lv[t].count);
+}
+
+void propagate_norms(spamm_mat m) {
+  spamm_ctx ctx = m->ctx;
+  for (int t = m->L; t >= 1; --t) {
+    const Level& ch = m->lv[t];
+    const Level& pa = m->lv[t - 1];
+    if (pa.count == 0) continue;
+    parent_sum_kernel<<<grid_for(ctx, pa.count, kThreads), kThreads, 0, ctx->stream>>>(
+        pa.count, P<int4>(pa.child), P<double>(ch.sq), P<double>(pa.sq));
     CK_LAUNCH("parent_sum_kernel");
   }
+}
+
+// Parent norms of several matrices, one launch per height above the leaves:
+// segment q of height h is one matrix's level L - h.
+struct NormSeg {
+  const int4* child;
+  const double* csq;
+  double* psq;
+};
+__global__ void parent_sum_batch_kernel(const NormSeg* __restrict__ seg, const int64_t* __restrict__ begin, int nseg,
+                                        int64_t total) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total; u += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (begin[mid] <= u)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const NormSeg sg = seg[lo];
+    const int64_t p = u - begin[lo];
+    const int4 ch = sg.child[p];
+    double s = 0.0;
+    if (ch.x >= 0) s += sg.csq[ch.x];
+    if (ch.y >= 0) s += sg.csq[ch.y];
+    if (ch.z >= 0) s += sg.csq[ch.z];
+    if (ch.w >= 0) s += sg.csq[ch.w];
+    sg.psq[p] = s;
+  }
+}
+
+BufP norm_batch_tables(spamm_ctx ctx, const std::vector<spamm_mat>& ms, std::vector<NormBatchLevel>* levels) {
+  int H = 0;
+  for (spamm_mat m : ms) H = m->L > H ? m->L : H;
+  std::vector<NormSeg> segs;
+  std::vector<int64_t> begins;
+  levels->clear();
+  for (int h = 1; h <= H; ++h) {
+    NormBatchLevel lv;
+    lv.first = (int)segs.size();
+    int64_t tot = 0;
+    for (spamm_mat m : ms) {
+      if (m->L < h) continue;
+      const Level& pa = m->lv[m->L - h];
+      if (pa.count == 0) continue;
+      segs.push_back({P<int4>(pa.child), P<double>(m->lv[m->L - h + 1].sq), P<double>(pa.sq)});
+      begins.push_back(tot);
+      tot += pa.count;
+    }
+    lv.nseg = (int)segs.size() - lv.first;
+    lv.total = tot;
+    levels->push_back(lv);
+  }
+  // pageable sources: each copy has read them by the time it returns
+  const size_t sb = segs.size() * sizeof(NormSeg), bb = begins.size() * sizeof(int64_t);
+  BufP tab = alloc_bytes(ctx, sb + bb + 16);
+  if (!segs.empty()) {
+    CK(cudaMemcpyAsync(tab->p, segs.data(), sb, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(static_cast<uint8_t*>(tab->p) + sb, begins.data(), bb, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  for (NormBatchLevel& lv : *levels) {
+    lv.seg = static_cast<const void*>(static_cast<const NormSeg*>(tab->p) + lv.first);
+    lv.begin = reinterpret_cast<const int64_t*>(static_cast<const uint8_t*>(tab->p) + sb) + lv.first;
+  }
+  return tab;
+}
+
+void propagate_norms_batch(spamm_ctx ctx, const std::vector<NormBatchLevel>& levels) {
+  for (const NormBatchLevel& lv : levels) {
+    if (lv.total == 0) continue;
+    parent_sum_batch_kernel<<<grid_for(ctx, lv.total, kThreads), kThreads, 0, ctx->stream>>>(
+        static_cast<const NormSeg*>(lv.seg), lv.begin, lv.nseg, lv.total);
+    CK_LAUNCH("parent_sum_batch_kernel");
+  }
+}
+
+void build_tree(spamm_mat m) {
+  build_skeleton(m);
+  alloc_level_norms(m);
+  propagate_norms(m);
 }
 
 // ----------------------------------------------------------- truncation

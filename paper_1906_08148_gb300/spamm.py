@@ -35,6 +35,7 @@ ENTRY_POINTS = (
     "spamm_multiply", "spamm_kept_tasks", "spamm_frob_norm", "spamm_error", "spamm_mat_info", "spamm_to_dense",
     "spamm_to_blocks", "spamm_gather_leaves", "spamm_level_norms", "spamm_leaf_sqnorms_noalloc",
     "spamm_plan_create", "spamm_plan_info", "spamm_execute", "spamm_plan_release", "spamm_set_gemm_sms",
+    "spamm_set_exec_graph",
 )
 NOALLOC_MAX_LEAVES = 1 << 24
 
@@ -57,7 +58,8 @@ class Stats(ctypes.Structure):
                 ("n_a_leaves", ctypes.c_int64), ("n_b_leaves", ctypes.c_int64), ("levels", ctypes.c_int32),
                 ("bs", ctypes.c_int32), ("kept_flops", ctypes.c_double), ("ms_truncate", ctypes.c_double),
                 ("ms_tasks", ctypes.c_double), ("ms_gemm", ctypes.c_double), ("ms_cnorm", ctypes.c_double),
-                ("n_launches", ctypes.c_int64), ("ms_prep", ctypes.c_double)]
+                ("n_launches", ctypes.c_int64), ("ms_prep", ctypes.c_double), ("n_steps", ctypes.c_int64),
+                ("executed_flops", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         L = self.levels
@@ -66,7 +68,7 @@ class Stats(ctypes.Structure):
                 "n_a_leaves": self.n_a_leaves, "n_b_leaves": self.n_b_leaves, "levels": L, "bs": self.bs,
                 "kept_flops": self.kept_flops, "ms_truncate": self.ms_truncate, "ms_tasks": self.ms_tasks,
                 "ms_gemm": self.ms_gemm, "ms_cnorm": self.ms_cnorm, "n_launches": self.n_launches,
-                "ms_prep": self.ms_prep}
+                "ms_prep": self.ms_prep, "n_steps": self.n_steps, "executed_flops": self.executed_flops}
 
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -115,6 +117,7 @@ def load(path: str = LIB_PATH):
         "spamm_execute": [vp, i64, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(Stats)],
         "spamm_plan_release": [vp],
         "spamm_set_gemm_sms": [vp, ctypes.c_int],
+        "spamm_set_exec_graph": [vp, ctypes.c_int],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -437,3 +440,7 @@ def spamm_execute(ctx: Context, plans, stats: bool = False):
 
 def spamm_set_gemm_sms(ctx: Context, nsms: int):
     _check(ctx.handle, load().spamm_set_gemm_sms(ctx.handle, int(nsms)))
+
+
+def spamm_set_exec_graph(ctx: Context, enable: bool):
+    _check(ctx.handle, load().spamm_set_exec_graph(ctx.handle, 1 if enable else 0))

@@ -75,6 +75,9 @@ def _load():
         lib.synth_lattice_point_host.argtypes = [ctypes.c_int64, ip]
         lib.synth_leaf_bound_host.argtypes = [P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64]
         lib.synth_leaf_bound_host.restype = ctypes.c_double
+        lib.synth_block_sparse.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64,
+                                           ip, ip, dp]
+        lib.synth_block_sparse.restype = ctypes.c_int64
         _lib = lib
     return _lib
 
@@ -125,6 +128,22 @@ def lattice_point(i: int):
     xyz = np.zeros(3, dtype=np.int32)
     _load().synth_lattice_point_host(i, _ptr(xyz, ctypes.c_int32))
     return tuple(int(v) for v in xyz)
+
+
+def block_sparse(n: int, bs: int, fill: float, seed: int = 1):
+    """Random block-sparse n x n matrix (Section 5.2's leaf-library benchmark):
+    each bs x bs block non-zero with probability `fill`, elements U[-1, 1).
+    Returns (bi, bj, data) with data of shape (count, bs, bs)."""
+    nb = -(-n // bs)
+    lib = _load()
+    cnt = lib.synth_block_sparse(nb, bs, float(fill), seed, None, None, None)
+    bi = np.empty(cnt, np.int32)
+    bj = np.empty(cnt, np.int32)
+    data = np.empty((cnt, bs, bs), np.float64)
+    if cnt:
+        lib.synth_block_sparse(nb, bs, float(fill), seed, _ptr(bi, ctypes.c_int32), _ptr(bj, ctypes.c_int32),
+                               _ptr(data, ctypes.c_double))
+    return bi, bj, data
 
 
 # The synthetic workloads (sizes and decay of the paper's model problem and

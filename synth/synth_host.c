@@ -29,3 +29,33 @@ void synth_lattice_point_host(int64_t i, int32_t* xyz) { synth_lattice_point(i, 
 double synth_leaf_bound_host(const synth_params* p, int32_t bs, int64_t bi, int64_t bj) {
   return synth_leaf_bound(p, bs, bi, bj);
 }
+
+/* Random block-sparse matrix (the leaf-library benchmark of Section 5.2): on
+ * an nb x nb grid of bs x bs blocks, block (I, J) is non-zero with probability
+ * `fill`, independently of the others (uniformly distributed positions); its
+ * elements are uniform in [-1, 1).  Position draws use the SplitMix64 stream
+ * `seed`, element draws the stream `seed` + 1 (number I*nb+J, resp. i<<32|j).
+ * Returns the block count; with non-null outputs also writes the blocks in
+ * row-major block order (coordinates and bs*bs row-major values each). */
+int64_t synth_block_sparse(int64_t nb, int32_t bs, double fill, uint64_t seed, int32_t* bi, int32_t* bj,
+                           double* out) {
+  int64_t m = 0;
+  for (int64_t I = 0; I < nb; ++I)
+    for (int64_t J = 0; J < nb; ++J) {
+      const double u = (double)(synth_splitmix64(seed, (uint64_t)(I * nb + J)) >> 11) * 0x1.0p-53;
+      if (!(u < fill)) continue;
+      if (bi) {
+        bi[m] = (int32_t)I;
+        bj[m] = (int32_t)J;
+        double* dst = out + m * (int64_t)bs * bs;
+        for (int32_t r = 0; r < bs; ++r)
+          for (int32_t c = 0; c < bs; ++c) {
+            const uint64_t i = (uint64_t)(I * bs + r), j = (uint64_t)(J * bs + c);
+            const uint64_t h = synth_splitmix64(seed + 1ull, (i << 32) | j);
+            dst[r * bs + c] = (double)(h >> 11) * 0x1.0p-52 - 1.0;
+          }
+      }
+      ++m;
+    }
+  return m;
+}

@@ -1,0 +1,52 @@
+"""Autotuner decision logic (no GPU): admissibility by error, fastest wins,
+nearest calibrated point, determinism, the leaf-size-restricted choice."""
+import math
+
+from paper_1906_08148_gb300.autotune import Autotuner, Choice, Point, decide
+
+
+def _pt(n, alpha, tau, ms, arith, trunc):
+    return Point(n, alpha, tau, decide(ms, arith, trunc), ms, arith, trunc)
+
+
+MS = {"fp64/32": 40.0, "fp64/64": 30.0, "bf16_split/64": 3.0, "fp16_scaled/64": 2.0}
+
+
+def test_fastest_admissible_form_wins():
+    # both tensor forms accurate enough: the faster one
+    assert decide(MS, {"bf16_split/64": 1e-6, "fp16_scaled/64": 2e-6}, 1e-4) == Choice("fp16_scaled", 64)
+    # FP16 too coarse for this truncation error, BF16 fine
+    assert decide(MS, {"bf16_split/64": 1e-6, "fp16_scaled/64": 2e-4}, 1e-4) == Choice("bf16_split", 64)
+    # neither tensor form within the truncation error: the faster FP64 leaf size
+    assert decide(MS, {"bf16_split/64": 1e-3, "fp16_scaled/64": 2e-3}, 1e-4) == Choice("fp64", 64)
+    assert decide({**MS, "fp64/32": 20.0}, {}, 1e-4) == Choice("fp64", 32)
+    # missing error measurement: not admissible
+    assert decide(MS, {}, 1.0) == Choice("fp64", 64)
+    assert decide({}, {}, 1.0) == Choice("fp64", 64)
+
+
+def test_nearest_point_and_defaults():
+    pts = [_pt(4096, 1.0, 1e-4, MS, {"bf16_split/64": 1e-6, "fp16_scaled/64": 1e-6}, 1e-3),
+           _pt(65536, 1.0, 1e-8, MS, {"bf16_split/64": 1e-5, "fp16_scaled/64": 1e-5}, 1e-7)]
+    t = Autotuner(pts)
+    assert t.choose(4000, 1.05, 2e-4) == Choice("fp16_scaled", 64)
+    assert t.choose(60000, 0.95, 1e-8) == Choice("fp64", 64)
+    assert t.choose(60000, 0.95, 0.0) == Choice("fp64", 64)
+    # inputs already built with 32 x 32 leaves: only the FP64 form exists there
+    assert t.choose(4000, 1.0, 1e-4, bs=32) == Choice("fp64", 32)
+    assert t.choose(4000, 1.0, 1e-4, bs=64) == Choice("fp16_scaled", 64)
+    assert Autotuner([]).choose(4096, 1.0, 1e-4) == Choice("fp64", 64)
+    # a pure function of the request: repeated and interleaved calls agree
+    seq = [(4096, 1.0, 1e-4), (65536, 0.9, 1e-8), (8192, 1.2, 1e-6)]
+    first = [t.choose(*q) for q in seq]
+    assert [t.choose(*q) for q in seq[::-1]][::-1] == first
+
+
+def test_table_round_trip(tmp_path):
+    from paper_1906_08148_gb300 import autotune
+    pts = [_pt(4096, 0.6, 1e-6, MS, {"bf16_split/64": 1e-6, "fp16_scaled/64": 5e-6}, 2e-6)]
+    path = str(tmp_path / "t.json")
+    autotune.save(pts, path, meta={"x": 1})
+    back = autotune.load(path)
+    assert back[0].choice == Choice("bf16_split", 64) and math.isclose(back[0].trunc_err, 2e-6)
+    assert Autotuner(path=path).choose(4096, 0.6, 1e-6) == Choice("bf16_split", 64)

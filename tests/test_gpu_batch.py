@@ -97,3 +97,31 @@ def test_gemm_sm_limit_keeps_results(S, ctx):
     finally:
         S.spamm_set_gemm_sms(ctx, 0)
     assert np.array_equal(ref[2], got[2])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16_split", "fp16_scaled"])
+def test_graph_execute_equals_eager(S, ctx, prec):
+    """The execute phase captured as one CUDA graph gives the same leaves and
+    the same norms at every quadtree level as the eager launch sequence."""
+    plans, keep = [], []
+    for n, alpha, tau, mode in REQUESTS:
+        GA, GB = _inputs(S, ctx, n, alpha, 64)
+        keep.append((GA, GB))
+        plans.append(S.spamm_plan_create(ctx, GA, GB, tau, mode, prec))
+    eager, st_e = S.spamm_execute(ctx, plans, stats=True)
+    S.spamm_set_exec_graph(ctx, True)
+    try:
+        graph, st_g = S.spamm_execute(ctx, plans, stats=True)
+        single = S.spamm_multiply(ctx, keep[0][0], keep[0][1], REQUESTS[0][2], REQUESTS[0][3], prec)
+    finally:
+        S.spamm_set_exec_graph(ctx, False)
+    for r, (E, G) in enumerate(zip(eager, graph)):
+        for a, b in zip(S.spamm_to_blocks(ctx, E), S.spamm_to_blocks(ctx, G)):
+            assert np.array_equal(a, b), (prec, r)
+        L = E.info()["levels"]
+        for lev in range(L + 1):
+            ce, se = S.spamm_level_norms(ctx, E, lev)
+            cg, sg = S.spamm_level_norms(ctx, G, lev)
+            assert np.array_equal(ce, cg) and np.array_equal(se, sg), (prec, r, lev)
+        assert st_g[r]["ms_gemm"] > 0.0
+    assert np.array_equal(S.spamm_to_blocks(ctx, single)[2], S.spamm_to_blocks(ctx, eager[0])[2])

@@ -241,6 +241,29 @@ def test_tau_zero_is_the_dense_product(S, ctx):
     assert np.linalg.norm(D - ref) <= 1e-13 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("bs,fill", [(32, 0.05), (64, 0.3), (32, 0.9)])
+@pytest.mark.parametrize("prec", ["fp64", "bf16_split", "fp16_scaled"])
+def test_random_block_sparse_tau_zero(S, ctx, bs, fill, prec):
+    """Section 5.2's leaf-library workload: uniformly placed random blocks,
+    tau = 0 keeps every non-null pair; leaf set and product match the oracle."""
+    if prec != "fp64" and bs != 64:
+        pytest.skip("tensor-core forms are built for 64 x 64 leaves")
+    n = 1024
+    ai, aj, ad = synth.block_sparse(n, bs, fill, seed=3)
+    bi, bj, bd = synth.block_sparse(n, bs, fill, seed=4)
+    GA, GB = S.spamm_from_blocks(ctx, n, bs, ai, aj, ad), S.spamm_from_blocks(ctx, n, bs, bi, bj, bd)
+    C, st = S.spamm_multiply(ctx, GA, GB, 0.0, "spamm", prec, stats=True)
+    OA, OB = oracle.from_leaves(n, bs, ai, aj, ad), oracle.from_leaves(n, bs, bi, bj, bd)
+    ref, ikj = oracle.multiply(OA, OB, 0.0, oracle.MODES["spamm"])
+    assert st["n_kept"] == len(ikj)
+    got = S.spamm_to_blocks(ctx, C)
+    key = lambda i, j: np.sort(np.asarray(i, np.int64) * 65536 + np.asarray(j, np.int64))
+    assert np.array_equal(key(got[0], got[1]), key(ref.bi, ref.bj))
+    D, R = S.spamm_to_dense(ctx, C), oracle.to_dense(ref)
+    rel = np.linalg.norm(D - R) / np.linalg.norm(R)
+    assert rel <= (REL_C if prec == "fp64" else 1e-6), rel
+
+
 def test_edge_cases(S, ctx):
     # single leaf (L = 0), with the leaf-level test
     A, B = _dense_pair(20, 0.3)

@@ -97,3 +97,23 @@ def test_leaf_bound_dominates_every_element(params, bs):
             assert m <= b
             tight += m > 0.1 * b
     assert tight > 0
+
+
+@pytest.mark.parametrize("fill", [0.05, 0.3, 0.9])
+def test_block_sparse_fill_and_values(fill):
+    """Section 5.2's random block-sparse input: independent uniform block
+    positions (fill fraction within a 4-sigma binomial band), elements in
+    [-1, 1) with mean ~0, deterministic per seed, different for another seed."""
+    n, bs = 2048, 32
+    nb = n // bs
+    bi, bj, d = synth.block_sparse(n, bs, fill, seed=11)
+    m = len(bi)
+    sd = np.sqrt(nb * nb * fill * (1 - fill))
+    assert abs(m - fill * nb * nb) <= 4 * sd
+    assert np.all((d >= -1.0) & (d < 1.0))
+    assert abs(d.mean()) < 4 * np.sqrt(1 / 3 / d.size)
+    assert len(set(zip(bi.tolist(), bj.tolist()))) == m
+    b2 = synth.block_sparse(n, bs, fill, seed=11)
+    assert np.array_equal(b2[2], d)
+    b3 = synth.block_sparse(n, bs, fill, seed=12)
+    assert not (len(b3[0]) == m and np.array_equal(b3[0], bi) and np.array_equal(b3[1], bj))
