@@ -266,6 +266,24 @@ SPAMM_API spamm_status spamm_set_exec_graph(spamm_ctx ctx, int enable);
 SPAMM_API spamm_status spamm_kept_tasks(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_mode mode,
                               int32_t* ikj_out, int64_t cap, int64_t* count);
 
+/* ------------------------------------------- operations of a purification chain */
+
+/* *out = alpha X + beta Y (same n and bs), element by element as
+ * fl(fl(alpha x) + fl(beta y)) with an absent leaf taken as zero; the leaf set
+ * is the union of X's and Y's, without leaves that come out exactly zero
+ * (null = zero).  Section 4.4 lists addition and rescaling among the
+ * operations of the leaf library; with the identity it gives the shifts and
+ * the 2X - X^2 step of density-matrix purification (Section 1).  Errors:
+ * INVALID_ARG, SHAPE, NONFINITE (an element overflowed), OOM, CUDA. */
+SPAMM_API spamm_status spamm_add(spamm_ctx ctx, double alpha, spamm_mat X, double beta, spamm_mat Y, spamm_mat* out);
+
+/* The n x n identity as a quadtree of bs x bs leaves (diagonal leaves only). */
+SPAMM_API spamm_status spamm_identity(spamm_ctx ctx, int64_t n, int bs, spamm_mat* out);
+
+/* Trace of X (the sum of the diagonals of its diagonal leaves, each leaf in
+ * row order, the leaf sums by a fixed reduction tree). */
+SPAMM_API spamm_status spamm_trace(spamm_ctx ctx, spamm_mat X, double* out);
+
 /* ------------------------------------------------------------ evaluation */
 
 /* ||M||_F = sqrt of the root's squared norm (Section 2); 0 for an empty M. */

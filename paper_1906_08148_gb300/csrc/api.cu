@@ -593,6 +593,33 @@ spamm_status spamm_kept_tasks(spamm_ctx ctx, spamm_mat A, spamm_mat B, double ta
   });
 }
 
+spamm_status spamm_add(spamm_ctx ctx, double alpha, spamm_mat X, double beta, spamm_mat Y, spamm_mat* out) {
+  if (!ctx || !X || !Y || !out) return SPAMM_E_INVALID_ARG;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    need(std::isfinite(alpha) && std::isfinite(beta), "alpha and beta must be finite");
+    if (X->n != Y->n || X->bs != Y->bs) fail(SPAMM_E_SHAPE, "X and Y differ in n or bs");
+    if (X->ctx->device != ctx->device || Y->ctx->device != ctx->device)
+      fail(SPAMM_E_INVALID_ARG, "operands live on another device");
+    *out = registered(add_scaled(alpha, X, beta, Y, ctx));
+  });
+}
+
+spamm_status spamm_identity(spamm_ctx ctx, int64_t n, int bs, spamm_mat* out) {
+  if (!ctx || !out) return SPAMM_E_INVALID_ARG;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    check_bs(bs);
+    check_n(n, bs);
+    *out = registered(identity_mat(ctx, n, bs));
+  });
+}
+
+spamm_status spamm_trace(spamm_ctx ctx, spamm_mat X, double* out) {
+  if (!ctx || !X || !out) return SPAMM_E_INVALID_ARG;
+  return guarded(ctx, [&] { *out = trace_of(X); });
+}
+
 spamm_status spamm_frob_norm(spamm_ctx ctx, spamm_mat m, double* out) {
   if (!ctx || !m || !out) return SPAMM_E_INVALID_ARG;
   return guarded(ctx, [&] {

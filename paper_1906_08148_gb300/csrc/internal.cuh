@@ -155,6 +155,12 @@ spamm_mat truncate_element(spamm_mat in, double tau);
 void leaf_sqnorms(spamm_ctx ctx, const double* pool, const int64_t* slot, int64_t nleaves, int bs, double* sq,
                   uint8_t* nonzero, int check_finite);
 double error_fro(spamm_mat X, spamm_mat Y);
+double device_sum(spamm_ctx ctx, const double* in, int64_t n);  // deterministic reduction, synchronises
+
+// ---- purification-chain operations (algebra.cu) ----
+spamm_mat add_scaled(double alpha, spamm_mat X, double beta, spamm_mat Y, spamm_ctx ctx);
+spamm_mat identity_mat(spamm_ctx ctx, int64_t n, int bs);
+double trace_of(spamm_mat X);
 
 // ---- task-list builder (tasks.cu) ----
 struct TaskList {

@@ -158,10 +158,4 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
       : "memory");
 }
 
-// Ask the TMA engine to bring `bytes` at src_gmem into L2 (no completion
-// tracking).  Address 16-byte aligned, bytes % 16 == 0.
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src_gmem, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src_gmem), "r"(bytes) : "memory");
-}
-
 }  // namespace spamm

@@ -61,14 +61,20 @@ __device__ __forceinline__ unsigned child_mask(const int4& ca, const int4& cb, c
 }
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    task_count_kernel(int64_t G, const int64_t* __restrict__ gstart, const int32_t* __restrict__ ta,
+    task_count_kernel(int64_t Gcap, const int64_t* __restrict__ dG, const int64_t* __restrict__ gstart,
+                      const int32_t* __restrict__ ta,
                       const int32_t* __restrict__ tb, const int4* __restrict__ childA, const int4* __restrict__ childB,
                       const double* __restrict__ sqA, const double* __restrict__ sqB, double tau, int test, int leaf,
                       uint8_t* __restrict__ mask, uint64_t* __restrict__ packed, unsigned long long* stats) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t G = *dG;
   long long cand = 0, border = 0;
-  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += nw) {
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < Gcap; g += nw) {
+    if (g >= G) {  // beyond this level's groups: no children (the scan runs over the capacity)
+      if (lane < 4) packed[4 * g + lane] = 0;
+      continue;
+    }
     const int64_t q0 = gstart[g], q1 = gstart[g + 1];
     unsigned cnt[4] = {0, 0, 0, 0};
     for (int64_t q = q0 + lane; q < q1; q += 32) {
@@ -100,7 +106,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 }
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    task_write_kernel(int64_t G, const int64_t* __restrict__ gstart, const uint32_t* __restrict__ gcode,
+    task_write_kernel(const int64_t* __restrict__ dG, const int64_t* __restrict__ gstart,
+                      const uint32_t* __restrict__ gcode,
                       const int32_t* __restrict__ ta, const int32_t* __restrict__ tb, const int4* __restrict__ childA,
                       const int4* __restrict__ childB, const uint8_t* __restrict__ mask,
                       const uint64_t* __restrict__ packed, const uint64_t* __restrict__ off,
@@ -108,6 +115,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                       int64_t* __restrict__ gstart2, int32_t* __restrict__ quad) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t G = *dG;
   for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += nw) {
     const int64_t q0 = gstart[g], q1 = gstart[g + 1];
     int64_t base[4];
@@ -177,6 +185,28 @@ static unsigned warps_grid(spamm_ctx ctx, int64_t items) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
+// Sizes of the next level from the scan total, on the device: its pair and
+// group counts, the closing entry of its group offsets, and this level's
+// statistics (lv[4 t ..]: candidates, borderline pairs, pairs, groups).
+__global__ void level_finish_kernel(const uint64_t* __restrict__ tot, const unsigned long long* __restrict__ stats,
+                                    int64_t* __restrict__ dQ2, int64_t* __restrict__ dG2, int64_t* __restrict__ gstart2,
+                                    int64_t* __restrict__ lv) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int64_t Q2 = (int64_t)(*tot & kCountMask), G2 = (int64_t)(*tot >> 36);
+  *dQ2 = Q2;
+  *dG2 = G2;
+  gstart2[G2] = Q2;
+  lv[0] = (int64_t)stats[0];
+  lv[1] = (int64_t)stats[1];
+  lv[2] = Q2;
+  lv[3] = G2;
+}
+
+// Upper bounds on the next level's sizes below which the host does not wait
+// for the exact counts (buffers are allocated at the bound instead).
+constexpr int64_t kPairsNoSync = 1ll << 22;
+constexpr int64_t kGroupsNoSync = 1ll << 20;
+
 TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm_ctx on) {
   spamm_ctx ctx = on ? on : A->ctx;
   TaskList T;
@@ -186,23 +216,32 @@ TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm
     return T;
   }
   // level 0: the root pair is entered
-  int64_t G = 1, Q = 1;
+  int64_t G = 1, Q = 1;  // capacities; exact when `exact`
+  bool exact = true;
   BufP gcode = alloc_n<uint32_t>(ctx, 1), gstart = alloc_n<int64_t>(ctx, 2);
   BufP ta = alloc_n<int32_t>(ctx, 1), tb = alloc_n<int32_t>(ctx, 1);
+  // device sizes: [2 t] pairs, [2 t + 1] groups of level t; per-level statistics after them
+  const int nlev = A->L + 1;
+  BufP sizes = alloc_n<int64_t>(ctx, 2 * nlev + 4 * nlev);
+  int64_t* dsz = P<int64_t>(sizes);
+  int64_t* dlv = dsz + 2 * nlev;
   {
     const int64_t h_gstart[2] = {0, 1};
+    const int64_t h_sz[2] = {1, 1};
+    CK(cudaMemsetAsync(dsz, 0, (2 * nlev + 4 * nlev) * sizeof(int64_t), ctx->stream));
     CK(cudaMemsetAsync(P<uint32_t>(gcode), 0, sizeof(uint32_t), ctx->stream));
     CK(cudaMemsetAsync(P<int32_t>(ta), 0, sizeof(int32_t), ctx->stream));
     CK(cudaMemsetAsync(P<int32_t>(tb), 0, sizeof(int32_t), ctx->stream));
     CK(cudaMemcpyAsync(P<int64_t>(gstart), h_gstart, sizeof(h_gstart), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(dsz, h_sz, sizeof(h_sz), cudaMemcpyHostToDevice, ctx->stream));
   }
   unsigned long long* stats = ctx->d_scratch;  // [0] candidates, [1] borderline
+  uint64_t* hp = static_cast<uint64_t*>(ctx->h_pinned);
   if (A->L == 0) {
     // a single leaf: the root pair is the only leaf pair and takes the leaf test
     root_test_kernel<<<1, 32, 0, ctx->stream>>>(P<double>(A->lv[0].sq), P<double>(B->lv[0].sq), tau, test_norms,
                                                 P<int64_t>(gstart), stats);
     CK_LAUNCH("root_test_kernel");
-    uint64_t* hp = static_cast<uint64_t*>(ctx->h_pinned);
     CK(cudaMemcpyAsync(hp, P<int64_t>(gstart) + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(hp + 1, stats, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -217,50 +256,69 @@ TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm
       CK(cudaMemcpyAsync(P<int32_t>(T.quads), q4, sizeof(q4), cudaMemcpyHostToDevice, ctx->stream));
     }
   }
+  int last = 0;  // level whose sizes describe the current arrays
   for (int t = 0; t < A->L; ++t) {
     const bool leaf = (t + 1 == A->L);
+    const int64_t* dG = dsz + 2 * t + 1;
     CK(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned long long), ctx->stream));
     BufP mask = alloc_n<uint8_t>(ctx, Q);
     BufP packed = alloc_n<uint64_t>(ctx, 4 * G), off = alloc_n<uint64_t>(ctx, 4 * G), tot = alloc_n<uint64_t>(ctx, 1);
     task_count_kernel<<<warps_grid(ctx, G), kWarpsPerBlock * 32, 0, ctx->stream>>>(
-        G, P<int64_t>(gstart), P<int32_t>(ta), P<int32_t>(tb), P<int4>(A->lv[t].child), P<int4>(B->lv[t].child),
+        G, dG, P<int64_t>(gstart), P<int32_t>(ta), P<int32_t>(tb), P<int4>(A->lv[t].child), P<int4>(B->lv[t].child),
         P<double>(A->lv[t + 1].sq), P<double>(B->lv[t + 1].sq), tau, test_norms, leaf, P<uint8_t>(mask),
         P<uint64_t>(packed), stats);
     CK_LAUNCH("task_count_kernel");
     scan_exclusive_u64(ctx, P<uint64_t>(packed), P<uint64_t>(off), 4 * G, P<uint64_t>(tot));
-    uint64_t* hp = static_cast<uint64_t*>(ctx->h_pinned);
-    CK(cudaMemcpyAsync(hp, P<uint64_t>(tot), sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(hp + 1, stats, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    const uint64_t total = hp[0];
-    const unsigned long long h_stats[2] = {hp[1], hp[2]};
-    const int64_t Q2 = (int64_t)(total & kCountMask), G2 = (int64_t)(total >> 36);
-    T.n_candidates[t + 1] = (int64_t)h_stats[0];
-    T.n_kept_level[t + 1] = Q2;
-    if (leaf) T.n_borderline = (int64_t)h_stats[1];
-    BufP gcode2 = alloc_n<uint32_t>(ctx, G2), gstart2 = alloc_n<int64_t>(ctx, G2 + 1);
-    if (leaf) {
-      // the parents of the C leaves: their four children form the quads
-      T.nquads = G;
-      T.quads = alloc_n<int32_t>(ctx, 4 * G);
+    // capacities of the next level: exact after a wait, else the bounds 8 Q and 4 G
+    int64_t Q2 = 8 * Q, G2 = 4 * G;
+    const bool wait = Q2 > kPairsNoSync || G2 > kGroupsNoSync || leaf;
+    BufP gstart2;
+    if (wait) {
+      CK(cudaMemcpyAsync(hp, P<uint64_t>(tot), sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(hp + 1, dG, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      Q2 = (int64_t)(hp[0] & kCountMask);
+      G2 = (int64_t)(hp[0] >> 36);
+      if (leaf) T.nquads = (int64_t)hp[1];  // this level's groups are the parents of the C leaves
     }
+    gstart2 = alloc_n<int64_t>(ctx, G2 + 1);
+    level_finish_kernel<<<1, 32, 0, ctx->stream>>>(P<uint64_t>(tot), stats, dsz + 2 * (t + 1), dsz + 2 * (t + 1) + 1,
+                                                   P<int64_t>(gstart2), dlv + 4 * (t + 1));
+    CK_LAUNCH("level_finish_kernel");
+    BufP gcode2 = alloc_n<uint32_t>(ctx, G2);
+    if (leaf) T.quads = alloc_n<int32_t>(ctx, 4 * G);  // the four children of each parent of the C leaves
     BufP ta2 = alloc_n<int32_t>(ctx, Q2), tb2 = alloc_n<int32_t>(ctx, Q2);
-    CK(cudaMemcpyAsync(P<int64_t>(gstart2) + G2, &T.n_kept_level[t + 1], sizeof(int64_t), cudaMemcpyHostToDevice,
-                       ctx->stream));
     if (G2 > 0) {
       task_write_kernel<<<warps_grid(ctx, G), kWarpsPerBlock * 32, 0, ctx->stream>>>(
-          G, P<int64_t>(gstart), P<uint32_t>(gcode), P<int32_t>(ta), P<int32_t>(tb), P<int4>(A->lv[t].child),
+          dG, P<int64_t>(gstart), P<uint32_t>(gcode), P<int32_t>(ta), P<int32_t>(tb), P<int4>(A->lv[t].child),
           P<int4>(B->lv[t].child), P<uint8_t>(mask), P<uint64_t>(packed), P<uint64_t>(off), P<int32_t>(ta2),
           P<int32_t>(tb2), P<uint32_t>(gcode2), P<int64_t>(gstart2), leaf ? P<int32_t>(T.quads) : nullptr);
       CK_LAUNCH("task_write_kernel");
     }
     G = G2;
     Q = Q2;
+    exact = wait;
     gcode = gcode2;
     gstart = gstart2;
     ta = ta2;
     tb = tb2;
-    if (G == 0) break;
+    last = t + 1;
+    if (exact && G == 0) break;
+  }
+  // exact sizes and per-level statistics, one read-back
+  const int nread = 4 * nlev;
+  std::vector<int64_t> h(2 + nread);
+  CK(cudaMemcpyAsync(h.data(), dsz + 2 * last, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(h.data() + 2, dlv, nread * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (A->L > 0) {
+    Q = h[0];
+    G = h[1];
+    for (int t = 1; t <= last; ++t) {
+      T.n_candidates[t] = h[2 + 4 * t + 0];
+      T.n_kept_level[t] = h[2 + 4 * t + 2];
+    }
+    if (last == A->L) T.n_borderline = h[2 + 4 * A->L + 1];
   }
   T.ngroups = G;
   T.ntasks = Q;

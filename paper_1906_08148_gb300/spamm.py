@@ -35,7 +35,7 @@ ENTRY_POINTS = (
     "spamm_multiply", "spamm_kept_tasks", "spamm_frob_norm", "spamm_error", "spamm_mat_info", "spamm_to_dense",
     "spamm_to_blocks", "spamm_gather_leaves", "spamm_level_norms", "spamm_leaf_sqnorms_noalloc",
     "spamm_plan_create", "spamm_plan_info", "spamm_execute", "spamm_plan_release", "spamm_set_gemm_sms",
-    "spamm_set_exec_graph",
+    "spamm_set_exec_graph", "spamm_add", "spamm_identity", "spamm_trace",
 )
 NOALLOC_MAX_LEAVES = 1 << 24
 
@@ -118,6 +118,9 @@ def load(path: str = LIB_PATH):
         "spamm_plan_release": [vp],
         "spamm_set_gemm_sms": [vp, ctypes.c_int],
         "spamm_set_exec_graph": [vp, ctypes.c_int],
+        "spamm_add": [vp, f64, vp, f64, vp, ctypes.POINTER(vp)],
+        "spamm_identity": [vp, i64, ctypes.c_int, ctypes.POINTER(vp)],
+        "spamm_trace": [vp, vp, pf64],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -440,6 +443,21 @@ def spamm_execute(ctx: Context, plans, stats: bool = False):
 
 def spamm_set_gemm_sms(ctx: Context, nsms: int):
     _check(ctx.handle, load().spamm_set_gemm_sms(ctx.handle, int(nsms)))
+
+
+def spamm_add(ctx: Context, alpha: float, X: Matrix, beta: float, Y: Matrix) -> Matrix:
+    """alpha X + beta Y (union of the leaf sets, exact-zero leaves dropped)."""
+    return _new(ctx, load().spamm_add, float(alpha), X.handle, float(beta), Y.handle)
+
+
+def spamm_identity(ctx: Context, n: int, bs: int) -> Matrix:
+    return _new(ctx, load().spamm_identity, int(n), int(bs))
+
+
+def spamm_trace(ctx: Context, X: Matrix) -> float:
+    v = ctypes.c_double()
+    _check(ctx.handle, load().spamm_trace(ctx.handle, X.handle, ctypes.byref(v)))
+    return v.value
 
 
 def spamm_set_exec_graph(ctx: Context, enable: bool):

@@ -10,6 +10,7 @@ and wraps it with ctypes.  Nothing here computes norms, thresholds or products.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from dataclasses import dataclass
@@ -130,18 +131,35 @@ def lattice_point(i: int):
     return tuple(int(v) for v in xyz)
 
 
+def spectral_bound(p: DecayParams) -> float:
+    """An upper bound of ||A||_2 for the matrices of `p`: the largest absolute
+    row sum (Gershgorin) is at most |c| sum_j exp(-alpha d(i, j)) over all
+    lattice points j, which for the 1-D kind is the closed form coth(alpha/2)
+    and for the 3-D kind the sum over integer offsets within radius 48/alpha
+    (the rest is below 1e-12 relative), enlarged by 1e-9 relative."""
+    a = float(p.alpha)
+    if p.kind == KIND_1D:
+        s = 1.0 + 2.0 * math.exp(-a) / (1.0 - math.exp(-a))
+    else:
+        R = int(math.ceil(48.0 / a))
+        r = np.arange(-R, R + 1, dtype=np.float64)
+        d2 = r[:, None, None] ** 2 + r[None, :, None] ** 2 + r[None, None, :] ** 2
+        s = float(np.sum(np.exp(-a * np.sqrt(d2))))
+    return abs(p.c) * s * (1.0 + 1e-9)
+
+
 def block_sparse(n: int, bs: int, fill: float, seed: int = 1):
     """Random block-sparse n x n matrix (Section 5.2's leaf-library benchmark):
-    each bs x bs block non-zero with probability `fill`, elements U[-1, 1).
+    each bs x bs block non-zero with probability `fill`, elements U[-1, 1)
+    (zero past row / column n).
     Returns (bi, bj, data) with data of shape (count, bs, bs)."""
-    nb = -(-n // bs)
     lib = _load()
-    cnt = lib.synth_block_sparse(nb, bs, float(fill), seed, None, None, None)
+    cnt = lib.synth_block_sparse(n, bs, float(fill), seed, None, None, None)
     bi = np.empty(cnt, np.int32)
     bj = np.empty(cnt, np.int32)
     data = np.empty((cnt, bs, bs), np.float64)
     if cnt:
-        lib.synth_block_sparse(nb, bs, float(fill), seed, _ptr(bi, ctypes.c_int32), _ptr(bj, ctypes.c_int32),
+        lib.synth_block_sparse(n, bs, float(fill), seed, _ptr(bi, ctypes.c_int32), _ptr(bj, ctypes.c_int32),
                                _ptr(data, ctypes.c_double))
     return bi, bj, data
 

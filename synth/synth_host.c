@@ -30,15 +30,18 @@ double synth_leaf_bound_host(const synth_params* p, int32_t bs, int64_t bi, int6
   return synth_leaf_bound(p, bs, bi, bj);
 }
 
-/* Random block-sparse matrix (the leaf-library benchmark of Section 5.2): on
- * an nb x nb grid of bs x bs blocks, block (I, J) is non-zero with probability
- * `fill`, independently of the others (uniformly distributed positions); its
- * elements are uniform in [-1, 1).  Position draws use the SplitMix64 stream
- * `seed`, element draws the stream `seed` + 1 (number I*nb+J, resp. i<<32|j).
- * Returns the block count; with non-null outputs also writes the blocks in
- * row-major block order (coordinates and bs*bs row-major values each). */
-int64_t synth_block_sparse(int64_t nb, int32_t bs, double fill, uint64_t seed, int32_t* bi, int32_t* bj,
+/* Random block-sparse n x n matrix (the leaf-library benchmark of Section
+ * 5.2): on the nb x nb grid of bs x bs blocks (nb = ceil(n / bs)), block
+ * (I, J) is non-zero with probability `fill`, independently of the others
+ * (uniformly distributed positions); its elements inside the matrix are
+ * uniform in [-1, 1), those past row or column n (the padding of the last
+ * blocks) are 0.  Position draws use the SplitMix64 stream `seed`, element
+ * draws the stream `seed` + 1 (number I*nb+J, resp. i<<32|j).  Returns the
+ * block count; with non-null outputs also writes the blocks in row-major
+ * block order (coordinates and bs*bs row-major values each). */
+int64_t synth_block_sparse(int64_t n, int32_t bs, double fill, uint64_t seed, int32_t* bi, int32_t* bj,
                            double* out) {
+  const int64_t nb = (n + bs - 1) / bs;
   int64_t m = 0;
   for (int64_t I = 0; I < nb; ++I)
     for (int64_t J = 0; J < nb; ++J) {
@@ -52,7 +55,7 @@ int64_t synth_block_sparse(int64_t nb, int32_t bs, double fill, uint64_t seed, i
           for (int32_t c = 0; c < bs; ++c) {
             const uint64_t i = (uint64_t)(I * bs + r), j = (uint64_t)(J * bs + c);
             const uint64_t h = synth_splitmix64(seed + 1ull, (i << 32) | j);
-            dst[r * bs + c] = (double)(h >> 11) * 0x1.0p-52 - 1.0;
+            dst[r * bs + c] = ((int64_t)i < n && (int64_t)j < n) ? (double)(h >> 11) * 0x1.0p-52 - 1.0 : 0.0;
           }
       }
       ++m;

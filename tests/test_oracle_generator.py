@@ -117,3 +117,13 @@ def test_block_sparse_fill_and_values(fill):
     assert np.array_equal(b2[2], d)
     b3 = synth.block_sparse(n, bs, fill, seed=12)
     assert not (len(b3[0]) == m and np.array_equal(b3[0], bi) and np.array_equal(b3[1], bj))
+
+
+def test_block_sparse_padding_stays_zero():
+    n, bs = 300, 32
+    bi, bj, d = synth.block_sparse(n, bs, 0.9, seed=5)
+    for q in range(len(bi)):
+        r0, c0 = bi[q] * bs, bj[q] * bs
+        rows, cols = max(0, min(bs, n - r0)), max(0, min(bs, n - c0))
+        assert not np.any(d[q, rows:, :]) and not np.any(d[q, :, cols:])
+        assert np.all(d[q, :rows, :cols] != 0.0)
