@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -53,7 +54,8 @@ def parse_args():
     ap.add_argument("--config", default="lattice65536", choices=sorted(CONFIGS))
     ap.add_argument("--mode", default="combined", choices=["truncate", "spamm", "combined"])
     ap.add_argument("--tau", type=float, default=1e-6)
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16_split", "fp16_scaled"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16_split", "fp16_scaled", "auto"],
+                    help="auto: the autotuner's choice per request (served stream only)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -63,15 +65,31 @@ def parse_args():
     ap.add_argument("--serve-inputs", type=int, default=8)
     ap.add_argument("--serve-nmax", type=int, default=32768)
     ap.add_argument("--serve-batch", type=int, default=32)
+    ap.add_argument("--serve-alpha", type=float, nargs=2, default=[0.8, 1.2])
+    ap.add_argument("--no-forms", action="store_true", help="skip the tensor-form comparison in the bench line")
+    ap.add_argument("--form-steps", type=int, default=5)
     ap.add_argument("--model-problem", action="store_true", help="the paper's 1-D model problem sweep")
     ap.add_argument("--sweep", action="store_true", help="the three methods at equal accuracy on --config")
     ap.add_argument("--sweep-taus", type=float, nargs="+", default=[1e-4, 1e-6, 1e-8])
     ap.add_argument("--sigmas", type=float, nargs="+", default=[1e-2, 1e-4, 1e-6])
+    ap.add_argument("--sweep-precs", nargs="+", default=["fp64", "bf16_split", "fp16_scaled"])
     ap.add_argument("--block-sparse", action="store_true", help="random block-sparse sweep over fill-in")
     ap.add_argument("--bsp-n", type=int, default=2048)
     ap.add_argument("--bsp-bs", type=int, nargs="+", default=[32, 64])
     ap.add_argument("--bsp-fills", type=float, nargs="+", default=[0.05, 0.1, 0.2, 0.3, 0.5, 0.7, 0.9])
     ap.add_argument("--bsp-repeats", type=int, default=20)
+    ap.add_argument("--chain", action="store_true", help="repeated squaring chain")
+    ap.add_argument("--chain-n", type=int, default=262144)
+    ap.add_argument("--chain-alpha", type=float, default=1.0)
+    ap.add_argument("--chain-tau", type=float, default=1e-6)
+    ap.add_argument("--chain-steps", type=int, default=20)
+    ap.add_argument("--chain-precs", nargs="+", default=["fp64", "fp16_scaled"])
+    ap.add_argument("--sp2", action="store_true", help="SP2 purification chain")
+    ap.add_argument("--sp2-n", type=int, default=8192)
+    ap.add_argument("--sp2-alpha", type=float, default=1.0)
+    ap.add_argument("--sp2-tau", type=float, default=1e-6)
+    ap.add_argument("--sp2-iters", type=int, default=40)
+    ap.add_argument("--sp2-tol", type=float, default=1e-6)
     ap.add_argument("--mp-n", type=int, default=40000)
     ap.add_argument("--mp-bs", type=int, nargs="+", default=[64])
     ap.add_argument("--mp-sigma", type=float, default=1e-6)
@@ -205,7 +223,10 @@ def run_served(args):
     """Continuous batching: a Poisson stream of combined-method requests on
     resident 3-D lattice matrices (n log-uniform, alpha uniform, tau from
     {1e-4, 1e-6, 1e-8}), first all at once (saturated capacity), then at 0.9 x
-    that rate; p50/p99 latency from arrival to completion."""
+    that rate; p50/p99 latency from arrival to completion.  --prec auto: each
+    request's precision form and leaf size from the autotuner (a function of
+    its n, alpha and tau only); otherwise every request in --prec with 64 x 64
+    leaves."""
     import math
     import random
 
@@ -215,21 +236,28 @@ def run_served(args):
     import synth
     __graft_entry__.build()
     from paper_1906_08148_gb300 import spamm as S
+    from paper_1906_08148_gb300.autotune import Autotuner, Choice
     from paper_1906_08148_gb300.serving import Request, Server
 
     rng = random.Random(7)
     data = S.Context(0)
     taus = [1e-4, 1e-6, 1e-8]
-    pool = []
+    tuner = Autotuner() if args.prec == "auto" else None
+    specs = []
     for i in range(args.serve_inputs):
         n = int(2 ** rng.uniform(math.log2(4096), math.log2(args.serve_nmax))) // 64 * 64
-        alpha = rng.uniform(0.8, 1.2)
-        # resident inputs truncated at the smallest tau of the stream while generating
-        # (exact for the combined method: truncation is per leaf)
-        A = S.spamm_generate(data, synth.lattice_3d(n, alpha=alpha, seed=2 * i + 1), 64, min(taus))
-        B = S.spamm_generate(data, synth.lattice_3d(n, alpha=alpha, seed=2 * i + 2), 64, min(taus))
-        pool.append((n, alpha, A, B))
-    torch.cuda.synchronize()
+        alpha = rng.uniform(args.serve_alpha[0], args.serve_alpha[1])
+        specs.append((n, alpha))
+    inputs = {}
+
+    def resident(i, bs):
+        # inputs truncated at the smallest tau of the stream while generating
+        # (exact for the combined method: the block rule is per leaf)
+        if (i, bs) not in inputs:
+            n, alpha = specs[i]
+            inputs[(i, bs)] = (S.spamm_generate(data, synth.lattice_3d(n, alpha=alpha, seed=2 * i + 1), bs, min(taus)),
+                               S.spamm_generate(data, synth.lattice_3d(n, alpha=alpha, seed=2 * i + 2), bs, min(taus)))
+        return inputs[(i, bs)]
 
     def stream(rate):
         reqs, t = [], 0.0
@@ -237,8 +265,12 @@ def run_served(args):
         for _ in range(args.serve_requests):
             if rate:
                 t += r2.expovariate(rate)
-            n, alpha, A, B = pool[r2.randrange(len(pool))]
-            reqs.append(Request(A, B, tau=r2.choice(taus), mode="combined", prec=args.prec, arrival=t))
+            i = r2.randrange(len(specs))
+            tau = r2.choice(taus)
+            n, alpha = specs[i]
+            ch = tuner.choose(n, alpha, tau) if tuner else Choice(args.prec, 64)
+            A, B = resident(i, ch.bs)
+            reqs.append(Request(A, B, tau=tau, mode="combined", prec=ch.prec, arrival=t))
         return reqs
 
     def serve(reqs):
@@ -246,55 +278,66 @@ def run_served(args):
         srv.start()
         ids = [srv.submit(r) for r in reqs]
         for i in ids:
-            srv.wait(i, timeout=600)
+            srv.wait(i, timeout=3600)
         srv.stop()
         return srv.summary()
 
-    serve(stream(0.0)[: min(8, args.serve_requests)])  # warm-up
+    first = stream(0.0)
+    torch.cuda.synchronize()
+    forms = {}
+    for r in first:
+        k = f"{r.prec}/{r.A.info()['bs']}"
+        forms[k] = forms.get(k, 0) + 1
+    serve(first[: min(8, args.serve_requests)])  # warm-up
     sat = serve(stream(0.0))
     cap = sat["requests_per_s"]
     load = serve(stream(0.9 * cap))
     line = {"metric": "requests/s (served stream)", "value": load["requests_per_s"], "unit": "req/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": args.prec, "data": "synthetic",
             "config": {"workload": "served_stream", "requests": args.serve_requests, "inputs": args.serve_inputs,
-                       "n_range": [4096, args.serve_nmax], "alpha": [0.8, 1.2], "tau": taus, "method": "combined",
-                       "bs": 64, "arrivals": "Poisson at 0.9 x saturated capacity"},
+                       "n_range": [4096, args.serve_nmax], "alpha": list(args.serve_alpha), "tau": taus,
+                       "method": "combined", "forms": forms, "arrivals": "Poisson at 0.9 x saturated capacity"},
             "saturated": sat, "loaded": load, "p50_s": load["p50_s"], "p99_s": load["p99_s"],
             "kept_gflops": load["kept_gflops"]}
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------ methods at equal accuracy
-def tau_sweep(S, ctx, GA, GB, taus, sigmas, prec="fp64"):
+def tau_sweep(S, ctx, GA, GB, taus, sigmas, precs=("fp64",)):
     """The paper's comparison of the three methods (Section 5.3): multiply with
     each method over a tau grid, measure ||AB - C||_F against the exact product
     (tau = 0, no truncation, FP64), and for each target accuracy sigma take,
-    per method, the largest tau whose error is <= sigma.  Times are wall time
-    of the synchronous multiply (truncation + task list + leaf GEMM + C norms)."""
+    per method (and precision form), the largest tau whose error is <= sigma.
+    Times are wall time of the synchronous multiply (truncation + task list +
+    operand prep + leaf products + C norms)."""
     X, xs = S.spamm_multiply(ctx, GA, GB, 0.0, "spamm", "fp64", stats=True)
     exact = {"n_kept": xs["n_kept"], "frob": S.spamm_frob_norm(ctx, X), "ms_gemm": xs["ms_gemm"]}
     rows = {}
-    for mode in ("truncate", "spamm", "combined"):
-        rows[mode] = []
-        for tau in taus:
-            t0 = time.perf_counter()
-            C, st = S.spamm_multiply(ctx, GA, GB, tau, mode, prec, stats=True)
-            ms = 1e3 * (time.perf_counter() - t0)
-            err = S.spamm_error(ctx, X, C)
-            rows[mode].append({"tau": tau, "n_kept": st["n_kept"], "error": err, "ms": ms,
-                               "ms_gemm": st["ms_gemm"], "gflops": st["kept_flops"] / ms / 1e6,
-                               "mults_per_s": st["n_kept"] / ms * 1e3})
-            C.close()
+    for prec in precs:
+        S.spamm_multiply(ctx, GA, GB, max(taus), "spamm", prec).close()  # first launch of this form, untimed
+        for mode in ("truncate", "spamm", "combined"):
+            key = mode if prec == "fp64" else f"{mode}/{prec}"
+            rows[key] = []
+            for tau in taus:
+                t0 = time.perf_counter()
+                C, st = S.spamm_multiply(ctx, GA, GB, tau, mode, prec, stats=True)
+                ms = 1e3 * (time.perf_counter() - t0)
+                err = S.spamm_error(ctx, X, C)
+                rows[key].append({"tau": tau, "n_kept": st["n_kept"], "error": err, "ms": ms,
+                                  "ms_gemm": st["ms_gemm"], "gflops": st["kept_flops"] / ms / 1e6,
+                                  "mults_per_s": st["n_kept"] / ms * 1e3})
+                C.close()
     X.close()
     chosen = {}
     for sigma in sigmas:
         pick = {}
-        for mode, rs in rows.items():
+        for key, rs in rows.items():
             ok = [r for r in rs if r["error"] <= sigma]
-            pick[mode] = max(ok, key=lambda r: r["tau"]) if ok else None
-        base = pick["truncate"]
+            pick[key] = max(ok, key=lambda r: r["tau"]) if ok else None
+        base = pick.get("truncate")
         chosen["%g" % sigma] = {
             m: (c and {"tau": c["tau"], "n_kept": c["n_kept"], "error": c["error"], "ms": c["ms"],
+                       "gflops": c["gflops"], "mults_per_s": c["mults_per_s"],
                        "gemm_vs_truncmul": c["n_kept"] / base["n_kept"] if base else None,
                        "time_vs_truncmul": c["ms"] / base["ms"] if base else None})
             for m, c in pick.items()}
@@ -314,10 +357,10 @@ def run_sweep(args, cfg):
     pb = synth.DecayParams(n=cfg["n"], kind=cfg["kind"], alpha=cfg["alpha"], seed=cfg["seeds"][1])
     GA = S.spamm_generate(ctx, pa, cfg["bs"])
     GB = GA if pb == pa else S.spamm_generate(ctx, pb, cfg["bs"])
-    res = tau_sweep(S, ctx, GA, GB, args.sweep_taus, args.sigmas, args.prec)
+    res = tau_sweep(S, ctx, GA, GB, args.sweep_taus, args.sigmas, args.sweep_precs)
     print(json.dumps({"metric": "methods at equal accuracy", "unit": "ms", "data": "synthetic",
                       "config": {"workload": args.config, "desc": cfg["desc"], "bs": cfg["bs"],
-                                 "taus": args.sweep_taus, "sigmas": args.sigmas, "precision": args.prec},
+                                 "taus": args.sweep_taus, "sigmas": args.sigmas, "precisions": args.sweep_precs},
                       **res}), flush=True)
     for m in {id(GA): GA, id(GB): GB}.values():
         m.close()
@@ -392,6 +435,93 @@ def run_block_sparse(args):
                       "rows": rows}), flush=True)
 
 
+# ------------------------------------------------------ purification chains
+def run_chain(args):
+    """Repeated squaring X <- X X with the state resident on the device (the
+    purification-style chain): 3-D lattice decay matrix scaled by an upper
+    bound of its spectral norm (so ||X0||_2 <= 1), combined method, 64 x 64
+    leaves, `--chain-steps` squarings, FP64 leaves and a tensor-core form.
+    Squaring a matrix of spectral radius < 1 drives it to 0, so the work per
+    step shrinks as leaves fall below tau; that is reported, not hidden.
+    Per form: total and per-step time, kept products and ||X||_F; and the
+    relative difference of the two forms' final X."""
+    import torch
+
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_1906_08148_gb300 import chain
+    from paper_1906_08148_gb300 import spamm as S
+
+    ctx = S.Context(0)
+    p = synth.lattice_3d(args.chain_n, alpha=args.chain_alpha, seed=1)
+    bound = synth.spectral_bound(p)
+    ps = synth.DecayParams(n=p.n, kind=p.kind, alpha=p.alpha, seed=p.seed, c=1.0 / bound)
+    out = {"metric": "purification-style squaring chain", "unit": "s", "data": "synthetic",
+           "config": {"workload": "square_chain", "n": args.chain_n, "alpha": args.chain_alpha, "bs": 64,
+                      "tau": args.chain_tau, "method": "combined", "steps": args.chain_steps,
+                      "scale": "1 / spectral bound %.6g" % bound, "inputs": "generated with block truncation at tau"},
+           "forms": {}}
+    finals = {}
+    for prec in args.chain_precs:
+        X0 = S.spamm_generate(ctx, ps, 64, args.chain_tau)
+        nl0 = X0.info()["nleaves"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        X, hist = chain.square_chain(ctx, X0, args.chain_steps, args.chain_tau, "combined", prec, keep_input=False)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        flops = sum(h["kept_flops"] for h in hist)
+        out["forms"][prec] = {"seconds": secs, "x0_leaves": nl0, "kept_flops": flops,
+                              "kept_gflops": flops / secs / 1e9, "steps": hist}
+        finals[prec] = X
+    if "fp64" in finals:
+        ref = S.spamm_frob_norm(ctx, finals["fp64"])
+        for prec, X in finals.items():
+            if prec != "fp64":
+                e = S.spamm_error(ctx, finals["fp64"], X)
+                out["forms"][prec]["diff_vs_fp64"] = e / ref if ref > 0 else e
+    for X in finals.values():
+        X.close()
+    print(json.dumps(out), flush=True)
+
+
+def run_sp2(args):
+    """SP2 purification (second-order spectral projection) of a 3-D lattice
+    decay matrix F to half filling: X0 = (b I - F) / (2 b), b an upper bound
+    of ||F||_2, then X <- X^2 or 2X - X^2 by the trace rule, every product an
+    approximate multiply; per iteration the branch, trace, ||X - X^2||_F,
+    kept products and time, for FP64 leaves and a tensor-core form."""
+    import torch
+
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_1906_08148_gb300 import chain
+    from paper_1906_08148_gb300 import spamm as S
+
+    ctx = S.Context(0)
+    p = synth.lattice_3d(args.sp2_n, alpha=args.sp2_alpha, seed=1)
+    bound = synth.spectral_bound(p)
+    out = {"metric": "SP2 purification chain", "unit": "s", "data": "synthetic",
+           "config": {"workload": "sp2", "n": args.sp2_n, "alpha": args.sp2_alpha, "bs": 64, "tau": args.sp2_tau,
+                      "method": "combined", "n_occ": args.sp2_n // 2, "iterations": args.sp2_iters,
+                      "bound": bound}, "forms": {}}
+    for prec in args.chain_precs:
+        F = S.spamm_generate(ctx, p, 64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        X, hist = chain.sp2(ctx, F, args.sp2_n // 2, bound, args.sp2_tau, "combined", prec, args.sp2_iters,
+                            tol=args.sp2_tol)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        out["forms"][prec] = {"seconds": secs, "iterations": len(hist), "final_trace": S.spamm_trace(ctx, X),
+                              "final_leaves": X.info()["nleaves"], "history": hist}
+        X.close()
+        F.close()
+    print(json.dumps(out), flush=True)
+
+
 # ---------------------------------------------------------- multi-rank timing
 def aggregate_ranks(ms_local, flops_local, kept_local, dist=None):
     """Whole-job numbers over independent replicas (one per GPU): the timed
@@ -415,15 +545,19 @@ def main():
     if args.impl == "reference":
         return run_reference(args, cfg)
     if args.serve:
-        if args.prec == "fp64":
-            args.prec = "bf16_split"
         return run_served(args)
+    if args.prec == "auto":
+        raise SystemExit("--prec auto applies to the served stream (--serve)")
     if args.model_problem:
         return run_model_problem(args)
     if args.sweep:
         return run_sweep(args, cfg)
     if args.block_sparse:
         return run_block_sparse(args)
+    if args.chain:
+        return run_chain(args)
+    if args.sp2:
+        return run_sp2(args)
 
     import numpy as np
     import torch
@@ -487,6 +621,10 @@ def main():
     if not args.no_e2e and rank == 0:
         e2e = run_e2e(S, ctx, GA, GB, args, bs, torch, np)
 
+    forms = None
+    if not args.no_forms and rank == 0 and args.prec == "fp64":
+        forms = precision_forms(S, ctx, GA, GB, args, stream, torch)
+
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         cpu = cpu_baseline(cfg, args.mode, args.tau, args.cpu_seconds)
@@ -506,14 +644,49 @@ def main():
             "n_kept": kept, "n_steps": stats[-1]["n_steps"], "n_c_leaves": stats[-1]["n_c_leaves"], "n_borderline": stats[-1]["n_borderline"],
             "n_a_leaves": stats[-1]["n_a_leaves"], "n_b_leaves": stats[-1]["n_b_leaves"],
             "c_frob": nrm, "phase_ms": phases, "roofline": roof,
-            "gpu_launches": None, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": None, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "precision_forms": forms,
         }
         line["gpu_launches"] = int(sum(s["n_launches"] for s in stats))
+        if forms:
+            for f in forms.values():
+                f["vs_fp64"] = f["kept_gflops"] / value if value else None
         print(json.dumps(line), flush=True)
     for m in {id(GA): GA, id(GB): GB}.values():
         m.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def precision_forms(S, ctx, GA, GB, args, stream, torch):
+    """The same multiply in the tensor-core forms, after the timed FP64 steps:
+    kept-block GFLOP/s over `--form-steps` steps (CUDA events on the bench
+    stream) and the form's deviation from the FP64 product of the same tau,
+    ||C_form - C_fp64||_F / ||C_fp64||_F (the method's own truncation error
+    at this tau, against the exact product, is what --sweep measures)."""
+    ref = S.spamm_multiply(ctx, GA, GB, args.tau, args.mode, "fp64")
+    nref = S.spamm_frob_norm(ctx, ref)
+    out = {}
+    for prec in ("bf16_split", "fp16_scaled"):
+        C = S.spamm_multiply(ctx, GA, GB, args.tau, args.mode, prec)  # untimed first run of the form
+        dev = S.spamm_error(ctx, ref, C) / nref
+        C.close()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flops, gemm = 0.0, 0.0
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.form_steps):
+            C, st = S.spamm_multiply(ctx, GA, GB, args.tau, args.mode, prec, stats=True)
+            C.close()
+            flops += st["kept_flops"]
+            gemm += st["ms_gemm"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.form_steps
+        out[prec] = {"kept_gflops": flops / args.form_steps / ms / 1e6, "ms_per_step": ms,
+                     "ms_gemm": gemm / args.form_steps, "rel_dev_vs_fp64": dev,
+                     "vs_fp64": None}
+    ref.close()
+    return out
 
 
 def roofline(prec, bs, kept, ms_gemm, executed_flops):

@@ -77,8 +77,16 @@ typedef enum { SPAMM_MODE_TRUNCATE = 0, SPAMM_MODE_SPAMM = 1, SPAMM_MODE_COMBINE
 
 /* Input truncation rule.  BLOCK_FROB: a leaf is dropped iff its Frobenius
  * norm is < tau.  ELEMENT: a_ij -> 0 iff |a_ij| < tau (Theorem 1, equation
- * "truncated matrices"), then leaves left without a non-zero are dropped. */
-typedef enum { SPAMM_TRUNC_BLOCK_FROB = 0, SPAMM_TRUNC_ELEMENT = 1 } spamm_trunc_rule;
+ * "truncated matrices"), then leaves left without a non-zero are dropped.
+ * ERROR_CONTROL: tau is an error budget: the leaves with the smallest squared
+ * norms (ties in Morton order) are dropped as long as the sum of their squared
+ * norms, added in that order, stays <= tau^2, so ||A - A~||_F <= tau (the
+ * error-controlled truncation Section 1 cites, applied to whole leaves). */
+typedef enum {
+  SPAMM_TRUNC_BLOCK_FROB = 0,
+  SPAMM_TRUNC_ELEMENT = 1,
+  SPAMM_TRUNC_ERROR_CONTROL = 2
+} spamm_trunc_rule;
 
 /* Arithmetic of the leaf products.  FP64: plain double precision on the GPU.
  * BF16_SPLIT: each operand split into three bfloat16 terms, the six products
@@ -91,11 +99,13 @@ typedef enum { SPAMM_PREC_FP64 = 0, SPAMM_PREC_BF16_SPLIT = 1, SPAMM_PREC_FP16_S
  *   a_ij = c u_ij exp(-alpha d(i,j)),  u_ij ~ U[-1,1) symmetric, seeded;
  *   |a_ij| < cutoff -> 0.   kind 0: d = |i - j| (the model problem of
  * Section 5.3); kind 1: d = Euclidean distance between the points of a 3-D
- * unit lattice in Morton order (stand-in for the systems of Section 5.4). */
+ * unit lattice in Morton order (stand-in for the systems of Section 5.4).
+ * law 1: algebraic decay a_ij = c u_ij / (1 + d(i,j))^p, p = alpha rounded
+ * down to an integer >= 1 (the other decay class Section 1 mentions). */
 typedef struct {
   int64_t n;
   int32_t kind;
-  int32_t reserved;
+  int32_t law; /* 0: exponential, 1: algebraic */
   double alpha;
   double c;
   double cutoff;

@@ -209,7 +209,35 @@ def truncate_element(M: LeafMatrix, tau: float) -> LeafMatrix:
     return from_leaves(M.n, M.bs, M.bi, M.bj, data)
 
 
+def morton(bi, bj) -> np.ndarray:
+    """Morton code of leaf (row, col): bits interleaved, the row bit above the
+    column bit (the order in which quadtree leaves are enumerated)."""
+    code = np.zeros(len(bi), dtype=np.uint64)
+    r = np.asarray(bi, dtype=np.uint64)
+    c = np.asarray(bj, dtype=np.uint64)
+    for b in range(16):
+        code |= ((r >> np.uint64(b)) & np.uint64(1)) << np.uint64(2 * b + 1)
+        code |= ((c >> np.uint64(b)) & np.uint64(1)) << np.uint64(2 * b)
+    return code
+
+
+def truncate_error_controlled(M: LeafMatrix, tau: float) -> LeafMatrix:
+    """Error-controlled rule (tau is an error budget; Section 1 cites this
+    kind of truncation): visit the leaves by ascending squared norm (equal
+    norms in Morton order), add their squared norms one by one, and drop every
+    leaf whose running sum stays <= tau^2; so ||M - M~||_F <= tau and no more
+    leaves can be dropped within the budget."""
+    order = np.lexsort((morton(M.bi, M.bj), M.sq))
+    run = np.cumsum(M.sq[order])
+    k = int(np.sum(run <= tau * tau))
+    keep = np.ones(M.m, dtype=bool)
+    keep[order[:k]] = False
+    return LeafMatrix(M.n, M.bs, M.bi[keep], M.bj[keep], M.data[keep], M.sq[keep])
+
+
 def truncate(M: LeafMatrix, tau: float, rule: str = "block") -> LeafMatrix:
+    if rule == "error":
+        return truncate_error_controlled(M, tau)
     return truncate_block(M, tau) if rule == "block" else truncate_element(M, tau)
 
 

@@ -55,11 +55,22 @@ void need(bool ok, const char* what) {
 void check_bs(int bs) { need(bs == 32 || bs == 64 || bs == 128, "bs must be 32, 64 or 128"); }
 void check_tau(double tau) { need(std::isfinite(tau) && tau >= 0.0, "tau must be finite and >= 0"); }
 void check_rule(spamm_trunc_rule r) {
-  need(r == SPAMM_TRUNC_BLOCK_FROB || r == SPAMM_TRUNC_ELEMENT, "unknown truncation rule");
+  need(r == SPAMM_TRUNC_BLOCK_FROB || r == SPAMM_TRUNC_ELEMENT || r == SPAMM_TRUNC_ERROR_CONTROL,
+       "unknown truncation rule");
 }
 void check_n(int64_t n, int bs) {
   need(n > 0, "n must be > 0");
   need(levels_for(n, bs) <= 16, "n / bs exceeds 65536 leaves per dimension");
+}
+
+// The builders truncate per leaf while building (block and element rules); the
+// error-controlled rule needs every leaf's norm first, so it runs afterwards.
+double build_tau(double tau, spamm_trunc_rule r) { return r == SPAMM_TRUNC_ERROR_CONTROL ? 0.0 : tau; }
+spamm_trunc_rule build_rule(spamm_trunc_rule r) { return r == SPAMM_TRUNC_ERROR_CONTROL ? SPAMM_TRUNC_BLOCK_FROB : r; }
+spamm_mat after_build(spamm_mat m, double tau, spamm_trunc_rule r) {
+  if (r != SPAMM_TRUNC_ERROR_CONTROL || tau <= 0.0) return m;
+  std::unique_ptr<spamm_mat_s> full(m);
+  return truncate_error_controlled(m, tau);
 }
 
 spamm_mat registered(spamm_mat m) {
@@ -175,7 +186,8 @@ spamm_status spamm_from_dense(spamm_ctx ctx, int64_t n, const double* a, int64_t
     check_tau(tau);
     check_rule(rule);
     need(a != nullptr && lda >= n, "a must be non-NULL with lda >= n");
-    spamm_mat m = build_from_dense(ctx, n, a, lda, on_device, bs, tau, rule);
+    spamm_mat m = after_build(build_from_dense(ctx, n, a, lda, on_device, bs, build_tau(tau, rule), build_rule(rule)),
+                              tau, rule);
     *out = registered(m);
   });
 }
@@ -192,7 +204,9 @@ spamm_status spamm_from_blocks(spamm_ctx ctx, int64_t n, int bs, int64_t nblocks
     check_rule(rule);
     need(nblocks >= 0, "nblocks must be >= 0");
     need(nblocks == 0 || (bi && bj && payload), "bi, bj and payload must be non-NULL");
-    spamm_mat m = build_from_blocks(ctx, n, bs, nblocks, bi, bj, payload, on_device, tau, rule);
+    spamm_mat m = after_build(
+        build_from_blocks(ctx, n, bs, nblocks, bi, bj, payload, on_device, build_tau(tau, rule), build_rule(rule)), tau,
+        rule);
     *out = registered(m);
   });
 }
@@ -209,7 +223,8 @@ spamm_status spamm_from_coo(spamm_ctx ctx, int64_t n, int64_t nnz, const int64_t
     check_rule(rule);
     need(nnz >= 0, "nnz must be >= 0");
     need(nnz == 0 || (row && col && val), "row, col and val must be non-NULL");
-    spamm_mat m = build_from_coo(ctx, n, nnz, row, col, val, on_device, bs, tau, rule);
+    spamm_mat m = after_build(
+        build_from_coo(ctx, n, nnz, row, col, val, on_device, bs, build_tau(tau, rule), build_rule(rule)), tau, rule);
     *out = registered(m);
   });
 }
@@ -226,7 +241,7 @@ spamm_status spamm_generate(spamm_ctx ctx, const spamm_gen_params* params, int b
     need(params->kind == 0 || params->kind == 1, "kind must be 0 (1-D) or 1 (3-D lattice)");
     need(std::isfinite(params->alpha) && params->alpha >= 0.0, "alpha must be finite and >= 0");
     need(std::isfinite(params->c) && std::isfinite(params->cutoff) && params->cutoff >= 0.0, "bad c or cutoff");
-    spamm_mat m = build_generated(ctx, params, bs, tau, rule);
+    spamm_mat m = after_build(build_generated(ctx, params, bs, build_tau(tau, rule), build_rule(rule)), tau, rule);
     *out = registered(m);
   });
 }
@@ -237,7 +252,9 @@ spamm_status spamm_truncate(spamm_ctx ctx, spamm_mat in, double tau, spamm_trunc
   return guarded(ctx, [&] {
     check_tau(tau);
     check_rule(rule);
-    spamm_mat m = rule == SPAMM_TRUNC_BLOCK_FROB ? truncate_block(in, tau) : truncate_element(in, tau);
+    spamm_mat m = rule == SPAMM_TRUNC_BLOCK_FROB ? truncate_block(in, tau)
+                  : rule == SPAMM_TRUNC_ELEMENT  ? truncate_element(in, tau)
+                                                 : truncate_error_controlled(in, tau);
     sync_and_check(ctx);
     *out = registered(m);
   });

@@ -88,6 +88,8 @@ inline int levels_for(int64_t n, int bs) {
 // ---- primitives (prims.cu) ----
 // Exclusive prefix sum of n uint64 values; total written to d_total (device) if not null.
 void scan_exclusive_u64(spamm_ctx ctx, const uint64_t* in, uint64_t* out, int64_t n, uint64_t* d_total);
+// Inclusive prefix sum of n doubles (fixed tiling: the same rounding on every run).
+void scan_inclusive_f64(spamm_ctx ctx, const double* in, double* out, int64_t n);
 // Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the key.
 void radix_sort_pairs(spamm_ctx ctx, uint64_t* keys, int64_t* vals, int64_t n, int bits);
 // Copy a device scalar to the host (synchronises the context stream).
@@ -152,6 +154,7 @@ void set_leaves_compacted(spamm_mat m, int64_t ncand, const uint32_t* code, cons
                           const uint8_t* keep);
 spamm_mat truncate_block(spamm_mat in, double tau, spamm_ctx on = nullptr);  // work on `on` (default: in's context)
 spamm_mat truncate_element(spamm_mat in, double tau);
+spamm_mat truncate_error_controlled(spamm_mat in, double tau, spamm_ctx on = nullptr);
 void leaf_sqnorms(spamm_ctx ctx, const double* pool, const int64_t* slot, int64_t nleaves, int bs, double* sq,
                   uint8_t* nonzero, int check_finite);
 double error_fro(spamm_mat X, spamm_mat Y);

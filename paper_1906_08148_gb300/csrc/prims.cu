@@ -83,74 +83,85 @@ constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 // Exclusive scan across the 256 threads of a block; *total = block sum.
-__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* total) {
-  __shared__ uint64_t warp_tot[kScanThreads / 32];
+// T = uint64_t (exact) or double (fixed tiling, so the rounding is the same
+// on every run).
+template <class T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* total) {
+  __shared__ T warp_tot[kScanThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint64_t x = v;
+  T x = v;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
-    uint64_t y = __shfl_up_sync(0xffffffffu, x, off);
+    T y = __shfl_up_sync(0xffffffffu, x, off);
     if (lane >= off) x += y;
   }
   if (lane == 31) warp_tot[warp] = x;
   __syncthreads();
-  uint64_t before = 0, all = 0;
+  T before = 0, all = 0;
 #pragma unroll
   for (int w = 0; w < kScanThreads / 32; ++w) {
-    uint64_t t = warp_tot[w];
+    T t = warp_tot[w];
     if (w < warp) before += t;
     all += t;
   }
   __syncthreads();
   *total = all;
-  return before + x - v;
+  const T prev = __shfl_up_sync(0xffffffffu, x, 1);  // the previous lane's inclusive sum
+  return lane == 0 ? before : before + prev;
 }
 
-__global__ void scan_reduce_kernel(const uint64_t* __restrict__ in, int64_t n, uint64_t* __restrict__ bsum) {
+template <class T>
+__global__ void scan_reduce_kernel(const T* __restrict__ in, int64_t n, T* __restrict__ bsum) {
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
-  uint64_t s = 0;
+  T s = 0;
   for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
     int64_t q = base + i;
     if (q < n) s += in[q];
   }
-  uint64_t total;
+  T total;
   block_exclusive_scan(s, &total);
   if (threadIdx.x == 0) bsum[blockIdx.x] = total;
 }
 
-__global__ void scan_blocksums_kernel(uint64_t* bsum, int64_t nblocks, uint64_t* d_total) {
-  uint64_t carry = 0;
+template <class T>
+__global__ void scan_blocksums_kernel(T* bsum, int64_t nblocks, T* d_total) {
+  T carry = 0;
   for (int64_t base = 0; base < nblocks; base += kScanThreads) {
     int64_t q = base + threadIdx.x;
-    uint64_t v = q < nblocks ? bsum[q] : 0;
-    uint64_t total;
-    uint64_t ex = block_exclusive_scan(v, &total);
+    T v = q < nblocks ? bsum[q] : 0;
+    T total;
+    T ex = block_exclusive_scan(v, &total);
     if (q < nblocks) bsum[q] = carry + ex;
     carry += total;
   }
   if (threadIdx.x == 0 && d_total) *d_total = carry;
 }
 
-__global__ void scan_down_kernel(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n,
-                                 const uint64_t* __restrict__ bsum) {
-  __shared__ uint64_t tile[kScanTile];
+// inclusive = false: out[q] = sum of in[0 .. q-1]; true: sum of in[0 .. q]
+template <class T>
+__global__ void scan_down_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t n, const T* __restrict__ bsum,
+                                 bool inclusive) {
+  __shared__ T tile[kScanTile];
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
     int64_t q = base + i;
     tile[i] = q < n ? in[q] : 0;
   }
   __syncthreads();
-  uint64_t loc[kScanItems];
-  uint64_t s = 0;
+  T loc[kScanItems];
+  T s = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     loc[i] = s;
     s += tile[threadIdx.x * kScanItems + i];
   }
-  uint64_t total;
-  uint64_t ex = block_exclusive_scan(s, &total) + bsum[blockIdx.x];
+  T total;
+  T ex = block_exclusive_scan(s, &total) + bsum[blockIdx.x];
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) tile[threadIdx.x * kScanItems + i] = ex + loc[i];
+  for (int i = 0; i < kScanItems; ++i) {
+    const T mine = tile[threadIdx.x * kScanItems + i];
+    tile[threadIdx.x * kScanItems + i] = inclusive ? (ex + loc[i]) + mine : ex + loc[i];
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
     int64_t q = base + i;
@@ -158,19 +169,28 @@ __global__ void scan_down_kernel(const uint64_t* __restrict__ in, uint64_t* __re
   }
 }
 
-void scan_exclusive_u64(spamm_ctx ctx, const uint64_t* in, uint64_t* out, int64_t n, uint64_t* d_total) {
+template <class T>
+static void scan_any(spamm_ctx ctx, const T* in, T* out, int64_t n, T* d_total, bool inclusive) {
   if (n <= 0) {
-    if (d_total) CK(cudaMemsetAsync(d_total, 0, sizeof(uint64_t), ctx->stream));
+    if (d_total) CK(cudaMemsetAsync(d_total, 0, sizeof(T), ctx->stream));
     return;
   }
   const int64_t nblocks = (n + kScanTile - 1) / kScanTile;
-  BufP bs = alloc_n<uint64_t>(ctx, nblocks);
-  scan_reduce_kernel<<<(unsigned)nblocks, kScanThreads, 0, ctx->stream>>>(in, n, P<uint64_t>(bs));
+  BufP bs = alloc_n<T>(ctx, nblocks);
+  scan_reduce_kernel<T><<<(unsigned)nblocks, kScanThreads, 0, ctx->stream>>>(in, n, P<T>(bs));
   CK_LAUNCH("scan_reduce_kernel");
-  scan_blocksums_kernel<<<1, kScanThreads, 0, ctx->stream>>>(P<uint64_t>(bs), nblocks, d_total);
+  scan_blocksums_kernel<T><<<1, kScanThreads, 0, ctx->stream>>>(P<T>(bs), nblocks, d_total);
   CK_LAUNCH("scan_blocksums_kernel");
-  scan_down_kernel<<<(unsigned)nblocks, kScanThreads, 0, ctx->stream>>>(in, out, n, P<uint64_t>(bs));
+  scan_down_kernel<T><<<(unsigned)nblocks, kScanThreads, 0, ctx->stream>>>(in, out, n, P<T>(bs), inclusive);
   CK_LAUNCH("scan_down_kernel");
+}
+
+void scan_exclusive_u64(spamm_ctx ctx, const uint64_t* in, uint64_t* out, int64_t n, uint64_t* d_total) {
+  scan_any<uint64_t>(ctx, in, out, n, d_total, false);
+}
+
+void scan_inclusive_f64(spamm_ctx ctx, const double* in, double* out, int64_t n) {
+  scan_any<double>(ctx, in, out, n, nullptr, true);
 }
 
 // ------------------------------------------------------------- radix sort
@@ -206,7 +226,7 @@ __global__ void radix_scatter_kernel(const uint64_t* __restrict__ kin, const int
 #pragma unroll
   for (int d = 0; d < kRadixBins; ++d) {
     uint64_t tot;
-    pre[d] = block_exclusive_scan(c[d], &tot) + offs[(int64_t)d * nblocks + blockIdx.x];
+    pre[d] = block_exclusive_scan<uint64_t>(c[d], &tot) + offs[(int64_t)d * nblocks + blockIdx.x];
   }
   for (int i = 0; i < kScanItems; ++i) {
     int64_t q = base + i;

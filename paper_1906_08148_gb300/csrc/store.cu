@@ -142,14 +142,19 @@ void set_leaves_compacted(spamm_mat m, int64_t ncand, const uint32_t* code, cons
 // ||A^t||_F^2 = sum of the four children's squared norms, added in the fixed
 // order (0,0), (0,1), (1,0), (1,1); children are found from the sorted codes
 // of the level below (parent code = child code >> 2).
-__global__ void parent_flags_kernel(const uint32_t* __restrict__ code, int64_t n, uint64_t* __restrict__ flags) {
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
-    flags[q] = (q == 0 || (code[q] >> 2) != (code[q - 1] >> 2)) ? 1u : 0u;
+// The level below holds *dn nodes (the arrays have room for ncap); flags past
+// *dn are 0 so that a scan over the capacity gives the parent count.
+__global__ void parent_flags_kernel(const uint32_t* __restrict__ code, int64_t ncap, const uint64_t* __restrict__ dn,
+                                    uint64_t* __restrict__ flags) {
+  const int64_t n = (int64_t)*dn;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ncap; q += (int64_t)gridDim.x * blockDim.x)
+    flags[q] = q < n && (q == 0 || (code[q] >> 2) != (code[q - 1] >> 2)) ? 1u : 0u;
 }
 
-__global__ void parent_link_kernel(const uint32_t* __restrict__ code, int64_t n, const uint64_t* __restrict__ flags,
-                                   const uint64_t* __restrict__ excl, uint32_t* __restrict__ pcode,
-                                   int4* __restrict__ pchild) {
+__global__ void parent_link_kernel(const uint32_t* __restrict__ code, const uint64_t* __restrict__ dn,
+                                   const uint64_t* __restrict__ flags, const uint64_t* __restrict__ excl,
+                                   uint32_t* __restrict__ pcode, int4* __restrict__ pchild) {
+  const int64_t n = (int64_t)*dn;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
     int64_t p = (int64_t)(excl[q] + flags[q]) - 1;
     uint32_t c = code[q];
@@ -171,33 +176,53 @@ __global__ void parent_sum_kernel(int64_t np, const int4* __restrict__ child, co
   }
 }
 
+// Node counts stay on the device while the levels are built (each level's
+// arrays sized by an upper bound: no more parents than children, and no more
+// than the level's grid); one read-back at the end gives the exact counts.
 void build_skeleton(spamm_mat m) {
   spamm_ctx ctx = m->ctx;
-  for (int t = m->L; t >= 1; --t) {
+  const int L = m->L;
+  if (L == 0) return;
+  BufP dcnt = alloc_n<uint64_t>(ctx, L + 1);
+  uint64_t* d = P<uint64_t>(dcnt);
+  const uint64_t nleaf = (uint64_t)m->lv[L].count;
+  CK(cudaMemcpyAsync(d + L, &nleaf, sizeof(uint64_t), cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<BufP> keep;  // scan buffers live until the counts are read
+  int64_t ncap = m->lv[L].count;
+  int top = L;  // lowest level index built
+  for (int t = L; t >= 1 && ncap > 0; --t) {
     Level& ch = m->lv[t];
     Level& pa = m->lv[t - 1];
-    const int64_t n = ch.count;
-    if (n == 0) {
-      pa.count = 0;
+    const int64_t grid_nodes = (int64_t)1 << (2 * (t - 1));
+    const int64_t pcap = ncap < grid_nodes ? ncap : grid_nodes;
+    BufP flags = alloc_n<uint64_t>(ctx, ncap), excl = alloc_n<uint64_t>(ctx, ncap);
+    parent_flags_kernel<<<grid_for(ctx, ncap, kThreads), kThreads, 0, ctx->stream>>>(P<uint32_t>(ch.code), ncap,
+                                                                                    d + t, P<uint64_t>(flags));
+    CK_LAUNCH("parent_flags_kernel");
+    scan_exclusive_u64(ctx, P<uint64_t>(flags), P<uint64_t>(excl), ncap, d + t - 1);
+    pa.code = alloc_n<uint32_t>(ctx, pcap);
+    pa.sq.reset();
+    pa.child = alloc_n<int4>(ctx, pcap);
+    CK(cudaMemsetAsync(P<int4>(pa.child), 0xFF, pcap * sizeof(int4), ctx->stream));
+    parent_link_kernel<<<grid_for(ctx, ncap, kThreads), kThreads, 0, ctx->stream>>>(
+        P<uint32_t>(ch.code), d + t, P<uint64_t>(flags), P<uint64_t>(excl), P<uint32_t>(pa.code), P<int4>(pa.child));
+    CK_LAUNCH("parent_link_kernel");
+    keep.push_back(flags);
+    keep.push_back(excl);
+    ncap = pcap;
+    top = t - 1;
+  }
+  std::vector<uint64_t> h(L + 1, 0);
+  CK(cudaMemcpyAsync(h.data(), d, (L + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int t = 0; t < L; ++t) {
+    Level& pa = m->lv[t];
+    pa.count = t >= top ? (int64_t)h[t] : 0;
+    if (pa.count == 0) {
       pa.code.reset();
       pa.sq.reset();
       pa.child.reset();
-      continue;
     }
-    BufP flags = alloc_n<uint64_t>(ctx, n), excl = alloc_n<uint64_t>(ctx, n), tot = alloc_n<uint64_t>(ctx, 1);
-    parent_flags_kernel<<<grid_for(ctx, n, kThreads), kThreads, 0, ctx->stream>>>(P<uint32_t>(ch.code), n,
-                                                                                 P<uint64_t>(flags));
-    CK_LAUNCH("parent_flags_kernel");
-    scan_exclusive_u64(ctx, P<uint64_t>(flags), P<uint64_t>(excl), n, P<uint64_t>(tot));
-    const int64_t np = (int64_t)read_scalar<uint64_t>(ctx, P<uint64_t>(tot));
-    pa.count = np;
-    pa.code = alloc_n<uint32_t>(ctx, np);
-    pa.sq.reset();
-    pa.child = alloc_n<int4>(ctx, np);
-    CK(cudaMemsetAsync(P<int4>(pa.child), 0xFF, np * sizeof(int4), ctx->stream));
-    parent_link_kernel<<<grid_for(ctx, n, kThreads), kThreads, 0, ctx->stream>>>(
-        P<uint32_t>(ch.code), n, P<uint64_t>(flags), P<uint64_t>(excl), P<uint32_t>(pa.code), P<int4>(pa.child));
-    CK_LAUNCH("parent_link_kernel");
   }
 }
 
@@ -316,6 +341,67 @@ spamm_mat truncate_block(spamm_mat in, double tau, spamm_ctx on) {
     block_keep_kernel<<<grid_for(ctx, n, kThreads), kThreads, 0, ctx->stream>>>(P<double>(in->lv[in->L].sq), n, tau,
                                                                                P<uint8_t>(keep));
     CK_LAUNCH("block_keep_kernel");
+  }
+  set_leaves_compacted(out, n, P<uint32_t>(in->lv[in->L].code), P<double>(in->lv[in->L].sq), P<int64_t>(in->slot),
+                       P<uint8_t>(keep));
+  return out;
+}
+
+// Error-controlled rule: drop the smallest leaves (ascending squared norm,
+// ties in Morton order) as long as the sum of their squared norms, added in
+// that order, stays <= tau^2, so ||A - A~||_F <= tau.  The squared norms are
+// non-negative doubles, so their bit patterns sort like their values.
+__global__ void sq_sort_keys_kernel(const double* __restrict__ sq, int64_t n, uint64_t* __restrict__ keys,
+                                    int64_t* __restrict__ idx) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    keys[q] = (uint64_t)__double_as_longlong(sq[q]);
+    idx[q] = q;
+  }
+}
+
+__global__ void sorted_sq_kernel(const uint64_t* __restrict__ keys, int64_t n, double* __restrict__ v) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    v[q] = __longlong_as_double((long long)keys[q]);
+}
+
+__global__ void within_budget_kernel(const double* __restrict__ csum, int64_t n, double budget,
+                                     uint64_t* __restrict__ flag) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    flag[q] = csum[q] <= budget ? 1u : 0u;
+}
+
+// The first *ndrop leaves of the sorted order are dropped (a prefix, even if
+// rounding made the running sums non-monotone by an ulp).
+__global__ void drop_prefix_kernel(const int64_t* __restrict__ idx, int64_t n, const uint64_t* __restrict__ ndrop,
+                                   uint8_t* __restrict__ keep) {
+  const int64_t k = (int64_t)*ndrop;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    keep[idx[q]] = q >= k;
+}
+
+spamm_mat truncate_error_controlled(spamm_mat in, double tau, spamm_ctx on) {
+  spamm_ctx ctx = on ? on : in->ctx;
+  spamm_mat out = new_mat(ctx, in->n, in->bs);
+  out->pool = in->pool;
+  const int64_t n = in->nleaves;
+  BufP keep = alloc_n<uint8_t>(ctx, n);
+  if (n > 0) {
+    BufP keys = alloc_n<uint64_t>(ctx, n), idx = alloc_n<int64_t>(ctx, n), v = alloc_n<double>(ctx, n);
+    BufP csum = alloc_n<double>(ctx, n), flag = alloc_n<uint64_t>(ctx, n), pos = alloc_n<uint64_t>(ctx, n);
+    BufP ndrop = alloc_n<uint64_t>(ctx, 1);
+    const unsigned g = grid_for(ctx, n, kThreads);
+    sq_sort_keys_kernel<<<g, kThreads, 0, ctx->stream>>>(P<double>(in->lv[in->L].sq), n, P<uint64_t>(keys),
+                                                          P<int64_t>(idx));
+    CK_LAUNCH("sq_sort_keys_kernel");
+    radix_sort_pairs(ctx, P<uint64_t>(keys), P<int64_t>(idx), n, 64);  // stable: ties keep Morton order
+    sorted_sq_kernel<<<g, kThreads, 0, ctx->stream>>>(P<uint64_t>(keys), n, P<double>(v));
+    CK_LAUNCH("sorted_sq_kernel");
+    scan_inclusive_f64(ctx, P<double>(v), P<double>(csum), n);
+    within_budget_kernel<<<g, kThreads, 0, ctx->stream>>>(P<double>(csum), n, tau * tau, P<uint64_t>(flag));
+    CK_LAUNCH("within_budget_kernel");
+    scan_exclusive_u64(ctx, P<uint64_t>(flag), P<uint64_t>(pos), n, P<uint64_t>(ndrop));
+    drop_prefix_kernel<<<g, kThreads, 0, ctx->stream>>>(P<int64_t>(idx), n, P<uint64_t>(ndrop), P<uint8_t>(keep));
+    CK_LAUNCH("drop_prefix_kernel");
   }
   set_leaves_compacted(out, n, P<uint32_t>(in->lv[in->L].code), P<double>(in->lv[in->L].sq), P<int64_t>(in->slot),
                        P<uint8_t>(keep));
@@ -583,7 +669,7 @@ spamm_mat build_generated(spamm_ctx ctx, const spamm_gen_params* gp, int bs, dou
   GenElem el;
   el.p.n = gp->n;
   el.p.kind = gp->kind;
-  el.p.pad_ = 0;
+  el.p.law = gp->law;
   el.p.alpha = gp->alpha;
   el.p.c = gp->c;
   el.p.cutoff = gp->cutoff;

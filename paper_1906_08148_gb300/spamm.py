@@ -22,8 +22,8 @@ LIB_PATH = os.path.join(_PKG, "libspamm.so")
 OK, E_INVALID_ARG, E_SHAPE, E_NONFINITE, E_OOM, E_CUDA, E_TIMEOUT, E_BUSY, E_CAPACITY, E_UNSUPPORTED = range(10)
 MODE_TRUNCATE, MODE_SPAMM, MODE_COMBINED = 0, 1, 2
 MODES = {"truncate": MODE_TRUNCATE, "spamm": MODE_SPAMM, "combined": MODE_COMBINED}
-TRUNC_BLOCK_FROB, TRUNC_ELEMENT = 0, 1
-RULES = {"block": TRUNC_BLOCK_FROB, "element": TRUNC_ELEMENT}
+TRUNC_BLOCK_FROB, TRUNC_ELEMENT, TRUNC_ERROR_CONTROL = 0, 1, 2
+RULES = {"block": TRUNC_BLOCK_FROB, "element": TRUNC_ELEMENT, "error": TRUNC_ERROR_CONTROL}
 PREC_FP64, PREC_BF16_SPLIT, PREC_FP16_SCALED = 0, 1, 2
 PRECS = {"fp64": PREC_FP64, "bf16_split": PREC_BF16_SPLIT, "fp16_scaled": PREC_FP16_SCALED}
 MAX_LEVELS = 17
@@ -47,7 +47,7 @@ class SpammError(RuntimeError):
 
 
 class GenParams(ctypes.Structure):
-    _fields_ = [("n", ctypes.c_int64), ("kind", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    _fields_ = [("n", ctypes.c_int64), ("kind", ctypes.c_int32), ("law", ctypes.c_int32),
                 ("alpha", ctypes.c_double), ("c", ctypes.c_double), ("cutoff", ctypes.c_double),
                 ("seed", ctypes.c_uint64)]
 
@@ -264,8 +264,8 @@ def spamm_from_coo(ctx: Context, n: int, row, col, val, bs: int, tau: float = 0.
 
 def spamm_generate(ctx: Context, params, bs: int, tau: float = 0.0, rule: str = "block") -> Matrix:
     """params: any object with n, kind, alpha, c, cutoff, seed (e.g. synth.DecayParams)."""
-    gp = GenParams(int(params.n), int(params.kind), 0, float(params.alpha), float(params.c), float(params.cutoff),
-                   int(params.seed))
+    gp = GenParams(int(params.n), int(params.kind), int(getattr(params, "law", 0)), float(params.alpha),
+                   float(params.c), float(params.cutoff), int(params.seed))
     return _new(ctx, load().spamm_generate, ctypes.byref(gp), bs, float(tau), RULES[rule])
 
 

@@ -23,26 +23,30 @@ _lib = None
 
 KIND_1D = 0
 KIND_3D = 1
+LAW_EXPONENTIAL = 0
+LAW_ALGEBRAIC = 1
 
 
 class _Params(ctypes.Structure):
-    _fields_ = [("n", ctypes.c_int64), ("kind", ctypes.c_int32), ("pad_", ctypes.c_int32),
+    _fields_ = [("n", ctypes.c_int64), ("kind", ctypes.c_int32), ("law", ctypes.c_int32),
                 ("alpha", ctypes.c_double), ("c", ctypes.c_double), ("cutoff", ctypes.c_double),
                 ("seed", ctypes.c_uint64)]
 
 
 @dataclass(frozen=True)
 class DecayParams:
-    """One synthetic decay matrix: a_ij = c u_ij exp(-alpha d(i,j)), |a|<cutoff -> 0."""
+    """One synthetic decay matrix: a_ij = c u_ij exp(-alpha d(i,j)) (law 0) or
+    c u_ij / (1 + d(i,j))^alpha for integer alpha (law 1); |a| < cutoff -> 0."""
     n: int
     kind: int = KIND_3D
     alpha: float = 1.0
     seed: int = 1
     c: float = 1.0
     cutoff: float = 1e-16
+    law: int = 0
 
     def as_c(self) -> _Params:
-        return _Params(self.n, self.kind, 0, self.alpha, self.c, self.cutoff, self.seed)
+        return _Params(self.n, self.kind, self.law, self.alpha, self.c, self.cutoff, self.seed)
 
 
 def build(force: bool = False) -> str:
@@ -133,12 +137,30 @@ def lattice_point(i: int):
 
 def spectral_bound(p: DecayParams) -> float:
     """An upper bound of ||A||_2 for the matrices of `p`: the largest absolute
-    row sum (Gershgorin) is at most |c| sum_j exp(-alpha d(i, j)) over all
-    lattice points j, which for the 1-D kind is the closed form coth(alpha/2)
-    and for the 3-D kind the sum over integer offsets within radius 48/alpha
-    (the rest is below 1e-12 relative), enlarged by 1e-9 relative."""
+    row sum (Gershgorin) is at most |c| sum_j f(d(i, j)) over lattice points j,
+    f the decay factor.  Exponential law: over all integer offsets (1-D: the
+    closed form coth(alpha/2); 3-D: offsets within radius 48/alpha, the rest
+    below 1e-12 relative).  Algebraic law: over the offsets that fit the
+    matrix (|k| < n in 1-D; within the bounding box of the n lattice points in
+    3-D).  Enlarged by 1e-9 relative."""
     a = float(p.alpha)
-    if p.kind == KIND_1D:
+    if p.law == LAW_ALGEBRAIC:
+        k = max(1, int(a))
+        if p.kind == KIND_1D:
+            off = np.arange(-(p.n - 1), p.n, dtype=np.float64)
+            s = float(np.sum((1.0 + np.abs(off)) ** -k))
+        else:
+            i = np.arange(p.n, dtype=np.uint64)
+            box = []
+            for ax in range(3):  # bounding box of the points (Morton order, x first)
+                v = np.zeros(p.n, dtype=np.uint64)
+                for bit in range(21):
+                    v |= ((i >> np.uint64(3 * bit + ax)) & np.uint64(1)) << np.uint64(bit)
+                box.append(int(v.max()) + 1)
+            r = [np.arange(-(m - 1), m, dtype=np.float64) for m in box]
+            d = np.sqrt(r[0][:, None, None] ** 2 + r[1][None, :, None] ** 2 + r[2][None, None, :] ** 2)
+            s = float(np.sum((1.0 + d) ** -k))
+    elif p.kind == KIND_1D:
         s = 1.0 + 2.0 * math.exp(-a) / (1.0 - math.exp(-a))
     else:
         R = int(math.ceil(48.0 / a))
@@ -172,3 +194,8 @@ def model_1d(n=2048, alpha=0.05, seed=1) -> DecayParams:
 
 def lattice_3d(n=65536, alpha=1.0, seed=1) -> DecayParams:
     return DecayParams(n=n, kind=KIND_3D, alpha=alpha, seed=seed)
+
+
+def algebraic_3d(n=65536, p=4, seed=1) -> DecayParams:
+    """3-D lattice with algebraic decay |a_ij| <= (1 + d)^-p."""
+    return DecayParams(n=n, kind=KIND_3D, alpha=float(p), seed=seed, law=LAW_ALGEBRAIC)

@@ -7,6 +7,9 @@
  *
  * Element rule (Definition 1 of the paper, |a_ij| <= c exp(-alpha d(i,j))):
  *     a_ij = c * u_ij * exp(-alpha * d(i,j)),   set to 0 when |a_ij| < cutoff
+ * or, with law = SYNTH_LAW_ALGEBRAIC (the algebraic decay Section 1 mentions
+ * beside the exponential one), alpha an integer p >= 1:
+ *     a_ij = c * u_ij / (1 + d(i,j))^p
  * with u_ij uniform in [-1, 1) and symmetric in (i, j):
  *     u_ij = 2 * (h >> 11) * 2^-53 - 1,   h = SplitMix64 output number
  *     (min(i,j) << 32 | max(i,j)) of the stream seeded with `seed`
@@ -41,21 +44,24 @@
 #define SYNTH_ADD(a, b) __dadd_rn((a), (b))
 #define SYNTH_SUB(a, b) __dsub_rn((a), (b))
 #define SYNTH_SQRT(a) __dsqrt_rn(a)
+#define SYNTH_DIV(a, b) __ddiv_rn((a), (b))
 #else
 #include <math.h>
 #define SYNTH_MUL(a, b) ((a) * (b))
 #define SYNTH_ADD(a, b) ((a) + (b))
 #define SYNTH_SUB(a, b) ((a) - (b))
 #define SYNTH_SQRT(a) sqrt(a)
+#define SYNTH_DIV(a, b) ((a) / (b))
 #endif
 
 enum { SYNTH_KIND_1D = 0, SYNTH_KIND_3D = 1 };
+enum { SYNTH_LAW_EXPONENTIAL = 0, SYNTH_LAW_ALGEBRAIC = 1 };
 
 typedef struct synth_params {
   int64_t n;       /* matrix size */
   int32_t kind;    /* SYNTH_KIND_1D or SYNTH_KIND_3D */
-  int32_t pad_;
-  double alpha;    /* decay rate */
+  int32_t law;     /* SYNTH_LAW_EXPONENTIAL or SYNTH_LAW_ALGEBRAIC */
+  double alpha;    /* decay rate (exponential) or integer power p (algebraic) */
   double c;        /* decay constant (c = 1 in the paper) */
   double cutoff;   /* |a| < cutoff -> 0 (1e-16 in the paper's model problem) */
   uint64_t seed;
@@ -104,6 +110,22 @@ SYNTH_HD double synth_exp_nonpos(double x) {
   return SYNTH_MUL(p, s.d);
 }
 
+/* 1 / (1 + d)^p for integer p >= 1 (p < 1 taken as 1): p - 1 multiplications
+ * and one division, each correctly rounded, so host and device agree. */
+SYNTH_HD double synth_algebraic(double d, double p) {
+  const double x = SYNTH_ADD(1.0, d);
+  int k = (int)p;
+  if (k < 1) k = 1;
+  double pw = x;
+  for (int i = 1; i < k; ++i) pw = SYNTH_MUL(pw, x);
+  return SYNTH_DIV(1.0, pw);
+}
+
+/* The decay factor of distance d under the law of p. */
+SYNTH_HD double synth_decay(const struct synth_params* p, double d) {
+  return p->law == SYNTH_LAW_ALGEBRAIC ? synth_algebraic(d, p->alpha) : synth_exp_nonpos(SYNTH_MUL(-p->alpha, d));
+}
+
 SYNTH_HD uint32_t synth_compact1by2(uint64_t v) {
   /* keep bits 0, 3, 6, ... of v and pack them (21 bits) */
   v &= 0x1249249249249249ull;
@@ -134,7 +156,7 @@ SYNTH_HD double synth_distance(const synth_params* p, int64_t i, int64_t j) {
 SYNTH_HD double synth_element(const synth_params* p, int64_t i, int64_t j) {
   if (i < 0 || j < 0 || i >= p->n || j >= p->n) return 0.0;
   double d = synth_distance(p, i, j);
-  double e = synth_exp_nonpos(SYNTH_MUL(-p->alpha, d));
+  double e = synth_decay(p, d);
   double v = SYNTH_MUL(SYNTH_MUL(p->c, synth_uniform(p->seed, i, j)), e);
   double av = v < 0.0 ? -v : v;
   return av < p->cutoff ? 0.0 : v;
@@ -165,7 +187,7 @@ SYNTH_HD double synth_leaf_bound(const synth_params* p, int32_t bs, int64_t bi, 
     }
     dmin = SYNTH_SQRT((double)d2);
   }
-  double e = synth_exp_nonpos(SYNTH_MUL(-p->alpha, dmin));
+  double e = synth_decay(p, dmin);
   return SYNTH_MUL(SYNTH_MUL(p->c < 0.0 ? -p->c : p->c, e), 1.0 + 0x1.0p-40);
 }
 

@@ -127,3 +127,26 @@ def test_block_sparse_padding_stays_zero():
         rows, cols = max(0, min(bs, n - r0)), max(0, min(bs, n - c0))
         assert not np.any(d[q, rows:, :]) and not np.any(d[q, :, cols:])
         assert np.all(d[q, :rows, :cols] != 0.0)
+
+
+@pytest.mark.parametrize("kind,n,pw", [(synth.KIND_1D, 700, 2), (synth.KIND_3D, 512, 3), (synth.KIND_3D, 1000, 4)])
+def test_algebraic_decay_law(kind, n, pw):
+    """a_ij = c u_ij / (1 + d)^p: the bound holds, the law's value is exact in
+    closed form on sample pairs, the leaf bound dominates, and the spectral
+    bound dominates the largest eigenvalue magnitude."""
+    p = synth.DecayParams(n=n, kind=kind, alpha=float(pw), seed=5, law=synth.LAW_ALGEBRAIC)
+    A = synth.dense(p)
+    assert np.array_equal(A, A.T)
+    i, j = np.triu_indices(n, 1)
+    sel = np.random.default_rng(0).choice(len(i), 2000, replace=False)
+    for a, b in zip(i[sel], j[sel]):
+        d = synth.distance(p, int(a), int(b))
+        want = synth.uniform(p.seed, int(a), int(b)) / (1.0 + d) ** pw
+        assert A[a, b] == pytest.approx(want, rel=4e-16 * pw, abs=0)
+        assert abs(A[a, b]) <= 1.0 / (1.0 + d) ** pw
+    bs = 32
+    for bi in range(0, n // bs, 5):
+        for bj in range(0, n // bs, 3):
+            blk = A[bi * bs:(bi + 1) * bs, bj * bs:(bj + 1) * bs]
+            assert np.abs(blk).max() <= synth.leaf_bound(p, bs, bi, bj)
+    assert np.abs(np.linalg.eigvalsh(A)).max() <= synth.spectral_bound(p)

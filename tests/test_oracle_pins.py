@@ -249,3 +249,41 @@ def test_single_leaf_matrix_takes_the_leaf_test():
         _, kl = literal.spamm_literal(A, B, tau, 32)
         assert len(kl) == expect
     assert len(oracle.kept_recursive(LA, LB, prod * 2, oracle.TRUNCATE)) == 1
+
+
+# ---------------------------------------------------------------- error-controlled truncation
+def test_error_controlled_truncation_is_the_largest_admissible_drop():
+    """Brute force over every subset of a small leaf set: the rule drops the
+    largest number of leaves whose squared norms sum to <= tau^2 (dropping
+    the smallest first is optimal for the count), and ||M - M~||_F <= tau."""
+    import itertools
+    rng = np.random.default_rng(7)
+    for trial in range(40):
+        m = int(rng.integers(1, 9))
+        bs = 2
+        data = rng.standard_normal((m, bs, bs)) * np.exp(rng.uniform(-3, 1, (m, 1, 1)))
+        M = oracle.from_leaves(16, bs, np.arange(m), np.arange(m), data)
+        tau = float(np.sqrt(np.sum(M.sq)) * rng.uniform(0.0, 1.1))
+        T = oracle.truncate(M, tau, "error")
+        dropped = M.m - T.m
+        best = max(len(c) for r in range(m + 1) for c in itertools.combinations(range(m), r)
+                   if np.sum(M.sq[list(c)]) <= tau * tau)
+        assert dropped == best
+        assert oracle.error(M, T) <= tau * (1 + 1e-15)
+
+
+def test_error_controlled_truncation_edges_and_nesting():
+    p = synth.lattice_3d(1024, alpha=1.0, seed=3)
+    M = oracle.from_dense(synth.dense(p), 32)
+    assert oracle.truncate(M, 0.0, "error").m == M.m
+    assert oracle.truncate(M, oracle.frob_norm(M) * (1 + 1e-12), "error").m == 0
+    prev = M.m
+    for tau in [1e-12, 1e-9, 1e-6, 1e-3, 1e-1]:
+        T = oracle.truncate(M, tau, "error")
+        assert T.m <= prev and oracle.error(M, T) <= tau
+        prev = T.m
+    # equal norms fall in Morton order: identical leaves, budget for exactly two
+    one = np.ones((4, 2, 2))
+    E = oracle.from_leaves(8, 2, [1, 0, 1, 0], [1, 1, 0, 0], one)
+    T = oracle.truncate(E, np.sqrt(8.0), "error")
+    assert sorted(zip(T.bi.tolist(), T.bj.tolist())) == [(1, 0), (1, 1)]
