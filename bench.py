@@ -66,6 +66,7 @@ def parse_args():
     ap.add_argument("--serve-nmax", type=int, default=32768)
     ap.add_argument("--serve-batch", type=int, default=32)
     ap.add_argument("--serve-alpha", type=float, nargs=2, default=[0.8, 1.2])
+    ap.add_argument("--serve-graph", action="store_true", help="execute each batch as a captured CUDA graph")
     ap.add_argument("--no-forms", action="store_true", help="skip the tensor-form comparison in the bench line")
     ap.add_argument("--form-steps", type=int, default=5)
     ap.add_argument("--model-problem", action="store_true", help="the paper's 1-D model problem sweep")
@@ -274,7 +275,7 @@ def run_served(args):
         return reqs
 
     def serve(reqs):
-        srv = Server(max_batch=args.serve_batch, exec_sms=144)
+        srv = Server(max_batch=args.serve_batch, exec_sms=144, graph=args.serve_graph)
         srv.start()
         ids = [srv.submit(r) for r in reqs]
         for i in ids:
@@ -296,7 +297,8 @@ def run_served(args):
             "higher_is_better": True, "dtype": args.prec, "data": "synthetic",
             "config": {"workload": "served_stream", "requests": args.serve_requests, "inputs": args.serve_inputs,
                        "n_range": [4096, args.serve_nmax], "alpha": list(args.serve_alpha), "tau": taus,
-                       "method": "combined", "forms": forms, "arrivals": "Poisson at 0.9 x saturated capacity"},
+                       "method": "combined", "forms": forms, "arrivals": "Poisson at 0.9 x saturated capacity",
+                       "exec_graph": bool(args.serve_graph)},
             "saturated": sat, "loaded": load, "p50_s": load["p50_s"], "p99_s": load["p99_s"],
             "kept_gflops": load["kept_gflops"]}
     print(json.dumps(line), flush=True)
@@ -598,17 +600,21 @@ def main():
     for _ in range(args.warmup):
         st0, nrm0 = step()
     barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     stats = []
     with ClockSampler(local) as clk:
         barrier()
-        ev0.record(stream)
-        for _ in range(args.steps):
+        evs[0].record(stream)
+        for k in range(args.steps):
             st, nrm = step()
             stats.append(st)
-        ev1.record(stream)
+            evs[k + 1].record(stream)
         barrier()
-    ms_total, value, mults = aggregate_ranks(ev0.elapsed_time(ev1), sum(s["kept_flops"] for s in stats),
+    per_step = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps))
+    latency = {"p50_ms": per_step[(len(per_step) - 1) // 2],
+               "p99_ms": per_step[min(len(per_step) - 1, int(math.ceil(0.99 * len(per_step))) - 1)],
+               "steps": len(per_step)}
+    ms_total, value, mults = aggregate_ranks(evs[0].elapsed_time(evs[-1]), sum(s["kept_flops"] for s in stats),
                                              sum(s["n_kept"] for s in stats), dist)
     clocks = clk.summary()
 
@@ -643,7 +649,7 @@ def main():
             "mults_per_s": mults,
             "n_kept": kept, "n_steps": stats[-1]["n_steps"], "n_c_leaves": stats[-1]["n_c_leaves"], "n_borderline": stats[-1]["n_borderline"],
             "n_a_leaves": stats[-1]["n_a_leaves"], "n_b_leaves": stats[-1]["n_b_leaves"],
-            "c_frob": nrm, "phase_ms": phases, "roofline": roof,
+            "c_frob": nrm, "phase_ms": phases, "latency": latency, "roofline": roof,
             "gpu_launches": None, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "precision_forms": forms,
         }
         line["gpu_launches"] = int(sum(s["n_launches"] for s in stats))

@@ -2,8 +2,9 @@
 
 A request is described by (n, alpha, tau): the size, the decay rate of its
 inputs and the threshold.  The candidates are the library's forms: FP64 leaf
-products with 32 x 32 or 64 x 64 leaves, and the tensor-core forms (BF16
-three-term split, FP16 with per-leaf scaling) with 64 x 64 leaves.
+products with 32 x 32, 64 x 64 or 128 x 128 leaves, and the tensor-core
+forms (BF16 three-term split, FP16 with per-leaf scaling) with 64 x 64
+leaves.
 
 `calibrate` measures every candidate on synthetic decay inputs at a grid of
 (n, alpha, tau) points: the time of plan + execute, and for each tensor form
@@ -26,7 +27,7 @@ import time
 from dataclasses import dataclass
 from typing import Iterable, List, Optional, Sequence
 
-CANDIDATES = (("fp64", 32), ("fp64", 64), ("bf16_split", 64), ("fp16_scaled", 64))
+CANDIDATES = (("fp64", 32), ("fp64", 64), ("fp64", 128), ("bf16_split", 64), ("fp16_scaled", 64))
 TABLE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 

@@ -319,7 +319,8 @@ size_t held_bytes(const spamm_plan_s& p) {
 void check_form(spamm_prec prec, int bs) {
   need(prec == SPAMM_PREC_FP64 || prec == SPAMM_PREC_BF16_SPLIT || prec == SPAMM_PREC_FP16_SCALED,
        "unknown precision form");
-  if (prec == SPAMM_PREC_FP64 && bs > 64) fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32 and 64");
+  if (prec == SPAMM_PREC_FP64 && bs > 128)
+    fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32, 64 and 128");
   if (prec != SPAMM_PREC_FP64 && bs != 64)
     fail(SPAMM_E_UNSUPPORTED, "tensor-core precision forms are built for bs = 64");
 }

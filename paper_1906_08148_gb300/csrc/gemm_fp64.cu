@@ -10,7 +10,10 @@
 // batch).  Operand leaves are contiguous bs*bs FP64 blocks staged in shared
 // memory by 1-D TMA bulk copies, double-buffered on mbarriers; the product is
 // register-tiled DFMA (FP64 has no tcgen05 kind; DFMA measures faster than the
-// FP64 mma.sync path on this part).
+// FP64 mma.sync path on this part).  Leaves up to 64 x 64 are staged whole;
+// a 128 x 128 leaf (128 KB) in K-panels of KP = 32: A's panel as 128 row
+// segments of 256 bytes, B's as 32 whole rows (one copy), each leaf product
+// then four steps in the same ascending k order.
 #include "internal.cuh"
 #include "ptx.cuh"
 
@@ -18,15 +21,17 @@ namespace spamm {
 
 constexpr int kGemmThreads = 256;
 
-template <int BS>
+template <int BS, int KP>
 __global__ void __launch_bounds__(kGemmThreads)
     gemm_fp64_kernel(BatchDev batch, unsigned long long* __restrict__ work, int* __restrict__ err) {
   constexpr int LEAF = BS * BS;
-  constexpr uint32_t LEAF_BYTES = LEAF * sizeof(double);
+  constexpr int NP = BS / KP;                     // K-panels per leaf product
+  constexpr int PANEL = BS * KP;                  // doubles in one A panel (and one B panel)
+  constexpr uint32_t PANEL_BYTES = PANEL * sizeof(double);
   constexpr int TM = BS / 16;  // per-thread tile TM x TM: rows tr + 16 i, cols tc + 16 j
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  double* sA[2] = {reinterpret_cast<double*>(smem_raw), reinterpret_cast<double*>(smem_raw) + 2 * LEAF};
-  double* sB[2] = {reinterpret_cast<double*>(smem_raw) + LEAF, reinterpret_cast<double*>(smem_raw) + 3 * LEAF};
+  double* sA[2] = {reinterpret_cast<double*>(smem_raw), reinterpret_cast<double*>(smem_raw) + 2 * PANEL};
+  double* sB[2] = {reinterpret_cast<double*>(smem_raw) + PANEL, reinterpret_cast<double*>(smem_raw) + 3 * PANEL};
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int64_t s_u;
   __shared__ int s_abort;
@@ -53,23 +58,34 @@ __global__ void __launch_bounds__(kGemmThreads)
     const PlanDev& pl = batch.plans[r];
     const int64_t g = u - batch.ubegin[r];
     const int64_t q0 = pl.gstart[g], q1 = pl.gstart[g + 1];
-    auto issue = [&](int64_t q, int s) {
+    // step t: task q0 + t / NP, K-panel t % NP
+    auto issue = [&](int64_t t, int s) {
+      const int64_t q = q0 + t / NP;
+      const int p = (int)(t % NP);
+      const double* a = pl.poolA + pl.slotA[pl.ta[q]] * LEAF + p * KP;
+      const double* b = pl.poolB + pl.slotB[pl.tb[q]] * LEAF + (int64_t)p * KP * BS;
       fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&bar[s], 2 * LEAF_BYTES);
-      bulk_g2s(sA[s], pl.poolA + pl.slotA[pl.ta[q]] * LEAF, LEAF_BYTES, &bar[s]);
-      bulk_g2s(sB[s], pl.poolB + pl.slotB[pl.tb[q]] * LEAF, LEAF_BYTES, &bar[s]);
+      mbar_arrive_expect_tx(&bar[s], 2 * PANEL_BYTES);
+      if constexpr (NP == 1) {
+        bulk_g2s(sA[s], a, PANEL_BYTES, &bar[s]);
+      } else {
+        for (int row = 0; row < BS; ++row)
+          bulk_g2s(sA[s] + row * KP, a + (int64_t)row * BS, KP * sizeof(double), &bar[s]);
+      }
+      bulk_g2s(sB[s], b, PANEL_BYTES, &bar[s]);
     };
     double acc[TM][TM];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TM; ++j) acc[i][j] = 0.0;
-    if (tid == 0 && q0 < q1) issue(q0, 0);
+    const int64_t nsteps = (q1 - q0) * NP;
+    if (tid == 0 && nsteps > 0) issue(0, 0);
     inflight |= 1u;
-    for (int64_t q = q0; q < q1; ++q) {
-      const int s = (int)((q - q0) & 1);
-      if (q + 1 < q1) {
-        if (tid == 0) issue(q + 1, s ^ 1);
+    for (int64_t t = 0; t < nsteps; ++t) {
+      const int s = (int)(t & 1);
+      if (t + 1 < nsteps) {
+        if (tid == 0) issue(t + 1, s ^ 1);
         inflight |= 1u << (s ^ 1);
       }
       if (!mbar_wait_bounded(&bar[s], phase[s])) {
@@ -84,10 +100,10 @@ __global__ void __launch_bounds__(kGemmThreads)
       const double* As = sA[s];
       const double* Bs = sB[s];
 #pragma unroll 4
-      for (int kk = 0; kk < BS; ++kk) {
+      for (int kk = 0; kk < KP; ++kk) {
         double a[TM], b[TM];
 #pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = As[(tr + 16 * i) * BS + kk];
+        for (int i = 0; i < TM; ++i) a[i] = As[(tr + 16 * i) * KP + kk];
 #pragma unroll
         for (int j = 0; j < TM; ++j) b[j] = Bs[kk * BS + tc + 16 * j];
 #pragma unroll
@@ -97,7 +113,7 @@ __global__ void __launch_bounds__(kGemmThreads)
       }
       __syncthreads();
     }
-    if (q0 >= q1) inflight &= ~1u;
+    if (nsteps <= 0) inflight &= ~1u;
     if (s_abort) break;
     // epilogue: write C leaf g and its squared Frobenius norm (kernel (d))
     double* C = pl.cpool + g * LEAF;
@@ -129,17 +145,18 @@ __global__ void __launch_bounds__(kGemmThreads)
 
 template <int BS>
 static void launch_fp64(spamm_ctx ctx, const BatchDev& b) {
-  const size_t smem = 4 * (size_t)BS * BS * sizeof(double);
-  CK(cudaFuncSetAttribute(gemm_fp64_kernel<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  constexpr int KP = BS <= 64 ? BS : 32;
+  const size_t smem = 4 * (size_t)BS * KP * sizeof(double);
+  CK(cudaFuncSetAttribute(gemm_fp64_kernel<BS, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_fp64_kernel<BS>, kGemmThreads, smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_fp64_kernel<BS, KP>, kGemmThreads, smem));
   if (per_sm < 1) per_sm = 1;
   const int sms = ctx->gemm_sm_limit > 0 ? ctx->gemm_sm_limit : ctx->num_sms;
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > b.nunits) grid = b.nunits;
   unsigned long long* work = ctx->d_scratch + 8;
   CK(cudaMemsetAsync(work, 0, sizeof(unsigned long long), ctx->stream));
-  gemm_fp64_kernel<BS><<<(unsigned)grid, kGemmThreads, smem, ctx->stream>>>(b, work, ctx->d_err);
+  gemm_fp64_kernel<BS, KP><<<(unsigned)grid, kGemmThreads, smem, ctx->stream>>>(b, work, ctx->d_err);
   CK_LAUNCH("gemm_fp64_kernel");
 }
 
@@ -148,7 +165,8 @@ void gemm_fp64_batch(spamm_ctx ctx, int bs, const BatchDev& b) {
   switch (bs) {
     case 32: launch_fp64<32>(ctx, b); break;
     case 64: launch_fp64<64>(ctx, b); break;
-    default: fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32 and 64");
+    case 128: launch_fp64<128>(ctx, b); break;
+    default: fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32, 64 and 128");
   }
 }
 

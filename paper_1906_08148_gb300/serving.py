@@ -57,7 +57,7 @@ class Request:
 class SpammBackend:
     """The real device work: plan / execute / release through libspamm."""
 
-    def __init__(self, device: int = 0, exec_sms: Optional[int] = None):
+    def __init__(self, device: int = 0, exec_sms: Optional[int] = None, graph: bool = False):
         import torch
 
         from . import spamm as S
@@ -69,6 +69,8 @@ class SpammBackend:
         self.exec_ctx = S.Context(device, stream=self.exec_stream)
         if exec_sms:
             S.spamm_set_gemm_sms(self.exec_ctx, exec_sms)
+        if graph:  # each batch's execute phase as one captured CUDA graph
+            S.spamm_set_exec_graph(self.exec_ctx, True)
         free, _ = torch.cuda.mem_get_info(device)
         self.free_bytes = free
 
@@ -88,8 +90,8 @@ class SpammBackend:
 
 class Server:
     def __init__(self, backend=None, hbm_budget: Optional[int] = None, max_batch: int = 64, device: int = 0,
-                 exec_sms: Optional[int] = None):
-        self.backend = backend if backend is not None else SpammBackend(device, exec_sms)
+                 exec_sms: Optional[int] = None, graph: bool = False):
+        self.backend = backend if backend is not None else SpammBackend(device, exec_sms, graph)
         if hbm_budget is None:
             hbm_budget = int(0.8 * getattr(self.backend, "free_bytes", 1 << 40))
         self.budget = int(hbm_budget)

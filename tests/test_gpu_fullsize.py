@@ -93,3 +93,30 @@ def test_fullsize_scattered_leaves(S, setup):
         else:
             assert f[0]
             assert np.linalg.norm(g[0] - ref.data[0]) <= 1e-12 * np.linalg.norm(ref.data[0])
+
+
+@pytest.mark.parametrize("prec", ["bf16_split", "fp16_scaled"])
+def test_precision_form_config_262144(S, prec):
+    """The precision-form configuration: 64 x 64 x 64 lattice (n = 262144),
+    alpha = 0.8, combined tau = 1e-5.  Inputs are generated with the block
+    rule applied while generating (identical to truncating the full matrix:
+    the rule is per leaf; the untruncated inputs would not fit), the plan
+    keeps only the operand terms, so the FP64 inputs are released before the
+    leaf products run.  A window of output leaves against the FP64 oracle."""
+    ctx = S.Context(0)
+    n, alpha, tau = 262144, 0.8, 1e-5
+    pa, pb = synth.lattice_3d(n, alpha=alpha, seed=1), synth.lattice_3d(n, alpha=alpha, seed=2)
+    GA, GB = S.spamm_generate(ctx, pa, BS, tau), S.spamm_generate(ctx, pb, BS, tau)
+    na, nb = GA.info()["nleaves"], GB.info()["nleaves"]
+    plan = S.spamm_plan_create(ctx, GA, GB, tau, "combined", prec)
+    GA.close()
+    GB.close()
+    (C,), (st,) = S.spamm_execute(ctx, [plan], stats=True)
+    plan.close()
+    w = 6
+    A_rows, B_cols = sampled.window_inputs(pa, pb, BS, range(w), range(w))
+    ref, _ = sampled.window_product(A_rows, B_cols, tau, oracle.COMBINED)
+    rel = _window_check(S, ctx, C, ref, 1e-5)
+    print(f"{prec} n={n} alpha={alpha} tau={tau}: A {na} B {nb} leaves, kept {st['n_kept']}, "
+          f"C leaves {st['n_c_leaves']}, ms_gemm {st['ms_gemm']:.1f}, window rel error vs FP64 oracle {rel:.2e}")
+    C.close()

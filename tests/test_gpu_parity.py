@@ -247,7 +247,7 @@ def test_kept_tasks_are_grouped_by_c_leaf_in_morton_order(S, ctx):
     assert np.all(np.diff(ikj[:, 1])[same] > 0), "k must ascend within a C leaf"
 
 
-@pytest.mark.parametrize("n,bs,alpha", [(4096, 64, 1.0), (3000, 32, 0.8), (5000, 64, 0.6)])
+@pytest.mark.parametrize("n,bs,alpha", [(4096, 64, 1.0), (3000, 32, 0.8), (5000, 64, 0.6), (2048, 128, 0.8), (1500, 128, 1.0)])
 @pytest.mark.parametrize("mode", ["spamm", "truncate", "combined"])
 def test_lattice_parity_all_methods(S, ctx, n, bs, alpha, mode):
     pa, pb = synth.lattice_3d(n, alpha=alpha, seed=1), synth.lattice_3d(n, alpha=alpha, seed=2)

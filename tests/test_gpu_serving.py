@@ -22,7 +22,8 @@ def S():
     return spamm
 
 
-def test_served_results_equal_alone(S):
+@pytest.mark.parametrize("graph", [False, True])
+def test_served_results_equal_alone(S, graph):
     from paper_1906_08148_gb300.serving import Request, Server
     data = S.Context(0)
     rng = random.Random(7)
@@ -37,7 +38,7 @@ def test_served_results_equal_alone(S):
         A, B = pool[rng.randrange(len(pool))]
         reqs.append(Request(A, B, tau=rng.choice([1e-4, 1e-6, 1e-8]), mode=rng.choice(["combined", "spamm"]),
                             prec=rng.choice(["bf16_split", "fp16_scaled", "fp64"]), arrival=t))
-    srv = Server(max_batch=8, exec_sms=136)
+    srv = Server(max_batch=8, exec_sms=136, graph=graph)
     srv.start()
     ids = [srv.submit(r) for r in reqs]
     for i in ids:
@@ -54,4 +55,4 @@ def test_served_results_equal_alone(S):
         b = S.spamm_to_blocks(data, r.result)
         for x, y in zip(a, b):
             assert np.array_equal(x, y), (r.rid, r.prec, r.tau)
-    print("serving summary", s)
+    print("serving summary", "graph" if graph else "eager", s)
