@@ -92,7 +92,13 @@ typedef enum {
  * BF16_SPLIT: each operand split into three bfloat16 terms, the six products
  * with term-index sum <= 2 on the tensor cores, FP32 accumulation.
  * FP16_SCALED: per-leaf power-of-two scaling, two float16 terms, FP32
- * accumulation.  Norms, the tau test and errors are always FP64. */
+ * accumulation.  Norms, the tau test and errors are always FP64.
+ * Range of the two tensor-core forms: operand elements are rounded to FP32
+ * first (below 2^-126 they count as 0), and the output leaves are summed in
+ * FP32, so output elements must lie within the FP32 range (about 1e-38 ..
+ * 3e38, relative precision lost towards the bottom); the FP16 form's per-leaf
+ * scale exponents are clamped to [-120, 120].  A power-of-two rescaling of
+ * the inputs within that range rescales the result exactly. */
 typedef enum { SPAMM_PREC_FP64 = 0, SPAMM_PREC_BF16_SPLIT = 1, SPAMM_PREC_FP16_SCALED = 2 } spamm_prec;
 
 /* Synthetic matrix with exponential decay (Definition 1 with c, alpha):
@@ -293,6 +299,14 @@ SPAMM_API spamm_status spamm_identity(spamm_ctx ctx, int64_t n, int bs, spamm_ma
 /* Trace of X (the sum of the diagonals of its diagonal leaves, each leaf in
  * row order, the leaf sums by a fixed reduction tree). */
 SPAMM_API spamm_status spamm_trace(spamm_ctx ctx, spamm_mat X, double* out);
+
+/* Diagnostic (no counterpart in the paper): launch one kernel whose bounded
+ * device-side wait, wait_ns nanoseconds long (1 .. 2e9), runs out because
+ * nothing completes the awaited mbarrier phase.  Returns SPAMM_E_TIMEOUT, the
+ * status every library kernel reports when one of its waits runs out; the
+ * context's error word is cleared and the context stays usable.  Errors:
+ * INVALID_ARG, CUDA. */
+SPAMM_API spamm_status spamm_check_timeout_path(spamm_ctx ctx, int64_t wait_ns);
 
 /* ------------------------------------------------------------ evaluation */
 

@@ -169,10 +169,42 @@ __global__ void scan_down_kernel(const T* __restrict__ in, T* __restrict__ out, 
   }
 }
 
+// n <= kScanTile: the whole scan in one block, one launch.
+template <class T>
+__global__ void scan_one_tile_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t n, T* d_total,
+                                     bool inclusive) {
+  __shared__ T tile[kScanTile];
+  for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) tile[i] = i < n ? in[i] : 0;
+  __syncthreads();
+  T loc[kScanItems];
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    loc[i] = s;
+    s += tile[threadIdx.x * kScanItems + i];
+  }
+  T total;
+  const T ex = block_exclusive_scan(s, &total);
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const T mine = tile[threadIdx.x * kScanItems + i];
+    tile[threadIdx.x * kScanItems + i] = inclusive ? (ex + loc[i]) + mine : ex + loc[i];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kScanTile; i += kScanThreads)
+    if (i < n) out[i] = tile[i];
+  if (threadIdx.x == 0 && d_total) *d_total = total;
+}
+
 template <class T>
 static void scan_any(spamm_ctx ctx, const T* in, T* out, int64_t n, T* d_total, bool inclusive) {
   if (n <= 0) {
     if (d_total) CK(cudaMemsetAsync(d_total, 0, sizeof(T), ctx->stream));
+    return;
+  }
+  if (n <= kScanTile) {
+    scan_one_tile_kernel<T><<<1, kScanThreads, 0, ctx->stream>>>(in, out, n, d_total, inclusive);
+    CK_LAUNCH("scan_one_tile_kernel");
     return;
   }
   const int64_t nblocks = (n + kScanTile - 1) / kScanTile;

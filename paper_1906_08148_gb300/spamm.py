@@ -35,7 +35,7 @@ ENTRY_POINTS = (
     "spamm_multiply", "spamm_kept_tasks", "spamm_frob_norm", "spamm_error", "spamm_mat_info", "spamm_to_dense",
     "spamm_to_blocks", "spamm_gather_leaves", "spamm_level_norms", "spamm_leaf_sqnorms_noalloc",
     "spamm_plan_create", "spamm_plan_info", "spamm_execute", "spamm_plan_release", "spamm_set_gemm_sms",
-    "spamm_set_exec_graph", "spamm_add", "spamm_identity", "spamm_trace",
+    "spamm_set_exec_graph", "spamm_add", "spamm_identity", "spamm_trace", "spamm_check_timeout_path",
 )
 NOALLOC_MAX_LEAVES = 1 << 24
 
@@ -121,6 +121,7 @@ def load(path: str = LIB_PATH):
         "spamm_add": [vp, f64, vp, f64, vp, ctypes.POINTER(vp)],
         "spamm_identity": [vp, i64, ctypes.c_int, ctypes.POINTER(vp)],
         "spamm_trace": [vp, vp, pf64],
+        "spamm_check_timeout_path": [vp, i64],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -458,6 +459,11 @@ def spamm_trace(ctx: Context, X: Matrix) -> float:
     v = ctypes.c_double()
     _check(ctx.handle, load().spamm_trace(ctx.handle, X.handle, ctypes.byref(v)))
     return v.value
+
+
+def spamm_check_timeout_path(ctx: Context, wait_ns: int = 50_000_000) -> int:
+    """Run the device-timeout diagnostic; returns the raw status (E_TIMEOUT expected)."""
+    return int(load().spamm_check_timeout_path(ctx.handle, int(wait_ns)))
 
 
 def spamm_set_exec_graph(ctx: Context, enable: bool):

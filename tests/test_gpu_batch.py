@@ -125,3 +125,21 @@ def test_graph_execute_equals_eager(S, ctx, prec):
             assert np.array_equal(ce, cg) and np.array_equal(se, sg), (prec, r, lev)
         assert st_g[r]["ms_gemm"] > 0.0
     assert np.array_equal(S.spamm_to_blocks(ctx, single)[2], S.spamm_to_blocks(ctx, eager[0])[2])
+
+
+def test_device_timeout_becomes_a_status_and_the_context_stays_usable(S, ctx):
+    """A bounded device wait that runs out (an mbarrier phase nothing
+    completes, 50 ms bound) is reported as SPAMM_E_TIMEOUT; the error word is
+    cleared, so the next multiply on the same context succeeds and is exact."""
+    import time
+    t0 = time.perf_counter()
+    st = S.spamm_check_timeout_path(ctx, 50_000_000)
+    took = time.perf_counter() - t0
+    assert st == S.E_TIMEOUT
+    assert 0.04 <= took < 5.0
+    assert "ran out" in S.load().spamm_last_error(ctx.handle).decode()
+    assert S.spamm_check_timeout_path(ctx, 0) == S.E_INVALID_ARG
+    GA, GB = _inputs(S, ctx, 2048, 0.8, 64)
+    C = S.spamm_multiply(ctx, GA, GB, 1e-6, "combined", "fp64")
+    D = S.spamm_multiply(ctx, GA, GB, 1e-6, "combined", "fp64")
+    assert np.array_equal(S.spamm_to_blocks(ctx, C)[2], S.spamm_to_blocks(ctx, D)[2])

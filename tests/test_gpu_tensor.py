@@ -134,3 +134,17 @@ def test_tensor_forms_deterministic(S, ctx):
     for prec in ("bf16_split", "fp16_scaled"):
         outs = [S.spamm_to_blocks(ctx, S.spamm_multiply(ctx, G, G, 1e-6, "combined", prec))[2] for _ in range(2)]
         assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("prec", ["bf16_split", "fp16_scaled"])
+def test_power_of_two_scaling_is_exact(S, ctx, prec):
+    """Scaling A by 2^-40 and B by 2^40 (exact in FP64, in range for FP32) gives
+    bit for bit the same C: both forms only shift exponents."""
+    A, B = (synth.dense(synth.lattice_3d(4096, alpha=0.9, seed=s)) for s in (1, 2))
+    tau = 1e-6
+    ref = S.spamm_to_dense(ctx, S.spamm_multiply(ctx, S.spamm_from_dense(ctx, A, 64), S.spamm_from_dense(ctx, B, 64),
+                                                 tau, "spamm", prec))
+    As, Bs = np.ldexp(A, -40), np.ldexp(B, 40)
+    got = S.spamm_to_dense(ctx, S.spamm_multiply(ctx, S.spamm_from_dense(ctx, As, 64), S.spamm_from_dense(ctx, Bs, 64),
+                                                 tau, "spamm", prec))
+    assert np.array_equal(got, ref)
