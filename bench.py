@@ -34,6 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+L2_BYTES = 129 << 20  # GB300 L2 (for the flush rule)
 FP64_PEAK_GFLOPS = 1258.6  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (DFMA probe: 1208)
 CONFIGS = {
     "lattice65536": dict(n=65536, kind=1, alpha=1.0, bs=64, seeds=(1, 2),
@@ -597,24 +598,30 @@ def main():
         C.close()
         return st, nrm
 
+    # inputs smaller than twice the L2: write a 256 MB buffer before every step, outside its events
+    in_bytes = (GA.info()["nleaves"] + (0 if GB is GA else GB.info()["nleaves"])) * bs * bs * 8
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if in_bytes < 2 * L2_BYTES else None
     for _ in range(args.warmup):
         st0, nrm0 = step()
     barrier()
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stats = []
     with ClockSampler(local) as clk:
         barrier()
-        evs[0].record(stream)
         for k in range(args.steps):
+            if flush is not None:
+                flush.zero_()
+            ev_a[k].record(stream)
             st, nrm = step()
             stats.append(st)
-            evs[k + 1].record(stream)
+            ev_b[k].record(stream)
         barrier()
-    per_step = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps))
+    per_step = sorted(ev_a[k].elapsed_time(ev_b[k]) for k in range(args.steps))
     latency = {"p50_ms": per_step[(len(per_step) - 1) // 2],
                "p99_ms": per_step[min(len(per_step) - 1, int(math.ceil(0.99 * len(per_step))) - 1)],
                "steps": len(per_step)}
-    ms_total, value, mults = aggregate_ranks(evs[0].elapsed_time(evs[-1]), sum(s["kept_flops"] for s in stats),
+    ms_total, value, mults = aggregate_ranks(sum(per_step), sum(s["kept_flops"] for s in stats),
                                              sum(s["n_kept"] for s in stats), dist)
     clocks = clk.summary()
 
@@ -628,7 +635,7 @@ def main():
         e2e = run_e2e(S, ctx, GA, GB, args, bs, torch, np)
 
     forms = None
-    if not args.no_forms and rank == 0 and args.prec == "fp64":
+    if not args.no_forms and rank == 0 and args.prec == "fp64" and bs == 64:  # tensor forms: 64 x 64 leaves
         forms = precision_forms(S, ctx, GA, GB, args, stream, torch)
 
     cpu = None
@@ -637,14 +644,15 @@ def main():
 
     if rank == 0:
         roof = roofline(args.prec, bs, kept, ms_gemm, statistics.mean(s["executed_flops"] for s in stats))
-        in_gb = (GA.info()["nleaves"] + (0 if GB is GA else GB.info()["nleaves"])) * bs * bs * 8 / 1e9
+        in_gb = in_bytes / 1e9
         line = {
             "metric": "kept-block GFLOP/s", "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.prec == "fp64" else args.prec, "data": "synthetic",
             "config": {"workload": args.config, "desc": cfg["desc"], "n": cfg["n"], "bs": bs, "method": args.mode,
-                       "tau": args.tau, "precision": args.prec, "l2": "inputs (%.1f GB of leaves) larger than L2" % in_gb,
+                       "tau": args.tau, "precision": args.prec, "l2": ("inputs (%.1f GB of leaves) larger than L2" % in_gb) if flush is None
+                       else "L2 flushed before every step (256 MB write, outside the step's events)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "mults_per_s": mults,
             "n_kept": kept, "n_steps": stats[-1]["n_steps"], "n_c_leaves": stats[-1]["n_c_leaves"], "n_borderline": stats[-1]["n_borderline"],
