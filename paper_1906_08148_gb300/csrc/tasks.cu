@@ -35,10 +35,26 @@ __device__ __forceinline__ int comp4(const int4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
-// mask bit (2*c + ck) for child group c = 2*ci + cj and child k-index ck.
-__device__ __forceinline__ unsigned child_mask(const int4& ca, const int4& cb, const double* __restrict__ sqA,
-                                               const double* __restrict__ sqB, double tau, int test, bool leaf,
-                                               long long* cand, long long* border) {
+__device__ __forceinline__ double comp4d(const double4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// Per node of a level: the Frobenius norms sqrt(s) of its four children
+// (-1 where a child is null), so the descent reads one 32-byte record per
+// node of a pair instead of four scattered squared norms.
+__global__ void child_norms_kernel(int64_t n, const int4* __restrict__ child, const double* __restrict__ sq_next,
+                                   double4* __restrict__ out) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int4 c = child[q];
+    out[q] = make_double4(c.x >= 0 ? sqrt(sq_next[c.x]) : -1.0, c.y >= 0 ? sqrt(sq_next[c.y]) : -1.0,
+                          c.z >= 0 ? sqrt(sq_next[c.z]) : -1.0, c.w >= 0 ? sqrt(sq_next[c.w]) : -1.0);
+  }
+}
+
+// mask bit (2*c + ck) for child group c = 2*ci + cj and child k-index ck;
+// na / nb: the children's norms of the pair's A and B nodes.
+__device__ __forceinline__ unsigned child_mask(const int4& ca, const int4& cb, const double4& na, const double4& nb,
+                                               double tau, int test, bool leaf, long long* cand, long long* border) {
   unsigned m = 0;
 #pragma unroll
   for (int ci = 0; ci < 2; ++ci)
@@ -51,7 +67,7 @@ __device__ __forceinline__ unsigned child_mask(const int4& ca, const int4& cb, c
         ++*cand;
         bool keep = true;
         if (test) {
-          const double prod = __dmul_rn(sqrt(sqA[a]), sqrt(sqB[b]));
+          const double prod = __dmul_rn(comp4d(na, 2 * ci + ck), comp4d(nb, 2 * ck + cj));
           keep = prod >= tau;
           if (leaf && fabs(prod - tau) <= 1e-12 * tau) ++*border;
         }
@@ -64,7 +80,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     task_count_kernel(int64_t Gcap, const int64_t* __restrict__ dG, const int64_t* __restrict__ gstart,
                       const int32_t* __restrict__ ta,
                       const int32_t* __restrict__ tb, const int4* __restrict__ childA, const int4* __restrict__ childB,
-                      const double* __restrict__ sqA, const double* __restrict__ sqB, double tau, int test, int leaf,
+                      const double4* __restrict__ normA, const double4* __restrict__ normB, double tau, int test, int leaf,
                       uint8_t* __restrict__ mask, uint64_t* __restrict__ packed, unsigned long long* stats) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -78,8 +94,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const int64_t q0 = gstart[g], q1 = gstart[g + 1];
     unsigned cnt[4] = {0, 0, 0, 0};
     for (int64_t q = q0 + lane; q < q1; q += 32) {
-      const int4 ca = childA[ta[q]], cb = childB[tb[q]];
-      const unsigned m = child_mask(ca, cb, sqA, sqB, tau, test, leaf, &cand, &border);
+      const int32_t ia = ta[q], ib = tb[q];
+      const int4 ca = childA[ia], cb = childB[ib];
+      const unsigned m = child_mask(ca, cb, normA[ia], normB[ib], tau, test, leaf, &cand, &border);
       mask[q] = (uint8_t)m;
 #pragma unroll
       for (int c = 0; c < 4; ++c) cnt[c] += __popc((m >> (2 * c)) & 3u);
@@ -263,10 +280,18 @@ TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm
     CK(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned long long), ctx->stream));
     BufP mask = alloc_n<uint8_t>(ctx, Q);
     BufP packed = alloc_n<uint64_t>(ctx, 4 * G), off = alloc_n<uint64_t>(ctx, 4 * G), tot = alloc_n<uint64_t>(ctx, 1);
+    BufP normA = alloc_n<double4>(ctx, A->lv[t].count), normB = alloc_n<double4>(ctx, B->lv[t].count);
+    for (int side = 0; side < 2; ++side) {
+      const Level& lv = (side ? B : A)->lv[t];
+      if (lv.count == 0) continue;
+      const int64_t g = (lv.count + 255) / 256, cap = (int64_t)ctx->num_sms * 16;
+      child_norms_kernel<<<(unsigned)(g < cap ? g : cap), 256, 0, ctx->stream>>>(
+          lv.count, P<int4>(lv.child), P<double>((side ? B : A)->lv[t + 1].sq), P<double4>(side ? normB : normA));
+      CK_LAUNCH("child_norms_kernel");
+    }
     task_count_kernel<<<warps_grid(ctx, G), kWarpsPerBlock * 32, 0, ctx->stream>>>(
         G, dG, P<int64_t>(gstart), P<int32_t>(ta), P<int32_t>(tb), P<int4>(A->lv[t].child), P<int4>(B->lv[t].child),
-        P<double>(A->lv[t + 1].sq), P<double>(B->lv[t + 1].sq), tau, test_norms, leaf, P<uint8_t>(mask),
-        P<uint64_t>(packed), stats);
+        P<double4>(normA), P<double4>(normB), tau, test_norms, leaf, P<uint8_t>(mask), P<uint64_t>(packed), stats);
     CK_LAUNCH("task_count_kernel");
     scan_exclusive_u64(ctx, P<uint64_t>(packed), P<uint64_t>(off), 4 * G, P<uint64_t>(tot));
     // capacities of the next level: exact after a wait, else the bounds 8 Q and 4 G
