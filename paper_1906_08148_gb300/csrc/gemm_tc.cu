@@ -3,8 +3,9 @@
 // C-leaf norms of kernel (d) in the epilogue.
 //
 // Each leaf product of Algorithm 1 ("C = AB" at the lowest level) is a real
-// 64 x 64 x 64 contraction on tcgen05.  Operands are split into low-precision
-// terms, each the rounding of what the previous terms left:
+// 64 x 64 x 64 contraction on tcgen05.  Operands are split (prep.cu, layout in
+// tcforms.cuh) into low-precision terms, each the rounding of what the
+// previous terms left:
 //   BF16 split : a = a0 + a1 + a2, b = b0 + b1 + b2 (bf16); the six products
 //                with term-index sum <= 2 are formed.
 //   FP16 scaled: a' = a 2^eA with max|a'| in [2^14, 2^15) per leaf,
@@ -39,140 +40,11 @@
 //              output row; writes the FP64 output leaves and their squared norms.
 // No atomics on C: one CTA owns each output quad; k runs in ascending order.
 // Every wait is bounded; on timeout the CTA sets the error word and leaves.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-
-#include "fbits.cuh"
 #include "internal.cuh"
 #include "ptx.cuh"
+#include "tcforms.cuh"
 
 namespace spamm {
-
-constexpr uint32_t kTerm = 64 * 64 * 2;  // one 64 x 64 two-byte term tile: 8 KB
-
-template <int PREC>
-struct FormCfg;
-template <>
-struct FormCfg<SPAMM_PREC_BF16_SPLIT> {
-  static constexpr int TERMS = 3;  // terms per operand
-  static constexpr int NS = 2;     // pipeline stages of 96 KB
-  static constexpr uint32_t AB = 1u;  // operand format bf16
-};
-template <>
-struct FormCfg<SPAMM_PREC_FP16_SCALED> {
-  static constexpr int TERMS = 2;
-  static constexpr int NS = 3;     // stages of 64 KB
-  static constexpr uint32_t AB = 0u;  // f16
-};
-template <int PREC>
-__host__ __device__ constexpr uint32_t leaf_bytes() {
-  return FormCfg<PREC>::TERMS * kTerm;
-}
-
-// Byte offset of element (row, k) in a 128-byte-swizzled K-major tile of
-// 64 two-byte elements per row: 16-byte chunk index XOR (row mod 8).
-__device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
-  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((k >> 3) ^ row) & 7) << 4) + (k & 7) * 2);
-}
-
-// ---------------------------------------------------------------- operand prep
-// Terms of one leaf as 16-byte swizzled chunks: chunk (row, c8) holds k =
-// 8 c8 .. 8 c8 + 7 of one tile row.  role 0 (A): term s is a 64-row tile at
-// s * 8 KB, tile row = leaf row, k = leaf column.  role 1 (B): term s occupies
-// tile rows 64 s .. 64 s + 63 (row = leaf column n), k = leaf row.
-//
-// One CTA of 256 threads per leaf; a thread owns two chunks and loads their 16
-// elements first (A: 8 consecutive doubles of a row; B: one column, so the
-// lanes of a warp read consecutive doubles of each leaf row).  Each element is
-// rounded once to FP32 on its bits (fbits.cuh; the FP16 form's per-leaf scale
-// 2^e folded in), then split in FP32:
-//   BF16: b0 = bf16(a), b1 = bf16(a - b0), b2 = bf16(a - b0 - b1)
-//   FP16: h0 = f16(a 2^e), h1 = f16(a 2^e - h0), max|a 2^e| in [2^14, 2^15)
-// (each residual is exact in FP32).
-template <int PREC>
-__global__ void __launch_bounds__(256) prep_terms_kernel(const double* __restrict__ pool,
-                                                         const int64_t* __restrict__ slot, int64_t nleaves, int role,
-                                                         uint8_t* __restrict__ out, int32_t* __restrict__ expo) {
-  constexpr int TERMS = FormCfg<PREC>::TERMS;
-  constexpr uint32_t LEAF = leaf_bytes<PREC>();
-  __shared__ unsigned long long smax[8];
-  __shared__ int s_shift;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  for (int64_t m = blockIdx.x; m < nleaves; m += gridDim.x) {
-    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(pool + slot[m] * 4096);
-    unsigned long long v[2][8];
-    int row[2], c8[2];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      if (role == 0) {
-        row[j] = (t >> 3) + 32 * j;
-        c8[j] = t & 7;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[j][e] = __ldg(src + row[j] * 64 + 8 * c8[j] + e);
-      } else {
-        row[j] = t & 63;
-        c8[j] = (t >> 6) + 4 * j;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[j][e] = __ldg(src + (8 * c8[j] + e) * 64 + row[j]);
-      }
-    }
-    int shift = 0;
-    if constexpr (PREC == SPAMM_PREC_FP16_SCALED) {
-      // largest |a| of the leaf: |x| of doubles orders like their bits without the sign
-      unsigned long long mx = 0;
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const unsigned long long a = v[j][e] & 0x7FFFFFFFFFFFFFFFull;
-          mx = a > mx ? a : mx;
-        }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
-        mx = o > mx ? o : mx;
-      }
-      if (lane == 0) smax[warp] = mx;
-      __syncthreads();
-      if (t == 0) {
-        unsigned long long g = 0;
-        for (int w = 0; w < 8; ++w) g = smax[w] > g ? smax[w] : g;
-        s_shift = fp16_leaf_shift(g);
-        expo[m] = s_shift;
-      }
-      __syncthreads();
-      shift = s_shift;
-    }
-    uint8_t* dst = out + m * (int64_t)LEAF;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      __align__(16) uint16_t term[TERMS][8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        float a = __uint_as_float(fbits_from_double_rn(v[j][e], shift));
-#pragma unroll
-        for (int s = 0; s < TERMS; ++s) {
-          if constexpr (PREC == SPAMM_PREC_FP16_SCALED) {
-            const __half h = __float2half_rn(a);
-            term[s][e] = __half_as_ushort(h);
-            a -= __half2float(h);
-          } else {
-            const __nv_bfloat16 h = __float2bfloat16_rn(a);
-            term[s][e] = __bfloat16_as_ushort(h);
-            a -= __bfloat162float(h);
-          }
-        }
-      }
-#pragma unroll
-      for (int s = 0; s < TERMS; ++s) {
-        const uint32_t off = role == 0 ? s * kTerm + sw128_offset(row[j], 8 * c8[j])
-                                       : sw128_offset(64 * s + row[j], 8 * c8[j]);
-        *reinterpret_cast<uint4*>(dst + off) = *reinterpret_cast<const uint4*>(term[s]);
-      }
-    }
-    if constexpr (PREC == SPAMM_PREC_FP16_SCALED) __syncthreads();  // smax / s_shift are reused
-  }
-}
 
 // ------------------------------------------------------------- quad steps
 // The four kept-product runs of a quad (child c = 2h + cj, tasks of one C leaf
@@ -551,29 +423,6 @@ static unsigned gemm_grid(spamm_ctx ctx, int64_t nunits) {
   int64_t grid = ctx->gemm_sm_limit > 0 ? ctx->gemm_sm_limit : ctx->num_sms;
   if (grid > nunits) grid = nunits;
   return (unsigned)(grid < 1 ? 1 : grid);
-}
-
-void prep_terms(spamm_mat M, spamm_prec prec, int role, BufP* terms, BufP* expo, spamm_ctx on) {
-  spamm_ctx ctx = on ? on : M->ctx;
-  if (M->bs != 64) fail(SPAMM_E_UNSUPPORTED, "tensor-core precision forms are built for bs = 64");
-  const int64_t want = M->nleaves, cap = (int64_t)ctx->num_sms * 8;
-  const unsigned grid = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
-  if (prec == SPAMM_PREC_BF16_SPLIT) {
-    *terms = alloc_n<uint8_t>(ctx, M->nleaves * (int64_t)leaf_bytes<SPAMM_PREC_BF16_SPLIT>());
-    if (M->nleaves > 0) {
-      prep_terms_kernel<SPAMM_PREC_BF16_SPLIT><<<grid, 256, 0, ctx->stream>>>(
-          P<double>(M->pool), P<int64_t>(M->slot), M->nleaves, role, P<uint8_t>(*terms), nullptr);
-      CK_LAUNCH("prep_terms_kernel<bf16>");
-    }
-  } else {
-    *terms = alloc_n<uint8_t>(ctx, M->nleaves * (int64_t)leaf_bytes<SPAMM_PREC_FP16_SCALED>());
-    *expo = alloc_n<int32_t>(ctx, M->nleaves);
-    if (M->nleaves > 0) {
-      prep_terms_kernel<SPAMM_PREC_FP16_SCALED><<<grid, 256, 0, ctx->stream>>>(
-          P<double>(M->pool), P<int64_t>(M->slot), M->nleaves, role, P<uint8_t>(*terms), P<int32_t>(*expo));
-      CK_LAUNCH("prep_terms_kernel<fp16>");
-    }
-  }
 }
 
 template <int PREC>
