@@ -1,0 +1,113 @@
+// steps.cu -- the plan-time step list of the tensor-core leaf GEMM: for every
+// quad of output leaves (2I + h, 2J + c), the four kept-product runs merged by
+// k, one 32-byte record per k step (the leaves to load, each child's scale),
+// so the GEMM reads its steps sequentially.
+#include "internal.cuh"
+
+namespace spamm {
+
+// ------------------------------------------------------------- quad steps
+// The four kept-product runs of a quad (child c = 2h + cj, tasks of one C leaf
+// in ascending k) merged by k.
+struct QuadMerge {
+  int64_t p[4], e[4];
+  __device__ QuadMerge(const int32_t* g, const int64_t* gstart) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      p[c] = g[c] >= 0 ? gstart[g[c]] : 0;
+      e[c] = g[c] >= 0 ? gstart[g[c] + 1] : 0;
+    }
+  }
+  __device__ bool more() const { return p[0] < e[0] || p[1] < e[1] || p[2] < e[2] || p[3] < e[3]; }
+  // advance past the next k; bit c of the result: child c has a kept product there, task q[c]
+  __device__ unsigned next(const int32_t* ta, const uint32_t* codeA, int64_t* q) {
+    uint32_t k[4];
+    uint32_t kmin = 0xFFFFFFFFu;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      k[c] = p[c] < e[c] ? code_col(codeA[ta[p[c]]]) : 0xFFFFFFFFu;
+      kmin = k[c] < kmin ? k[c] : kmin;
+    }
+    unsigned has = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      q[c] = p[c];
+      if (k[c] == kmin) {
+        has |= 1u << c;
+        ++p[c];
+      }
+    }
+    return has;
+  }
+};
+
+// One thread per quad.  Count pass (out == null): count[Q] = its steps.
+// Write pass: its steps at out[qstart[Q] ...].
+__global__ void quad_steps_kernel(int64_t nquads, const int32_t* __restrict__ quads, const int64_t* __restrict__ gstart,
+                                  const int32_t* __restrict__ ta, const int32_t* __restrict__ tb,
+                                  const uint32_t* __restrict__ codeA, const int32_t* __restrict__ expA,
+                                  const int32_t* __restrict__ expB, uint64_t* __restrict__ count,
+                                  const uint64_t* __restrict__ qstart, QuadStep* __restrict__ out) {
+  for (int64_t Q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; Q < nquads; Q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t g[4] = {quads[4 * Q], quads[4 * Q + 1], quads[4 * Q + 2], quads[4 * Q + 3]};
+    QuadMerge m(g, gstart);
+    QuadStep* o = out ? out + qstart[Q] : nullptr;
+    int64_t s = 0;
+    while (m.more()) {
+      int64_t q[4];
+      const unsigned has = m.next(ta, codeA, q);
+      if (o) {
+        QuadStep st;
+        // children 0/1 share the A leaf of row half 0, 2/3 that of half 1; 0/2 and 1/3 share B leaves
+        st.a[0] = (has & 1u) ? ta[q[0]] : ((has & 2u) ? ta[q[1]] : -1);
+        st.a[1] = (has & 4u) ? ta[q[2]] : ((has & 8u) ? ta[q[3]] : -1);
+        st.b[0] = (has & 1u) ? tb[q[0]] : ((has & 4u) ? tb[q[2]] : -1);
+        st.b[1] = (has & 2u) ? tb[q[1]] : ((has & 8u) ? tb[q[3]] : -1);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float sc = 0.f;
+          if (has & (1u << c)) {
+            sc = 1.f;
+            if (expA) {
+              // 2^-(eA + eB) as a product of two normal powers of two (|e| <= 120)
+              const int ea = expA[ta[q[c]]], eb = expB[tb[q[c]]];
+              sc = __int_as_float((127 - ea) << 23) * __int_as_float((127 - eb) << 23);
+            }
+          }
+          st.scale[c] = sc;
+        }
+        o[s] = st;
+      }
+      ++s;
+    }
+    if (count) count[Q] = (uint64_t)s;
+  }
+}
+
+int64_t build_quad_steps(spamm_ctx ctx, const TaskList& T, const uint32_t* codeA, const int32_t* expA,
+                         const int32_t* expB, BufP* qstart, BufP* qsteps) {
+  const int64_t nq = T.ngroups > 0 ? T.nquads : 0;
+  *qstart = alloc_n<uint64_t>(ctx, nq + 1);
+  *qsteps = nullptr;
+  if (nq == 0) {
+    CK(cudaMemsetAsync(P<uint64_t>(*qstart), 0, sizeof(uint64_t), ctx->stream));
+    return 0;
+  }
+  BufP cnt = alloc_n<uint64_t>(ctx, nq);
+  const int64_t want = (nq + 255) / 256, cap = (int64_t)ctx->num_sms * 16;
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  quad_steps_kernel<<<grid, 256, 0, ctx->stream>>>(nq, P<int32_t>(T.quads), P<int64_t>(T.gstart), P<int32_t>(T.ta),
+                                                   P<int32_t>(T.tb), codeA, expA, expB, P<uint64_t>(cnt), nullptr,
+                                                   nullptr);
+  CK_LAUNCH("quad_steps_kernel(count)");
+  scan_exclusive_u64(ctx, P<uint64_t>(cnt), P<uint64_t>(*qstart), nq, P<uint64_t>(*qstart) + nq);
+  const int64_t total = (int64_t)read_scalar(ctx, P<uint64_t>(*qstart) + nq);
+  *qsteps = alloc_n<QuadStep>(ctx, total);
+  quad_steps_kernel<<<grid, 256, 0, ctx->stream>>>(nq, P<int32_t>(T.quads), P<int64_t>(T.gstart), P<int32_t>(T.ta),
+                                                   P<int32_t>(T.tb), codeA, expA, expB, nullptr,
+                                                   P<uint64_t>(*qstart), P<QuadStep>(*qsteps));
+  CK_LAUNCH("quad_steps_kernel(write)");
+  return total;
+}
+
+}  // namespace spamm
