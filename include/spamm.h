@@ -15,7 +15,7 @@
  * Conventions shared by every call
  * --------------------------------
  * - Matrices are n x n, FP64.  A matrix handle (spamm_mat) is a quadtree whose
- *   leaves are dense bs x bs row-major FP64 blocks, bs in {32, 64, 128}; a leaf
+ *   leaves are dense bs x bs row-major FP64 blocks, bs in {32, 64, 128, 256}; a leaf
  *   is stored iff it has at least one non-zero element and a null sub-matrix is
  *   never stored (Sections 4.2 and 4.4).  Every node carries its squared
  *   Frobenius norm, parents being the sums of their four children (Section 2).
@@ -61,7 +61,7 @@ typedef struct spamm_mat_s* spamm_mat;
 
 typedef enum {
   SPAMM_OK = 0,
-  SPAMM_E_INVALID_ARG = 1, /* bad size, tau < 0 or NaN, bs not 32/64/128, NULL pointer, index out of range */
+  SPAMM_E_INVALID_ARG = 1, /* bad size, tau < 0 or NaN, bs not 32/64/128/256, NULL pointer, index out of range */
   SPAMM_E_SHAPE = 2,       /* operands disagree in n or bs */
   SPAMM_E_NONFINITE = 3,   /* an input element is Inf or NaN */
   SPAMM_E_OOM = 4,         /* device allocation failed */
@@ -364,7 +364,7 @@ SPAMM_API spamm_status spamm_gather_leaves(spamm_ctx ctx, spamm_mat m, int64_t n
  * overlaps on the GPU race: order them on one stream or synchronise between
  * them.  Each call writes every scratch entry it reads before reading it.
  * Errors: SPAMM_E_CAPACITY if nleaves > SPAMM_NOALLOC_MAX_LEAVES,
- * SPAMM_E_INVALID_ARG (bs not 32/64/128, nleaves < 0, NULL pointer),
+ * SPAMM_E_INVALID_ARG (bs not 32/64/128/256, nleaves < 0, NULL pointer),
  * SPAMM_E_CUDA (set-up or launch failed). */
 SPAMM_API spamm_status spamm_leaf_sqnorms_noalloc(const double* payload, int64_t nleaves, int bs, double* sq_out,
                                                   double* total_out, void* cuda_stream);

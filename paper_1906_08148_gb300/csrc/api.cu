@@ -52,7 +52,7 @@ void need(bool ok, const char* what) {
   if (!ok) fail(SPAMM_E_INVALID_ARG, what);
 }
 
-void check_bs(int bs) { need(bs == 32 || bs == 64 || bs == 128, "bs must be 32, 64 or 128"); }
+void check_bs(int bs) { need(bs == 32 || bs == 64 || bs == 128 || bs == 256, "bs must be 32, 64, 128 or 256"); }
 void check_tau(double tau) { need(std::isfinite(tau) && tau >= 0.0, "tau must be finite and >= 0"); }
 void check_rule(spamm_trunc_rule r) {
   need(r == SPAMM_TRUNC_BLOCK_FROB || r == SPAMM_TRUNC_ELEMENT || r == SPAMM_TRUNC_ERROR_CONTROL,
@@ -319,8 +319,8 @@ size_t held_bytes(const spamm_plan_s& p) {
 void check_form(spamm_prec prec, int bs) {
   need(prec == SPAMM_PREC_FP64 || prec == SPAMM_PREC_BF16_SPLIT || prec == SPAMM_PREC_FP16_SCALED,
        "unknown precision form");
-  if (prec == SPAMM_PREC_FP64 && bs > 128)
-    fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32, 64 and 128");
+  if (prec == SPAMM_PREC_FP64 && bs > 256)
+    fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32, 64, 128 and 256");
   if (prec != SPAMM_PREC_FP64 && bs != 64)
     fail(SPAMM_E_UNSUPPORTED, "tensor-core precision forms are built for bs = 64");
 }

@@ -13,7 +13,12 @@
 // FP64 mma.sync path on this part).  Leaves up to 64 x 64 are staged whole;
 // a 128 x 128 leaf (128 KB) in K-panels of KP = 32: A's panel as 128 row
 // segments of 256 bytes, B's as 32 whole rows (one copy), each leaf product
-// then four steps in the same ascending k order.
+// then four steps in the same ascending k order.  A 256 x 256 leaf (512 KB)
+// is computed as four 128 x 128 quadrants of the output leaf, one after the
+// other by the same CTA (so the leaf still has one owner and its norm one
+// summation order); a quadrant is the sum over the kept k of eight K-panel
+// steps, A's panel as 128 row segments of 256 bytes and B's as 32 row
+// segments of 1 KB.
 #include "internal.cuh"
 #include "ptx.cuh"
 
@@ -21,14 +26,16 @@ namespace spamm {
 
 constexpr int kGemmThreads = 256;
 
-template <int BS, int KP>
+template <int BS, int KP, int TILE>
 __global__ void __launch_bounds__(kGemmThreads)
     gemm_fp64_kernel(BatchDev batch, unsigned long long* __restrict__ work, int* __restrict__ err) {
   constexpr int LEAF = BS * BS;
   constexpr int NP = BS / KP;                     // K-panels per leaf product
-  constexpr int PANEL = BS * KP;                  // doubles in one A panel (and one B panel)
+  constexpr int NQ = (BS / TILE) * (BS / TILE);   // output quadrants per leaf (1 or 4)
+  constexpr int PANEL = TILE * KP;                // doubles in one A panel (and one B panel)
   constexpr uint32_t PANEL_BYTES = PANEL * sizeof(double);
-  constexpr int TM = BS / 16;  // per-thread tile TM x TM: rows tr + 16 i, cols tc + 16 j
+  constexpr int TM = TILE / 16;  // per-thread tile TM x TM: rows tr + 16 i, cols tc + 16 j
+  static_assert(BS % TILE == 0 && BS % KP == 0 && TILE % 16 == 0, "tile shape");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double* sA[2] = {reinterpret_cast<double*>(smem_raw), reinterpret_cast<double*>(smem_raw) + 2 * PANEL};
   double* sB[2] = {reinterpret_cast<double*>(smem_raw) + PANEL, reinterpret_cast<double*>(smem_raw) + 3 * PANEL};
@@ -58,28 +65,52 @@ __global__ void __launch_bounds__(kGemmThreads)
     const PlanDev& pl = batch.plans[r];
     const int64_t g = u - batch.ubegin[r];
     const int64_t q0 = pl.gstart[g], q1 = pl.gstart[g + 1];
-    // step t: task q0 + t / NP, K-panel t % NP
+    const int64_t per_quad = (q1 - q0) * NP;  // steps of one output quadrant
+    // step t: quadrant t / per_quad, task q0 + (t % per_quad) / NP, K-panel t % NP
     auto issue = [&](int64_t t, int s) {
-      const int64_t q = q0 + t / NP;
-      const int p = (int)(t % NP);
-      const double* a = pl.poolA + pl.slotA[pl.ta[q]] * LEAF + p * KP;
-      const double* b = pl.poolB + pl.slotB[pl.tb[q]] * LEAF + (int64_t)p * KP * BS;
+      const int qd = (int)(t / per_quad);
+      const int64_t w = t - qd * per_quad;
+      const int64_t q = q0 + w / NP;
+      const int p = (int)(w % NP);
+      const int64_t r0 = (int64_t)(qd / (BS / TILE)) * TILE, c0 = (int64_t)(qd % (BS / TILE)) * TILE;
+      const double* a = pl.poolA + pl.slotA[pl.ta[q]] * LEAF + r0 * BS + p * KP;
+      const double* b = pl.poolB + pl.slotB[pl.tb[q]] * LEAF + (int64_t)p * KP * BS + c0;
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(&bar[s], 2 * PANEL_BYTES);
       if constexpr (NP == 1) {
         bulk_g2s(sA[s], a, PANEL_BYTES, &bar[s]);
       } else {
-        for (int row = 0; row < BS; ++row)
+        for (int row = 0; row < TILE; ++row)
           bulk_g2s(sA[s] + row * KP, a + (int64_t)row * BS, KP * sizeof(double), &bar[s]);
       }
-      bulk_g2s(sB[s], b, PANEL_BYTES, &bar[s]);
+      if constexpr (TILE == BS) {
+        bulk_g2s(sB[s], b, PANEL_BYTES, &bar[s]);
+      } else {
+        for (int row = 0; row < KP; ++row)
+          bulk_g2s(sB[s] + row * TILE, b + (int64_t)row * BS, TILE * sizeof(double), &bar[s]);
+      }
     };
     double acc[TM][TM];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TM; ++j) acc[i][j] = 0.0;
-    const int64_t nsteps = (q1 - q0) * NP;
+    double* C = pl.cpool + g * LEAF;
+    double s2 = 0.0;
+    // write output quadrant qd from the accumulators (and add its squares to
+    // this thread's share of the leaf's squared norm, kernel (d))
+    auto store_quad = [&](int qd) {
+      double* Cq = C + (int64_t)(qd / (BS / TILE)) * TILE * BS + (qd % (BS / TILE)) * TILE;
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TM; ++j) {
+          Cq[(tr + 16 * i) * BS + tc + 16 * j] = acc[i][j];
+          s2 = __fma_rn(acc[i][j], acc[i][j], s2);
+          acc[i][j] = 0.0;
+        }
+    };
+    const int64_t nsteps = per_quad * NQ;
     if (tid == 0 && nsteps > 0) issue(0, 0);
     inflight |= 1u;
     for (int64_t t = 0; t < nsteps; ++t) {
@@ -105,26 +136,26 @@ __global__ void __launch_bounds__(kGemmThreads)
 #pragma unroll
         for (int i = 0; i < TM; ++i) a[i] = As[(tr + 16 * i) * KP + kk];
 #pragma unroll
-        for (int j = 0; j < TM; ++j) b[j] = Bs[kk * BS + tc + 16 * j];
+        for (int j = 0; j < TM; ++j) b[j] = Bs[kk * TILE + tc + 16 * j];
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
           for (int j = 0; j < TM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
       }
       __syncthreads();
+      if constexpr (NQ > 1) {
+        if ((t + 1) % per_quad == 0 && t + 1 < nsteps) store_quad((int)(t / per_quad));
+      }
     }
     if (nsteps <= 0) inflight &= ~1u;
     if (s_abort) break;
-    // epilogue: write C leaf g and its squared Frobenius norm (kernel (d))
-    double* C = pl.cpool + g * LEAF;
-    double s2 = 0.0;
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-      for (int j = 0; j < TM; ++j) {
-        C[(tr + 16 * i) * BS + tc + 16 * j] = acc[i][j];
-        s2 = __fma_rn(acc[i][j], acc[i][j], s2);
-      }
+    // epilogue: the last quadrant (every quadrant, as zeros, for an empty
+    // task list), then the leaf's squared Frobenius norm
+    if (nsteps > 0) {
+      store_quad(NQ - 1);
+    } else {
+      for (int qd = 0; qd < NQ; ++qd) store_quad(qd);
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
     if (lane == 0) s_red[warp] = s2;
@@ -146,17 +177,19 @@ __global__ void __launch_bounds__(kGemmThreads)
 template <int BS>
 static void launch_fp64(spamm_ctx ctx, const BatchDev& b) {
   constexpr int KP = BS <= 64 ? BS : 32;
-  const size_t smem = 4 * (size_t)BS * KP * sizeof(double);
-  CK(cudaFuncSetAttribute(gemm_fp64_kernel<BS, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  constexpr int TILE = BS <= 128 ? BS : 128;
+  auto kern = gemm_fp64_kernel<BS, KP, TILE>;
+  const size_t smem = 4 * (size_t)TILE * KP * sizeof(double);
+  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_fp64_kernel<BS, KP>, kGemmThreads, smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGemmThreads, smem));
   if (per_sm < 1) per_sm = 1;
   const int sms = ctx->gemm_sm_limit > 0 ? ctx->gemm_sm_limit : ctx->num_sms;
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > b.nunits) grid = b.nunits;
   unsigned long long* work = ctx->d_scratch + 8;
   CK(cudaMemsetAsync(work, 0, sizeof(unsigned long long), ctx->stream));
-  gemm_fp64_kernel<BS, KP><<<(unsigned)grid, kGemmThreads, smem, ctx->stream>>>(b, work, ctx->d_err);
+  kern<<<(unsigned)grid, kGemmThreads, smem, ctx->stream>>>(b, work, ctx->d_err);
   CK_LAUNCH("gemm_fp64_kernel");
 }
 
@@ -166,7 +199,8 @@ void gemm_fp64_batch(spamm_ctx ctx, int bs, const BatchDev& b) {
     case 32: launch_fp64<32>(ctx, b); break;
     case 64: launch_fp64<64>(ctx, b); break;
     case 128: launch_fp64<128>(ctx, b); break;
-    default: fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32, 64 and 128");
+    case 256: launch_fp64<256>(ctx, b); break;
+    default: fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32, 64, 128 and 256");
   }
 }
 

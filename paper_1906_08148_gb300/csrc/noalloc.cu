@@ -82,7 +82,7 @@ spamm_status partials_address(int device, double** out) {
 
 extern "C" spamm_status spamm_leaf_sqnorms_noalloc(const double* payload, int64_t nleaves, int bs, double* sq_out,
                                                    double* total_out, void* cuda_stream) {
-  if (bs != 32 && bs != 64 && bs != 128) return SPAMM_E_INVALID_ARG;
+  if (bs != 32 && bs != 64 && bs != 128 && bs != 256) return SPAMM_E_INVALID_ARG;
   if (nleaves < 0 || !total_out || (nleaves > 0 && (!payload || !sq_out))) return SPAMM_E_INVALID_ARG;
   if (nleaves > SPAMM_NOALLOC_MAX_LEAVES) return SPAMM_E_CAPACITY;
   int device = 0;

@@ -86,7 +86,7 @@ def _assert_kept_parity(ikj_gpu, ikj_orc, A: oracle.LeafMatrix, B: oracle.LeafMa
 
 
 # ----------------------------------------------------------- building (a)
-@pytest.mark.parametrize("n,bs", [(2048, 32), (4096, 64), (1000, 32), (300, 128)])
+@pytest.mark.parametrize("n,bs", [(2048, 32), (4096, 64), (1000, 32), (300, 128), (700, 256)])
 def test_from_dense_leaves_norms_and_parents(S, ctx, n, bs):
     A, _ = _dense_pair(n, 0.7)
     G = S.spamm_from_dense(ctx, A, bs)
@@ -247,7 +247,8 @@ def test_kept_tasks_are_grouped_by_c_leaf_in_morton_order(S, ctx):
     assert np.all(np.diff(ikj[:, 1])[same] > 0), "k must ascend within a C leaf"
 
 
-@pytest.mark.parametrize("n,bs,alpha", [(4096, 64, 1.0), (3000, 32, 0.8), (5000, 64, 0.6), (2048, 128, 0.8), (1500, 128, 1.0)])
+@pytest.mark.parametrize("n,bs,alpha", [(4096, 64, 1.0), (3000, 32, 0.8), (5000, 64, 0.6), (2048, 128, 0.8), (1500, 128, 1.0),
+                                         (3000, 256, 0.8), (1500, 256, 1.0)])
 @pytest.mark.parametrize("mode", ["spamm", "truncate", "combined"])
 def test_lattice_parity_all_methods(S, ctx, n, bs, alpha, mode):
     pa, pb = synth.lattice_3d(n, alpha=alpha, seed=1), synth.lattice_3d(n, alpha=alpha, seed=2)
@@ -278,7 +279,7 @@ def test_tau_zero_is_the_dense_product(S, ctx):
     assert np.linalg.norm(D - ref) <= 1e-13 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("bs,fill", [(32, 0.05), (64, 0.3), (32, 0.9)])
+@pytest.mark.parametrize("bs,fill", [(32, 0.05), (64, 0.3), (32, 0.9), (256, 0.5)])
 @pytest.mark.parametrize("prec", ["fp64", "bf16_split", "fp16_scaled"])
 def test_random_block_sparse_tau_zero(S, ctx, bs, fill, prec):
     """Section 5.2's leaf-library workload: uniformly placed random blocks,
