@@ -299,6 +299,7 @@ struct spamm_plan_s {
   TaskList T;
   BufP poolA, slotA, poolB, slotB, termsA, termsB, expA, expB;
   BufP qstart, qsteps;  // tensor forms: the quad step list
+  BufP uorder;          // FP64 form: unit -> output leaf, longest first (empty: identity)
   int64_t nsteps = 0;
   std::vector<Level> cskel;  // output quadtree structure (codes, child links; no norms)
   int64_t na = 0, nb = 0;
@@ -311,7 +312,7 @@ namespace {
 size_t held_bytes(const spamm_plan_s& p) {
   size_t b = 0;
   for (const BufP* x : {&p.T.gcode, &p.T.gstart, &p.T.ta, &p.T.tb, &p.T.quads, &p.qstart, &p.qsteps, &p.slotA, &p.slotB, &p.termsA,
-                        &p.termsB, &p.expA, &p.expB})
+                        &p.termsB, &p.expA, &p.expB, &p.uorder})
     if (*x) b += (*x)->bytes;
   return b;
 }
@@ -358,6 +359,7 @@ spamm_plan make_plan(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_
     p->slotA = At->slot;
     p->poolB = Bt->pool;
     p->slotB = Bt->slot;
+    p->uorder = fp64_unit_order(ctx, p->T, p->bs);
   } else {
     prep_terms(At, prec, 0, &p->termsA, &p->expA, ctx);
     prep_terms(Bt, prec, 1, &p->termsB, &p->expB, ctx);
@@ -440,6 +442,7 @@ std::vector<spamm_mat> execute_plans(spamm_ctx ctx, const std::vector<spamm_plan
     d.qsteps = P<QuadStep>(p.qsteps);
     d.cpool = P<double>(Cm->pool);
     d.csq = P<double>(Cm->lv[Cm->L].sq);
+    d.uorder = P<int64_t>(p.uorder);
     // work units: output leaves for the FP64 kernel, quads of output leaves for the tensor-core kernel
     const int64_t units = p.T.ngroups == 0 ? 0 : (prec == SPAMM_PREC_FP64 ? p.T.ngroups : p.T.nquads);
     ubegin[r + 1] = ubegin[r] + units;

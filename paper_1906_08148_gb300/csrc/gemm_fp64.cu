@@ -5,7 +5,9 @@
 // work item (Algorithm 1, "C = AB" at the lowest level, run batched over the
 // task list as Section 4.4 describes).  The output leaves of every plan in a
 // batch form one work list; persistent CTAs claim them from an atomic
-// counter.  Every output leaf is owned by one CTA, so there are no atomics on
+// counter (for 128 and 256 leaves, whose output leaves take milliseconds each,
+// in order of decreasing kept-product count, so the last claims are short).
+// Every output leaf is owned by one CTA, so there are no atomics on
 // C and the k order is fixed (results do not depend on the schedule or on the
 // batch).  Operand leaves are contiguous bs*bs FP64 blocks staged in shared
 // memory by 1-D TMA bulk copies, double-buffered on mbarriers; the product is
@@ -25,6 +27,10 @@
 namespace spamm {
 
 constexpr int kGemmThreads = 256;
+// sort key of an output leaf: kUnitKeyMax - its kept-product count (at most
+// 2^16, the leaf grid side), so an ascending stable sort puts the longest first
+constexpr int kUnitKeyBits = 18;
+constexpr int64_t kUnitKeyMax = (int64_t)1 << 17;
 
 template <int BS, int KP, int TILE>
 __global__ void __launch_bounds__(kGemmThreads)
@@ -63,10 +69,11 @@ __global__ void __launch_bounds__(kGemmThreads)
     if (u >= batch.nunits || s_abort) break;
     const int r = plan_of(batch.ubegin, batch.nplans, u);
     const PlanDev& pl = batch.plans[r];
-    const int64_t g = u - batch.ubegin[r];
+    const int64_t g = pl.uorder ? pl.uorder[u - batch.ubegin[r]] : u - batch.ubegin[r];
     const int64_t q0 = pl.gstart[g], q1 = pl.gstart[g + 1];
     const int64_t per_quad = (q1 - q0) * NP;  // steps of one output quadrant
-    // step t: quadrant t / per_quad, task q0 + (t % per_quad) / NP, K-panel t % NP
+    // step t: quadrant t / per_quad, task q0 + (t % per_quad) / NP, K-panel t % NP;
+    // issued by the 32 lanes of warp 0 (lane 0 arms the barrier first)
     auto issue = [&](int64_t t, int s) {
       const int qd = (int)(t / per_quad);
       const int64_t w = t - qd * per_quad;
@@ -76,17 +83,18 @@ __global__ void __launch_bounds__(kGemmThreads)
       const double* a = pl.poolA + pl.slotA[pl.ta[q]] * LEAF + r0 * BS + p * KP;
       const double* b = pl.poolB + pl.slotB[pl.tb[q]] * LEAF + (int64_t)p * KP * BS + c0;
       fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&bar[s], 2 * PANEL_BYTES);
+      if (lane == 0) mbar_arrive_expect_tx(&bar[s], 2 * PANEL_BYTES);
+      __syncwarp();
       if constexpr (NP == 1) {
-        bulk_g2s(sA[s], a, PANEL_BYTES, &bar[s]);
+        if (lane == 0) bulk_g2s(sA[s], a, PANEL_BYTES, &bar[s]);
       } else {
-        for (int row = 0; row < TILE; ++row)
+        for (int row = lane; row < TILE; row += 32)
           bulk_g2s(sA[s] + row * KP, a + (int64_t)row * BS, KP * sizeof(double), &bar[s]);
       }
       if constexpr (TILE == BS) {
-        bulk_g2s(sB[s], b, PANEL_BYTES, &bar[s]);
+        if (lane == 0) bulk_g2s(sB[s], b, PANEL_BYTES, &bar[s]);
       } else {
-        for (int row = 0; row < KP; ++row)
+        for (int row = lane; row < KP; row += 32)
           bulk_g2s(sB[s] + row * TILE, b + (int64_t)row * BS, TILE * sizeof(double), &bar[s]);
       }
     };
@@ -111,12 +119,12 @@ __global__ void __launch_bounds__(kGemmThreads)
         }
     };
     const int64_t nsteps = per_quad * NQ;
-    if (tid == 0 && nsteps > 0) issue(0, 0);
+    if (warp == 0 && nsteps > 0) issue(0, 0);
     inflight |= 1u;
     for (int64_t t = 0; t < nsteps; ++t) {
       const int s = (int)(t & 1);
       if (t + 1 < nsteps) {
-        if (tid == 0) issue(t + 1, s ^ 1);
+        if (warp == 0) issue(t + 1, s ^ 1);
         inflight |= 1u << (s ^ 1);
       }
       if (!mbar_wait_bounded(&bar[s], phase[s])) {
@@ -191,6 +199,27 @@ static void launch_fp64(spamm_ctx ctx, const BatchDev& b) {
   CK(cudaMemsetAsync(work, 0, sizeof(unsigned long long), ctx->stream));
   kern<<<(unsigned)grid, kGemmThreads, smem, ctx->stream>>>(b, work, ctx->d_err);
   CK_LAUNCH("gemm_fp64_kernel");
+}
+
+__global__ void unit_order_keys_kernel(const int64_t* __restrict__ gstart, int64_t ng, uint64_t* __restrict__ keys,
+                                       int64_t* __restrict__ vals) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = gstart[g + 1] - gstart[g];
+    keys[g] = (uint64_t)(kUnitKeyMax - (c < kUnitKeyMax ? c : kUnitKeyMax));
+    vals[g] = g;
+  }
+}
+
+BufP fp64_unit_order(spamm_ctx ctx, const TaskList& T, int bs) {
+  if (bs < 128 || T.ngroups <= 1) return BufP();
+  BufP keys = alloc_n<uint64_t>(ctx, T.ngroups), vals = alloc_n<int64_t>(ctx, T.ngroups);
+  int64_t grid = (T.ngroups + 255) / 256;
+  if (grid > 4 * (int64_t)ctx->num_sms) grid = 4 * (int64_t)ctx->num_sms;
+  unit_order_keys_kernel<<<(unsigned)grid, 256, 0, ctx->stream>>>(P<int64_t>(T.gstart), T.ngroups, P<uint64_t>(keys),
+                                                                 P<int64_t>(vals));
+  CK_LAUNCH("unit_order_keys_kernel");
+  radix_sort_pairs(ctx, P<uint64_t>(keys), P<int64_t>(vals), T.ngroups, kUnitKeyBits);
+  return vals;
 }
 
 void gemm_fp64_batch(spamm_ctx ctx, int bs, const BatchDev& b) {

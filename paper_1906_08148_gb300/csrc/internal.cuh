@@ -210,6 +210,7 @@ struct PlanDev {
   const QuadStep* qsteps;
   double* cpool;
   double* csq;
+  const int64_t* uorder;  // FP64 form: output leaf of each work unit (longest first), or null for identity
 };
 struct BatchDev {
   const PlanDev* plans;
@@ -230,6 +231,10 @@ __device__ __forceinline__ int plan_of(const int64_t* __restrict__ ubegin, int n
   return lo;
 }
 void gemm_fp64_batch(spamm_ctx ctx, int bs, const BatchDev& b);
+// Output leaves ordered by their number of kept products, largest first
+// (stable), for the FP64 kernel's unit claiming; an empty buffer when the
+// leaves are small enough that the claiming tail does not matter.
+BufP fp64_unit_order(spamm_ctx ctx, const TaskList& T, int bs);
 void gemm_fp16_batch(spamm_ctx ctx, const BatchDev& b);
 void gemm_bf16_batch(spamm_ctx ctx, const BatchDev& b);
 // Operand terms of a leaf set for a tensor form (role 0: used as A, 1: as B).
