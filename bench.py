@@ -766,13 +766,18 @@ def run_e2e(S, ctx, GA, GB, args, bs, torch, np):
         S.spamm_to_blocks(ctx, GB, out=hB)
     hC = None
     times, flops, h2d, d2h = [], 0.0, 0, 0
+    phase = {"from_blocks_s": 0.0, "multiply_s": 0.0, "to_blocks_s": 0.0}
     n = ia["n"]
     for it in range(args.e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         A = S.spamm_from_blocks(ctx, n, bs, hA[0], hA[1], hA[2])
         B = A if hB is hA else S.spamm_from_blocks(ctx, n, bs, hB[0], hB[1], hB[2])
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         C, st = S.spamm_multiply(ctx, A, B, args.tau, args.mode, args.prec, stats=True)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
         nc = C.info()["nleaves"]
         if hC is None or len(hC[0]) < nc:
             hC = (pinned(nc, torch.int32), pinned(nc, torch.int32), pinned((nc, bs, bs), torch.float64),
@@ -787,14 +792,18 @@ def run_e2e(S, ctx, GA, GB, args, bs, torch, np):
             continue
         S.spamm_to_blocks(ctx, C, out=hC)
         torch.cuda.synchronize()
-        times.append(time.perf_counter() - t0)
+        t3 = time.perf_counter()
+        times.append(t3 - t0)
+        for k, v in zip(phase, (t1 - t0, t2 - t1, t3 - t2)):
+            phase[k] += v
         flops += st["kept_flops"]
         h2d = hA[2].nbytes + 8 * len(hA[0]) + (0 if hB is hA else hB[2].nbytes + 8 * len(hB[0]))
         d2h = 8 * nc * e + 16 * nc
         for m in {id(C): C, id(A): A, id(B): B}.values():
             m.close()
     return {"value": flops / sum(times) / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "steps": len(times), "ms_per_step": 1e3 * sum(times) / len(times)}
+            "d2h_bytes_per_step": d2h, "steps": len(times), "ms_per_step": 1e3 * sum(times) / len(times),
+            "phases_s_per_step": {k: v / len(times) for k, v in phase.items()}}
 
 
 if __name__ == "__main__":
