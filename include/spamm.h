@@ -165,6 +165,14 @@ SPAMM_API spamm_status spamm_set_allocator(spamm_ctx ctx, void* (*alloc)(size_t 
 /* Block until all work of `ctx` is done; reports a pending device error. */
 SPAMM_API spamm_status spamm_sync(spamm_ctx ctx);
 
+/* Wait for the context stream, then return to the driver the device memory
+ * that the device's stream-ordered pool keeps cached from freed blocks
+ * (cudaMemPoolTrimTo(pool, 0); the library sets that pool to keep freed
+ * memory).  Live handles are untouched.  With an allocator installed by
+ * spamm_set_allocator the pool is not the library's and nothing is trimmed.
+ * Errors: INVALID_ARG (ctx NULL), CUDA. */
+SPAMM_API spamm_status spamm_trim(spamm_ctx ctx);
+
 /* Message of the last failing call on `ctx` ("" if none).  Owned by ctx. */
 SPAMM_API const char* spamm_last_error(spamm_ctx ctx);
 

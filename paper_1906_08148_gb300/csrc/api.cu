@@ -174,6 +174,17 @@ spamm_status spamm_sync(spamm_ctx ctx) {
   return guarded(ctx, [&] { sync_and_check(ctx); });
 }
 
+spamm_status spamm_trim(spamm_ctx ctx) {
+  if (!ctx) return SPAMM_E_INVALID_ARG;
+  return guarded(ctx, [&] {
+    sync_and_check(ctx);
+    if (ctx->ualloc) return;
+    cudaMemPool_t pool;
+    CK(cudaDeviceGetDefaultMemPool(&pool, ctx->device));
+    CK(cudaMemPoolTrimTo(pool, 0));
+  });
+}
+
 const char* spamm_last_error(spamm_ctx ctx) { return ctx ? ctx->last_error.c_str() : "invalid context"; }
 
 spamm_status spamm_from_dense(spamm_ctx ctx, int64_t n, const double* a, int64_t lda, int on_device, int bs,

@@ -35,7 +35,7 @@ ENTRY_POINTS = (
     "spamm_multiply", "spamm_kept_tasks", "spamm_frob_norm", "spamm_error", "spamm_mat_info", "spamm_to_dense",
     "spamm_to_blocks", "spamm_gather_leaves", "spamm_level_norms", "spamm_leaf_sqnorms_noalloc",
     "spamm_plan_create", "spamm_plan_info", "spamm_execute", "spamm_plan_release", "spamm_set_gemm_sms",
-    "spamm_set_exec_graph", "spamm_add", "spamm_identity", "spamm_trace", "spamm_check_timeout_path",
+    "spamm_set_exec_graph", "spamm_add", "spamm_identity", "spamm_trace", "spamm_check_timeout_path", "spamm_trim",
 )
 NOALLOC_MAX_LEAVES = 1 << 24
 
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
         "spamm_set_stream": [vp, vp],
         "spamm_set_allocator": [vp, _ALLOC_T, _FREE_T, vp],
         "spamm_sync": [vp],
+        "spamm_trim": [vp],
         "spamm_from_dense": [vp, i64, vp, i64, ctypes.c_int, ctypes.c_int, f64, ctypes.c_int, ctypes.POINTER(vp)],
         "spamm_from_blocks": [vp, i64, ctypes.c_int, i64, vp, vp, vp, ctypes.c_int, f64, ctypes.c_int,
                               ctypes.POINTER(vp)],
@@ -240,6 +241,11 @@ def spamm_set_allocator(ctx: Context, which: Optional[str] = "torch"):
 
 def spamm_sync(ctx: Context):
     _check(ctx.handle, load().spamm_sync(ctx.handle))
+
+
+def spamm_trim(ctx: Context):
+    """Return the device memory the stream-ordered pool keeps cached to the driver (spamm_trim)."""
+    _check(ctx.handle, load().spamm_trim(ctx.handle))
 
 
 def spamm_from_dense(ctx: Context, a, bs: int, tau: float = 0.0, rule: str = "block") -> Matrix:

@@ -143,3 +143,20 @@ def test_device_timeout_becomes_a_status_and_the_context_stays_usable(S, ctx):
     C = S.spamm_multiply(ctx, GA, GB, 1e-6, "combined", "fp64")
     D = S.spamm_multiply(ctx, GA, GB, 1e-6, "combined", "fp64")
     assert np.array_equal(S.spamm_to_blocks(ctx, C)[2], S.spamm_to_blocks(ctx, D)[2])
+
+
+def test_trim_returns_cached_pool_memory(S, ctx):
+    import torch
+    GA, GB = _inputs(S, ctx, 8192, 0.8, 64)
+    C = S.spamm_multiply(ctx, GA, GB, 1e-6, "combined")
+    ref = S.spamm_to_dense(ctx, C)
+    big = S.spamm_multiply(ctx, GA, GB, 0.0, "spamm")  # a larger output, freed below: cached by the pool
+    big.close()
+    S.spamm_sync(ctx)
+    before = torch.cuda.mem_get_info()[0]
+    S.spamm_trim(ctx)
+    after = torch.cuda.mem_get_info()[0]
+    assert after >= before
+    # live handles are untouched
+    assert np.array_equal(S.spamm_to_dense(ctx, C), ref)
+    assert S.spamm_frob_norm(ctx, C) > 0
