@@ -77,7 +77,7 @@ def parse_args():
     ap.add_argument("--sweep-precs", nargs="+", default=["fp64", "bf16_split", "fp16_scaled"])
     ap.add_argument("--block-sparse", action="store_true", help="random block-sparse sweep over fill-in")
     ap.add_argument("--bsp-n", type=int, default=2048)
-    ap.add_argument("--bsp-bs", type=int, nargs="+", default=[32, 64])
+    ap.add_argument("--bsp-bs", type=int, nargs="+", default=[32, 64, 128, 256])
     ap.add_argument("--bsp-fills", type=float, nargs="+", default=[0.05, 0.1, 0.2, 0.3, 0.5, 0.7, 0.9])
     ap.add_argument("--bsp-repeats", type=int, default=20)
     ap.add_argument("--chain", action="store_true", help="repeated squaring chain")

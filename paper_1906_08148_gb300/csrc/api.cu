@@ -427,6 +427,7 @@ std::vector<spamm_mat> execute_plans(spamm_ctx ctx, const std::vector<spamm_plan
   std::vector<spamm_mat> outp;
   std::vector<PlanDev> host(np);
   std::vector<int64_t> ubegin(np + 1, 0);
+  std::vector<BufP> parts;  // FP64 sub-tile partial norms, alive until the launches below are queued
   for (int64_t r = 0; r < np; ++r) {
     const spamm_plan_s& p = *plans[r];
     outs.emplace_back(new_mat(ctx, p.n, bs));
@@ -454,8 +455,13 @@ std::vector<spamm_mat> execute_plans(spamm_ctx ctx, const std::vector<spamm_plan
     d.cpool = P<double>(Cm->pool);
     d.csq = P<double>(Cm->lv[Cm->L].sq);
     d.uorder = P<int64_t>(p.uorder);
-    // work units: output leaves for the FP64 kernel, quads of output leaves for the tensor-core kernel
-    const int64_t units = p.T.ngroups == 0 ? 0 : (prec == SPAMM_PREC_FP64 ? p.T.ngroups : p.T.nquads);
+    // work units: output leaves (or their sub-tiles) for the FP64 kernel, quads of output leaves for the tensor-core kernel
+    const int64_t per_leaf = prec == SPAMM_PREC_FP64 ? fp64_units_per_leaf(bs) : 1;
+    if (per_leaf > 1) {
+      parts.push_back(alloc_n<double>(ctx, p.T.ngroups * per_leaf));
+      d.csq_part = P<double>(parts.back());
+    }
+    const int64_t units = p.T.ngroups == 0 ? 0 : (prec == SPAMM_PREC_FP64 ? p.T.ngroups * per_leaf : p.T.nquads);
     ubegin[r + 1] = ubegin[r] + units;
   }
   BufP dplans = alloc_n<PlanDev>(ctx, np), dub = alloc_n<int64_t>(ctx, np + 1);

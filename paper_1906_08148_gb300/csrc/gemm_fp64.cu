@@ -1,26 +1,25 @@
 // gemm_fp64.cu -- kernel (c), FP64 form, with the C-leaf norms of kernel (d)
 // fused into its epilogue.
 //
-// C_ij = sum over the kept k (ascending) of A_ik B_kj, one output leaf per
-// work item (Algorithm 1, "C = AB" at the lowest level, run batched over the
-// task list as Section 4.4 describes).  The output leaves of every plan in a
-// batch form one work list; persistent CTAs claim them from an atomic
-// counter (for 128 and 256 leaves, whose output leaves take milliseconds each,
-// in order of decreasing kept-product count, so the last claims are short).
-// Every output leaf is owned by one CTA, so there are no atomics on
-// C and the k order is fixed (results do not depend on the schedule or on the
-// batch).  Operand leaves are contiguous bs*bs FP64 blocks staged in shared
-// memory by 1-D TMA bulk copies, double-buffered on mbarriers; the product is
-// register-tiled DFMA (FP64 has no tcgen05 kind; DFMA measures faster than the
-// FP64 mma.sync path on this part).  Leaves up to 64 x 64 are staged whole;
-// a 128 x 128 leaf (128 KB) in K-panels of KP = 32: A's panel as 128 row
-// segments of 256 bytes, B's as 32 whole rows (one copy), each leaf product
-// then four steps in the same ascending k order.  A 256 x 256 leaf (512 KB)
-// is computed as four 128 x 128 quadrants of the output leaf, one after the
-// other by the same CTA (so the leaf still has one owner and its norm one
-// summation order); a quadrant is the sum over the kept k of eight K-panel
-// steps, A's panel as 128 row segments of 256 bytes and B's as 32 row
-// segments of 1 KB.
+// C_ij = sum over the kept k (ascending) of A_ik B_kj (Algorithm 1, "C = AB"
+// at the lowest level, run batched over the task list as Section 4.4
+// describes).  A work unit is one output leaf, or for 128 x 128 and 256 x 256
+// leaves one 64 x 64 sub-tile of an output leaf (4 or 16 per leaf: a leaf
+// product of that size takes milliseconds on one SM, so whole leaves would
+// leave most SMs idle on small problems).  The units of every plan in a batch
+// form one work list; persistent CTAs claim them from an atomic counter (the
+// large leaves in order of decreasing kept-product count, so the last claims
+// are short).  Every output element is computed by one CTA, so there are no
+// atomics on C and the k order is fixed (results do not depend on the schedule
+// or on the batch); a sub-tile writes its partial squared norm, and a second
+// launch adds a leaf's partials in sub-tile order.  Operand panels are staged
+// in shared memory by 1-D TMA bulk copies issued by one warp, double-buffered
+// on mbarriers; the product is register-tiled DFMA (FP64 has no tcgen05 kind;
+// DFMA measures faster than the FP64 mma.sync path on this part).  A 32 x 32
+// leaf is staged whole (one copy per operand); a 64 x 64 output tile in
+// K-panels of KP = 32 (A's panel as 64 row segments of 256 bytes, B's as 32
+// rows: one copy for 64 x 64 leaves, 32 segments of 512 bytes for larger
+// ones), so three CTAs share an SM (64 KB of shared memory each).
 #include "internal.cuh"
 #include "ptx.cuh"
 
@@ -36,12 +35,12 @@ template <int BS, int KP, int TILE>
 __global__ void __launch_bounds__(kGemmThreads)
     gemm_fp64_kernel(BatchDev batch, unsigned long long* __restrict__ work, int* __restrict__ err) {
   constexpr int LEAF = BS * BS;
-  constexpr int NP = BS / KP;                     // K-panels per leaf product
-  constexpr int NQ = (BS / TILE) * (BS / TILE);   // output quadrants per leaf (1 or 4)
-  constexpr int PANEL = TILE * KP;                // doubles in one A panel (and one B panel)
+  constexpr int NP = BS / KP;                    // K-panels per leaf product
+  constexpr int NQ = (BS / TILE) * (BS / TILE);  // work units (sub-tiles) per output leaf
+  constexpr int PANEL = TILE * KP;               // doubles in one A panel (and one B panel)
   constexpr uint32_t PANEL_BYTES = PANEL * sizeof(double);
   constexpr int TM = TILE / 16;  // per-thread tile TM x TM: rows tr + 16 i, cols tc + 16 j
-  static_assert(BS % TILE == 0 && BS % KP == 0 && TILE % 16 == 0, "tile shape");
+  static_assert(BS % TILE == 0 && BS % KP == 0 && TILE % 16 == 0 && KP % 2 == 0, "tile shape");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double* sA[2] = {reinterpret_cast<double*>(smem_raw), reinterpret_cast<double*>(smem_raw) + 2 * PANEL};
   double* sB[2] = {reinterpret_cast<double*>(smem_raw) + PANEL, reinterpret_cast<double*>(smem_raw) + 3 * PANEL};
@@ -69,23 +68,23 @@ __global__ void __launch_bounds__(kGemmThreads)
     if (u >= batch.nunits || s_abort) break;
     const int r = plan_of(batch.ubegin, batch.nplans, u);
     const PlanDev& pl = batch.plans[r];
-    const int64_t g = pl.uorder ? pl.uorder[u - batch.ubegin[r]] : u - batch.ubegin[r];
+    const int64_t lu = u - batch.ubegin[r];
+    const int64_t li = lu / NQ;  // leaf position in claiming order
+    const int sub = (int)(lu - li * NQ);
+    const int64_t g = pl.uorder ? pl.uorder[li] : li;
+    const int64_t r0 = (int64_t)(sub / (BS / TILE)) * TILE, c0 = (int64_t)(sub % (BS / TILE)) * TILE;
     const int64_t q0 = pl.gstart[g], q1 = pl.gstart[g + 1];
-    const int64_t per_quad = (q1 - q0) * NP;  // steps of one output quadrant
-    // step t: quadrant t / per_quad, task q0 + (t % per_quad) / NP, K-panel t % NP;
-    // issued by the 32 lanes of warp 0 (lane 0 arms the barrier first)
+    // step t: task q0 + t / NP, K-panel t % NP; issued by the 32 lanes of
+    // warp 0 (lane 0 arms the barrier first)
     auto issue = [&](int64_t t, int s) {
-      const int qd = (int)(t / per_quad);
-      const int64_t w = t - qd * per_quad;
-      const int64_t q = q0 + w / NP;
-      const int p = (int)(w % NP);
-      const int64_t r0 = (int64_t)(qd / (BS / TILE)) * TILE, c0 = (int64_t)(qd % (BS / TILE)) * TILE;
+      const int64_t q = q0 + t / NP;
+      const int p = (int)(t % NP);
       const double* a = pl.poolA + pl.slotA[pl.ta[q]] * LEAF + r0 * BS + p * KP;
       const double* b = pl.poolB + pl.slotB[pl.tb[q]] * LEAF + (int64_t)p * KP * BS + c0;
       fence_proxy_async_smem();
       if (lane == 0) mbar_arrive_expect_tx(&bar[s], 2 * PANEL_BYTES);
       __syncwarp();
-      if constexpr (NP == 1) {
+      if constexpr (NP == 1 && TILE == BS) {
         if (lane == 0) bulk_g2s(sA[s], a, PANEL_BYTES, &bar[s]);
       } else {
         for (int row = lane; row < TILE; row += 32)
@@ -103,22 +102,7 @@ __global__ void __launch_bounds__(kGemmThreads)
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TM; ++j) acc[i][j] = 0.0;
-    double* C = pl.cpool + g * LEAF;
-    double s2 = 0.0;
-    // write output quadrant qd from the accumulators (and add its squares to
-    // this thread's share of the leaf's squared norm, kernel (d))
-    auto store_quad = [&](int qd) {
-      double* Cq = C + (int64_t)(qd / (BS / TILE)) * TILE * BS + (qd % (BS / TILE)) * TILE;
-#pragma unroll
-      for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TM; ++j) {
-          Cq[(tr + 16 * i) * BS + tc + 16 * j] = acc[i][j];
-          s2 = __fma_rn(acc[i][j], acc[i][j], s2);
-          acc[i][j] = 0.0;
-        }
-    };
-    const int64_t nsteps = per_quad * NQ;
+    const int64_t nsteps = (q1 - q0) * NP;
     if (warp == 0 && nsteps > 0) issue(0, 0);
     inflight |= 1u;
     for (int64_t t = 0; t < nsteps; ++t) {
@@ -151,19 +135,19 @@ __global__ void __launch_bounds__(kGemmThreads)
           for (int j = 0; j < TM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
       }
       __syncthreads();
-      if constexpr (NQ > 1) {
-        if ((t + 1) % per_quad == 0 && t + 1 < nsteps) store_quad((int)(t / per_quad));
-      }
     }
     if (nsteps <= 0) inflight &= ~1u;
     if (s_abort) break;
-    // epilogue: the last quadrant (every quadrant, as zeros, for an empty
-    // task list), then the leaf's squared Frobenius norm
-    if (nsteps > 0) {
-      store_quad(NQ - 1);
-    } else {
-      for (int qd = 0; qd < NQ; ++qd) store_quad(qd);
-    }
+    // epilogue: write the output tile and its squared Frobenius norm (kernel (d))
+    double* C = pl.cpool + g * LEAF + r0 * BS + c0;
+    double s2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TM; ++j) {
+        C[(tr + 16 * i) * BS + tc + 16 * j] = acc[i][j];
+        s2 = __fma_rn(acc[i][j], acc[i][j], s2);
+      }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
     if (lane == 0) s_red[warp] = s2;
@@ -171,7 +155,10 @@ __global__ void __launch_bounds__(kGemmThreads)
     if (tid == 0) {
       double t = 0.0;
       for (int w = 0; w < kGemmThreads / 32; ++w) t += s_red[w];
-      pl.csq[g] = t;
+      if constexpr (NQ == 1)
+        pl.csq[g] = t;
+      else
+        pl.csq_part[g * NQ + sub] = t;
     }
   }
   // leave no bulk copy in flight into this CTA's shared memory
@@ -182,10 +169,26 @@ __global__ void __launch_bounds__(kGemmThreads)
   __syncthreads();
 }
 
+// Squared norm of each output leaf from its sub-tiles' partials, added in
+// sub-tile order; one thread per leaf over every plan of the batch.
+__global__ void leaf_norm_from_parts_kernel(BatchDev batch, int nq) {
+  const int64_t nleaves = batch.nunits / nq;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nleaves;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = x * nq;
+    const int r = plan_of(batch.ubegin, batch.nplans, u);
+    const PlanDev& pl = batch.plans[r];
+    const int64_t g = (u - batch.ubegin[r]) / nq;
+    double t = 0.0;
+    for (int k = 0; k < nq; ++k) t += pl.csq_part[g * nq + k];
+    pl.csq[g] = t;
+  }
+}
+
 template <int BS>
 static void launch_fp64(spamm_ctx ctx, const BatchDev& b) {
-  constexpr int KP = BS <= 64 ? BS : 32;
-  constexpr int TILE = BS <= 128 ? BS : 128;
+  constexpr int KP = BS <= 32 ? BS : 32;
+  constexpr int TILE = BS <= 64 ? BS : 64;
   auto kern = gemm_fp64_kernel<BS, KP, TILE>;
   const size_t smem = 4 * (size_t)TILE * KP * sizeof(double);
   CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -199,7 +202,16 @@ static void launch_fp64(spamm_ctx ctx, const BatchDev& b) {
   CK(cudaMemsetAsync(work, 0, sizeof(unsigned long long), ctx->stream));
   kern<<<(unsigned)grid, kGemmThreads, smem, ctx->stream>>>(b, work, ctx->d_err);
   CK_LAUNCH("gemm_fp64_kernel");
+  constexpr int NQ = (BS / TILE) * (BS / TILE);
+  if constexpr (NQ > 1) {
+    int64_t g2 = (b.nunits / NQ + 255) / 256;
+    if (g2 > 4 * (int64_t)ctx->num_sms) g2 = 4 * (int64_t)ctx->num_sms;
+    leaf_norm_from_parts_kernel<<<(unsigned)g2, 256, 0, ctx->stream>>>(b, NQ);
+    CK_LAUNCH("leaf_norm_from_parts_kernel");
+  }
 }
+
+int fp64_units_per_leaf(int bs) { return bs <= 64 ? 1 : (bs / 64) * (bs / 64); }
 
 __global__ void unit_order_keys_kernel(const int64_t* __restrict__ gstart, int64_t ng, uint64_t* __restrict__ keys,
                                        int64_t* __restrict__ vals) {

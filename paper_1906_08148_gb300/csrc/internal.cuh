@@ -210,7 +210,8 @@ struct PlanDev {
   const QuadStep* qsteps;
   double* cpool;
   double* csq;
-  const int64_t* uorder;  // FP64 form: output leaf of each work unit (longest first), or null for identity
+  const int64_t* uorder;  // FP64 form: output leaf at each claiming position (longest first), or null for identity
+  double* csq_part;       // FP64 form, leaves split into sub-tile units: partial squared norms [leaf][sub-tile]
 };
 struct BatchDev {
   const PlanDev* plans;
@@ -231,6 +232,8 @@ __device__ __forceinline__ int plan_of(const int64_t* __restrict__ ubegin, int n
   return lo;
 }
 void gemm_fp64_batch(spamm_ctx ctx, int bs, const BatchDev& b);
+// Work units per output leaf of the FP64 kernel (sub-tiles of 64 x 64 for larger leaves).
+int fp64_units_per_leaf(int bs);
 // Output leaves ordered by their number of kept products, largest first
 // (stable), for the FP64 kernel's unit claiming; an empty buffer when the
 // leaves are small enough that the claiming tail does not matter.
