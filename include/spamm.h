@@ -69,7 +69,7 @@ typedef enum {
   SPAMM_E_TIMEOUT = 6,     /* a bounded device-side wait ran out */
   SPAMM_E_BUSY = 7,        /* resource in use */
   SPAMM_E_CAPACITY = 8,    /* caller buffer too small; required size returned where the call says so */
-  SPAMM_E_UNSUPPORTED = 9  /* valid request this build does not implement (named in the message) */
+  SPAMM_E_UNSUPPORTED = 9  /* valid request the library does not implement (named in the message) */
 } spamm_status;
 
 /* The three methods of Section 5: Truncmul, SpAMM, Hybrid. */
