@@ -157,9 +157,9 @@ def test_structural_examples_of_section_4_4():
 
 
 # ---------------------------------------------------------------- the product
-@pytest.mark.parametrize("bs", [1, 4, 16, 32])
+@pytest.mark.parametrize("bs", [1, 4, 16, 32, 256])
 def test_tau_zero_is_the_dense_product(bs):
-    n = 130 if bs > 1 else 48
+    n = 300 if bs == 256 else (130 if bs > 1 else 48)  # 300: two ragged 256-leaves per side
     A, B = _pair(n, alpha=0.05)
     C, _ = oracle.multiply(oracle.from_dense(A, bs), oracle.from_dense(B, bs), 0.0, oracle.SPAMM)
     ref = A @ B
