@@ -543,7 +543,12 @@ spamm_status spamm_plan_info(spamm_plan p, int64_t* n_kept, int64_t* n_c_leaves,
   if (n_kept) *n_kept = p->T.ntasks;
   if (n_c_leaves) *n_c_leaves = p->T.ngroups;
   if (plan_bytes) *plan_bytes = (int64_t)held_bytes(*p);
-  if (exec_bytes) *exec_bytes = p->T.ngroups * ((int64_t)p->bs * p->bs * 8 + 8 + 8) + 4096;
+  if (exec_bytes) {
+    // output payload, slot and squared norm per leaf, the FP64 sub-tile partial
+    // norms, the parents' norms (at most a third of the leaves), the batch tables
+    const int64_t parts = p->prec == SPAMM_PREC_FP64 && fp64_units_per_leaf(p->bs) > 1 ? fp64_units_per_leaf(p->bs) : 0;
+    *exec_bytes = p->T.ngroups * ((int64_t)p->bs * p->bs * 8 + 8 + 8 + 8 * parts) + (p->T.ngroups / 3 + 1) * 8 + 4096;
+  }
   return SPAMM_OK;
 }
 
