@@ -9,8 +9,6 @@ the result equals the corresponding leaves of the full oracle product.
 """
 from __future__ import annotations
 
-import numpy as np
-
 import oracle
 import synth
 

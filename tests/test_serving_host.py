@@ -3,8 +3,6 @@ import random
 import threading
 import time
 
-import pytest
-
 from paper_1906_08148_gb300.serving import Request, Server
 
 
