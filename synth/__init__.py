@@ -80,6 +80,8 @@ def _load():
         lib.synth_lattice_point_host.argtypes = [ctypes.c_int64, ip]
         lib.synth_leaf_bound_host.argtypes = [P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64]
         lib.synth_leaf_bound_host.restype = ctypes.c_double
+        lib.synth_leaf_bounds_row.argtypes = [P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                                              ctypes.POINTER(ctypes.c_int64), dp]
         lib.synth_block_sparse.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64,
                                            ip, ip, dp]
         lib.synth_block_sparse.restype = ctypes.c_int64
@@ -127,6 +129,16 @@ def leaf_bound(p: DecayParams, bs: int, bi: int, bj: int) -> float:
     """Upper bound of |a_ij| over leaf (bi, bj)."""
     cp = p.as_c()
     return _load().synth_leaf_bound_host(ctypes.byref(cp), bs, bi, bj)
+
+
+def leaf_bounds_row(p: DecayParams, bs: int, bi: int, bj) -> np.ndarray:
+    """leaf_bound(p, bs, bi, bj[q]) for every q, in one call."""
+    bj = np.ascontiguousarray(bj, dtype=np.int64)
+    out = np.empty(len(bj), dtype=np.float64)
+    cp = p.as_c()
+    _load().synth_leaf_bounds_row(ctypes.byref(cp), bs, int(bi), len(bj), _ptr(bj, ctypes.c_int64),
+                                  _ptr(out, ctypes.c_double))
+    return out
 
 
 def lattice_point(i: int):

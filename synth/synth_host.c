@@ -30,6 +30,12 @@ double synth_leaf_bound_host(const synth_params* p, int32_t bs, int64_t bi, int6
   return synth_leaf_bound(p, bs, bi, bj);
 }
 
+/* The leaf bounds of leaves (bi, bj[q]), q < m: one block row at a time. */
+void synth_leaf_bounds_row(const synth_params* p, int32_t bs, int64_t bi, int64_t m, const int64_t* bj, double* out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t q = 0; q < m; ++q) out[q] = synth_leaf_bound(p, bs, bi, bj[q]);
+}
+
 /* Random block-sparse n x n matrix (the leaf-library benchmark of Section
  * 5.2): on the nb x nb grid of bs x bs blocks (nb = ceil(n / bs)), block
  * (I, J) is non-zero with probability `fill`, independently of the others
