@@ -55,15 +55,20 @@ def _band(bound: np.ndarray, decades: int, nbands: int) -> np.ndarray:
     return np.minimum((np.maximum(lg, 0.0) // decades).astype(np.int64), nbands - 1)
 
 
-def leaf_error_sq(pa, pb, bs: int, i: int, j: int, tau: float, mode: int, rule="block") -> float:
-    """||(AB)_ij - C_ij||_F^2 for one output leaf: the exact leaf over every
-    non-null k of the untruncated inputs against the method's leaf (its
-    truncation and kept set restricted to block row i of A and block column j
-    of B, which is all the leaf depends on)."""
+def leaf_sq(pa, pb, bs: int, i: int, j: int, tau: float, mode: int, rule="block"):
+    """(||(AB)_ij - C_ij||_F^2, ||(AB)_ij||_F^2) for one output leaf: the exact
+    leaf over every non-null k of the untruncated inputs against the method's
+    leaf (its truncation and kept set restricted to block row i of A and block
+    column j of B, which is all the leaf depends on)."""
     A_row, B_col = window_inputs(pa, pb, bs, [i], [j])
     X = window_exact(A_row, B_col)
     C, _ = window_product(A_row, B_col, tau, mode, rule)
-    return oracle.error(X, C) ** 2
+    return oracle.error(X, C) ** 2, oracle.frob_norm(X) ** 2
+
+
+def leaf_error_sq(pa, pb, bs: int, i: int, j: int, tau: float, mode: int, rule="block") -> float:
+    """||(AB)_ij - C_ij||_F^2 for one output leaf (see `leaf_sq`)."""
+    return leaf_sq(pa, pb, bs, i, j, tau, mode, rule)[0]
 
 
 def _positions(pa, bs: int, nb: int, decades: int, nbands: int, ranks: dict) -> dict:
@@ -101,7 +106,10 @@ def error_estimate(pa, pb, bs: int, tau: float, mode: int, samples: int = 256, s
     and the interval for ||E||_F is sqrt(max(0, T -/+ z sqrt(V))) (a normal
     approximation: for skewed strata and few samples it covers less often
     than its nominal rate; on the 1-D model problem n = 2048 it covered the
-    true error in 14, 17 and 19 of 20 seeds with 64, 128 and 256 samples).  Returns the estimate, the interval and the strata."""
+    true error in 14, 17 and 19 of 20 seeds with 64, 128 and 256 samples).
+    The same samples give the stratified estimate of ||AB||_F^2 (sum of the
+    exact leaves' squared norms), hence the relative error.  Returns the
+    estimate, the interval, ||AB||_F and the strata."""
     nb = -(-pa.n // bs)
     cols = np.arange(nb, dtype=np.int64)
     counts = np.zeros(nbands, np.int64)
@@ -113,9 +121,16 @@ def error_estimate(pa, pb, bs: int, tau: float, mode: int, samples: int = 256, s
     pilot = max(2, samples // (2 * max(1, len(live))))
     n0 = {h: min(int(counts[h]), pilot) for h in live}
 
+    xsq = {h: [] for h in live}
+
     def evaluate(ranks):
         pos = _positions(pa, bs, nb, decades, nbands, ranks)
-        return {h: [leaf_error_sq(pa, pb, bs, i, j, tau, mode, rule) for i, j in pos[h]] for h in ranks}
+        out = {}
+        for h in ranks:
+            pairs = [leaf_sq(pa, pb, bs, i, j, tau, mode, rule) for i, j in pos[h]]
+            out[h] = [e for e, _ in pairs]
+            xsq[h].extend(x for _, x in pairs)
+        return out
 
     y = evaluate({h: perm[h][:n0[h]] for h in live})
     rest = samples - sum(n0.values())
@@ -136,19 +151,21 @@ def error_estimate(pa, pb, bs: int, tau: float, mode: int, samples: int = 256, s
         for h, v in more.items():
             y[h] = y[h] + v
     strata = []
-    total, var = 0.0, 0.0
+    total, var, xtotal = 0.0, 0.0, 0.0
     for h in live:
         v = np.asarray(y[h])
         N, m = int(counts[h]), len(v)
         mean = float(np.mean(v))
         s2 = float(np.var(v, ddof=1)) if m > 1 else 0.0
         total += N * mean
+        xtotal += N * float(np.mean(xsq[h]))
         var += N * N * (1.0 - m / N) * s2 / m
         strata.append({"band": h, "positions": N, "sampled": m, "mean_err_sq": mean, "var_err_sq": s2})
     half = z * np.sqrt(var)
     return {"estimate": float(np.sqrt(total)), "low": float(np.sqrt(max(0.0, total - half))),
             "high": float(np.sqrt(total + half)), "err_sq": total, "err_sq_sd": float(np.sqrt(var)),
-            "samples": int(sum(s["sampled"] for s in strata)), "strata": strata}
+            "exact_norm": float(np.sqrt(xtotal)), "samples": int(sum(s["sampled"] for s in strata)),
+            "strata": strata}
 
 
 def _main(argv=None):

@@ -51,6 +51,7 @@ def test_census_reproduces_the_full_error():
     assert r["samples"] == 16 * 16
     assert r["estimate"] == pytest.approx(truth, rel=1e-12)
     assert r["low"] == r["high"] == r["estimate"]
+    assert r["exact_norm"] == pytest.approx(np.linalg.norm(synth.dense(pa) @ synth.dense(pb)), rel=1e-12)
 
 
 def test_interval_covers_the_error_at_about_the_nominal_rate():
