@@ -5,7 +5,6 @@ import ctypes
 import math
 import os
 import subprocess
-import tempfile
 
 import numpy as np
 import pytest
@@ -15,8 +14,8 @@ CSRC = os.path.join(ROOT, "paper_1906_08148_gb300", "csrc")
 
 
 @pytest.fixture(scope="module")
-def fb():
-    d = tempfile.mkdtemp(prefix="fbits")
+def fb(tmp_path_factory):
+    d = str(tmp_path_factory.mktemp("fbits"))
     src = os.path.join(d, "shim.c")
     with open(src, "w") as f:
         f.write('#include "fbits.cuh"\n'
