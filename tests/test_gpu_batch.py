@@ -160,3 +160,32 @@ def test_trim_returns_cached_pool_memory(S, ctx):
     # live handles are untouched
     assert np.array_equal(S.spamm_to_dense(ctx, C), ref)
     assert S.spamm_frob_norm(ctx, C) > 0
+
+
+@pytest.mark.parametrize("bs", [128, 256])
+def test_graph_and_batch_with_subtile_units(S, ctx, bs):
+    """128 and 256 leaves run as 64 x 64 sub-tile units whose partial norms a
+    second launch adds: eager, graph and alone give the same leaves and norms."""
+    plans, keep = [], []
+    for n, alpha, tau, mode in [(4096, 0.9, 1e-6, "combined"), (2048, 0.7, 1e-4, "spamm"), (1000, 0.8, 1e-5, "truncate")]:
+        GA, GB = _inputs(S, ctx, n, alpha, bs)
+        keep.append((GA, GB, tau, mode))
+        plans.append(S.spamm_plan_create(ctx, GA, GB, tau, mode, "fp64"))
+    eager = S.spamm_execute(ctx, plans)
+    S.spamm_set_exec_graph(ctx, True)
+    try:
+        graph = S.spamm_execute(ctx, plans)
+    finally:
+        S.spamm_set_exec_graph(ctx, False)
+    for (GA, GB, tau, mode), E, G in zip(keep, eager, graph):
+        alone = S.spamm_multiply(ctx, GA, GB, tau, mode, "fp64")
+        for X in (G, alone):
+            for a, b in zip(S.spamm_to_blocks(ctx, E), S.spamm_to_blocks(ctx, X)):
+                assert np.array_equal(a, b)
+        for lev in range(E.info()["levels"] + 1):
+            ce, se = S.spamm_level_norms(ctx, E, lev)
+            cg, sg = S.spamm_level_norms(ctx, G, lev)
+            assert np.array_equal(ce, cg) and np.array_equal(se, sg)
+        # the leaf norms are the norms of the leaves
+        bi, bj, pay, sq = S.spamm_to_blocks(ctx, E)
+        assert np.allclose(sq, np.sum(pay ** 2, axis=(1, 2)), rtol=1e-13, atol=0)
