@@ -364,7 +364,7 @@ SPAMM_API spamm_status spamm_gather_leaves(spamm_ctx ctx, spamm_mat m, int64_t n
  * bit, the leaf norms the library stores for the same payload.
  *
  * It calls no cudaMalloc, cudaFree or allocating library routine.  Its scratch
- * (one FP64 partial sum per 4096 leaves, 32 KB) is a fixed device array in this
+ * (one FP64 partial sum per 64 leaves, 2 MB) is a fixed device array in this
  * library, which every GPU that loads the library holds until the process
  * exits.  The first call on a device looks up that array's device address with
  * the device current (a one-time set-up); make that first call before any

@@ -7,10 +7,10 @@
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int64_t kLeavesPerPartial = 4096;
+constexpr int64_t kLeavesPerPartial = 64;  // a block's share: grids of ~nleaves / 64 blocks fill the SMs evenly
 constexpr int64_t kMaxPartials = SPAMM_NOALLOC_MAX_LEAVES / kLeavesPerPartial;
 
-// One FP64 partial sum per 4096 leaves, shared by every call on a device.
+// One FP64 partial sum per 64 leaves, shared by every call on a device.
 static __device__ __align__(256) double g_noalloc_partials[kMaxPartials];
 
 // Device address of g_noalloc_partials per device ordinal, looked up once.
@@ -26,7 +26,7 @@ __global__ void noalloc_sqnorm_kernel(const double* __restrict__ payload, int64_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t e = (int64_t)bs * bs;
   const int pairs = (int)(e / 2);
-  // block b owns leaves [b * 4096, (b + 1) * 4096); each warp takes every 8th of them
+  // block b owns leaves [b * 64, (b + 1) * 64); each warp takes every 8th of them
   const int64_t first = (int64_t)blockIdx.x * kLeavesPerPartial;
   double block_part = 0.0;
   for (int64_t i = warp; i < kLeavesPerPartial; i += kThreads / 32) {
@@ -53,12 +53,15 @@ __global__ void noalloc_sqnorm_kernel(const double* __restrict__ payload, int64_
   }
 }
 
-// One block adds the partials in index order.
+// One warp adds the partials: lane l those at l, l + 32, ... in index order,
+// then a butterfly (a fixed order, so the total is reproducible).
 __global__ void noalloc_total_kernel(const double* __restrict__ partials, int64_t nparts, double* __restrict__ out) {
-  if (threadIdx.x != 0) return;
+  const int lane = threadIdx.x & 31;
   double t = 0.0;
-  for (int64_t i = 0; i < nparts; ++i) t += partials[i];
-  *out = t;
+  for (int64_t i = lane; i < nparts; i += 32) t += partials[i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  if (lane == 0) *out = t;
 }
 
 // Set-up, once per device, with that device current: the kernel needs the
