@@ -1,0 +1,97 @@
+"""Host logic of bench.py (no GPU): the roofline entry, the traffic lookup
+keyed by kernel source hash, the clock-record summary and the choice of tau
+at equal accuracy."""
+import json
+import os
+
+import pytest
+
+import bench
+
+
+def test_fp64_roofline_is_kept_flops_over_event_time():
+    kept, ms = 1000, 1.0
+    r = bench.roofline("fp64", 64, kept, ms, 0.0)
+    assert r["bound"] == "alu" and r["unit"] == "GFLOP/s"
+    assert r["achieved"] == pytest.approx(2 * 64 ** 3 * kept / 1e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_PEAK_GFLOPS)
+    entry = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))["gemm_fp64_kernel<64>"]
+    assert r["traffic"] == pytest.approx(entry["dram_bytes_per_product"] * kept)  # capture of the current source
+
+
+def test_tensor_roofline_reports_kept_and_executed_rates():
+    r = bench.roofline("fp16_scaled", 64, 2000, 2.0, 3.0e12)
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(2 * 64 ** 3 * 2000 / 2e-3 / 1e12)
+    assert r["executed"] == pytest.approx(3.0e12 / 2e-3 / 1e12)
+    assert r["executed_frac"] == pytest.approx(r["executed"] / r["peak"])
+
+
+def test_traffic_is_null_once_the_kernel_source_changed(tmp_path, monkeypatch):
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "k.cu").write_text("kernel v1\n")
+    import hashlib
+    h = hashlib.sha256(b"kernel v1\n").hexdigest()[:16]
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(
+        {"k": {"source": "k.cu", "source_sha256_16": h, "dram_bytes_per_product": 100.0}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_traffic("k", 10) == 1000.0
+    assert bench.load_traffic("other", 10) is None
+    (tmp_path / "k.cu").write_text("kernel v2\n")
+    assert bench.load_traffic("k", 10) is None
+
+
+def test_clock_summary_median_under_load_and_reasons(tmp_path):
+    c = bench.ClockSampler(0)
+    c.path = str(tmp_path / "clocks.csv")
+    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 2070, 2070, 1300.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 345, 2070, 150.0, 0x1, Not Active, Not Active, Not Active, Not Active",  # idle sample
+            "0, 1995, 2070, 1350.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "garbage line"]
+    open(c.path, "w").write("\n".join(rows) + "\n")
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 4
+    assert not os.path.exists(c.path)
+
+
+class _FakeMat:
+    def close(self):
+        pass
+
+
+class _FakeS:
+    """tau_sweep's calls with a made-up error and product count per (mode, tau)."""
+    ERR = {"truncate": {1e-4: 3e-2, 1e-6: 3e-4, 1e-8: 3e-6},
+           "spamm": {1e-4: 1e-2, 1e-6: 1e-4, 1e-8: 1e-6},
+           "combined": {1e-4: 2e-2, 1e-6: 2e-4, 1e-8: 2e-6}}
+    KEPT = {"truncate": 10, "spamm": 4, "combined": 5}
+
+    def __init__(self):
+        self.last = None
+
+    def spamm_multiply(self, ctx, A, B, tau, mode, prec="fp64", stats=False):
+        self.last = (mode, tau)
+        m = _FakeMat()
+        if not stats:
+            return m
+        k = self.KEPT[mode] * (1 if tau > 0 else 10)
+        return m, {"n_kept": k, "ms_gemm": 1.0, "kept_flops": 2.0 * 64 ** 3 * k}
+
+    def spamm_error(self, ctx, X, C):
+        mode, tau = self.last
+        return self.ERR[mode][tau]
+
+    def spamm_frob_norm(self, ctx, X):
+        return 1.0
+
+
+def test_tau_sweep_takes_the_largest_tau_within_each_sigma():
+    out = bench.tau_sweep(_FakeS(), None, None, None, [1e-4, 1e-6, 1e-8], [1e-2, 1e-4, 1e-6])
+    ch = out["chosen"]
+    assert ch["0.01"]["spamm"]["tau"] == 1e-4 and ch["0.01"]["truncate"]["tau"] == 1e-6
+    assert ch["0.0001"]["spamm"]["tau"] == 1e-6 and ch["0.0001"]["combined"]["tau"] == 1e-8
+    assert ch["1e-06"]["truncate"] is None and ch["1e-06"]["spamm"]["tau"] == 1e-8
+    assert ch["0.01"]["spamm"]["gemm_vs_truncmul"] == pytest.approx(4 / 10)
+    assert out["exact"]["n_kept"] == 40
