@@ -92,6 +92,8 @@ def parse_args():
     ap.add_argument("--sp2-tau", type=float, default=1e-6)
     ap.add_argument("--sp2-iters", type=int, default=40)
     ap.add_argument("--sp2-tol", type=float, default=1e-6)
+    ap.add_argument("--passes", action="store_true",
+                    help="bandwidth of the norm pass and the task-list pass on the bench workload")
     ap.add_argument("--mp-n", type=int, default=40000)
     ap.add_argument("--mp-bs", type=int, nargs="+", default=[64])
     ap.add_argument("--mp-sigma", type=float, default=1e-6)
@@ -526,6 +528,70 @@ def run_sp2(args):
 
 
 # ---------------------------------------------------------- multi-rank timing
+def run_passes(args, cfg):
+    """The two passes around the leaf GEMM, timed with CUDA events on the
+    bench workload.  Kernel (a), the leaf norms, in its allocation-free form
+    (the same per-leaf arithmetic) over as many random 64 x 64 leaves as the
+    workload's truncated input has (far above L2; L2 written over before each
+    run): bytes read and written / time.  Kernel (b), the task list, inside
+    the multiply (FP16 form, whose leaf products are short): its algorithmic
+    traffic per level, per kept parent pair its two node indices (8 B), both
+    nodes' child-norm records (2 x 32 B) and child links (2 x 16 B), and 8 B
+    per kept child written, over the task-list time the library reports."""
+    import torch
+
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_1906_08148_gb300 import spamm as S
+
+    stream = torch.cuda.current_stream()
+    ctx = S.Context(0, stream=stream)
+    bs = cfg["bs"]
+    GA = S.spamm_generate(ctx, synth.DecayParams(n=cfg["n"], kind=cfg["kind"], alpha=cfg["alpha"],
+                                                 seed=cfg["seeds"][0]), bs)
+    GB = S.spamm_generate(ctx, synth.DecayParams(n=cfg["n"], kind=cfg["kind"], alpha=cfg["alpha"],
+                                                 seed=cfg["seeds"][1]), bs)
+    tasks = []
+    for _ in range(max(2, args.steps)):
+        C, st = S.spamm_multiply(ctx, GA, GB, args.tau, args.mode, "fp16_scaled" if bs == 64 else "fp64", stats=True)
+        C.close()
+        tasks.append(st)
+    st = tasks[-1]
+    kept = [1] + list(st["n_kept_level"])  # the root pair, then every level's kept pairs
+    task_bytes = 104.0 * sum(kept[:-1]) + 8.0 * sum(kept[1:])
+    ms_tasks = statistics.median(s["ms_tasks"] for s in tasks[1:])
+    nl = st["n_a_leaves"]
+    pay = torch.rand(nl * bs * bs, dtype=torch.float64, device="cuda")
+    sq = torch.empty(nl, dtype=torch.float64, device="cuda")
+    tot = torch.empty(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ms = []
+    for _ in range(max(4, args.steps)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if S.spamm_leaf_sqnorms_noalloc(pay, nl, bs, sq, tot, stream) != 0:
+            raise RuntimeError("spamm_leaf_sqnorms_noalloc failed")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    norm_ms = statistics.median(ms[1:])
+    norm_bytes = nl * (bs * bs * 8 + 8)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    print(json.dumps({
+        "metric": "pass bandwidth", "unit": "GB/s", "data": "synthetic",
+        "config": {"workload": args.config, "method": args.mode, "tau": args.tau},
+        "hbm_peak_gbs": hbm, "hbm_peak_source": "MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback",
+        "norm_pass": {"kernel": "noalloc_sqnorm_kernel", "leaves": nl, "bytes": norm_bytes, "ms": norm_ms,
+                      "gbs": norm_bytes / norm_ms / 1e6, "frac": norm_bytes / norm_ms / 1e6 / hbm},
+        "task_pass": {"levels": st["levels"], "candidates": st["n_candidates"], "kept": st["n_kept_level"],
+                      "bytes": task_bytes, "ms": ms_tasks, "gbs": task_bytes / ms_tasks / 1e6,
+                      "frac": task_bytes / ms_tasks / 1e6 / hbm}}), flush=True)
+
+
 def aggregate_ranks(ms_local, flops_local, kept_local, dist=None):
     """Whole-job numbers over independent replicas (one per GPU): the timed
     region is the slowest rank's, the work is every rank's.
@@ -561,6 +627,8 @@ def main():
         return run_chain(args)
     if args.sp2:
         return run_sp2(args)
+    if args.passes:
+        return run_passes(args, cfg)
 
     import numpy as np
     import torch
