@@ -64,6 +64,6 @@ def test_interval_covers_the_error_at_about_the_nominal_rate():
         assert r["samples"] == 128
         est.append(r["err_sq"])
         cover += r["low"] <= truth <= r["high"]
-    assert cover >= 9, cover  # nominal 95 %; measured 17 of 20 seeds at this size
+    assert cover >= 9, cover  # nominal 95 %; measured 16 of 20 seeds at this size
     # the squared-error estimator is unbiased: its mean over seeds is near the truth
     assert np.mean(est) == pytest.approx(truth ** 2, rel=0.12)
