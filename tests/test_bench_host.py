@@ -95,3 +95,20 @@ def test_tau_sweep_takes_the_largest_tau_within_each_sigma():
     assert ch["1e-06"]["truncate"] is None and ch["1e-06"]["spamm"]["tau"] == 1e-8
     assert ch["0.01"]["spamm"]["gemm_vs_truncmul"] == pytest.approx(4 / 10)
     assert out["exact"]["n_kept"] == 40
+
+
+@pytest.mark.parametrize("argv", [[], ["--steps", "5", "--warmup", "3"], ["--gpus", "2"], ["--impl", "reference"],
+                                  ["--sweep"], ["--model-problem", "--mp-bs", "32", "256"], ["--block-sparse"],
+                                  ["--passes"], ["--chain"], ["--sp2"], ["--serve", "--prec", "auto"],
+                                  ["--prec", "fp16_scaled", "--config", "lattice16384"]])
+def test_every_mode_parses(monkeypatch, argv):
+    monkeypatch.setattr("sys.argv", ["bench.py"] + argv)
+    a = bench.parse_args()
+    assert a.steps >= 1
+
+
+def test_defaults_are_one_gpu_the_bench_workload_and_three_warmups(monkeypatch):
+    monkeypatch.setattr("sys.argv", ["bench.py"])
+    a = bench.parse_args()
+    assert a.gpus == 1 and a.warmup >= 3 and a.config == "lattice65536" and a.prec == "fp64"
+    assert a.impl != "reference"
