@@ -86,3 +86,39 @@ def test_pins_reject_each_mutant(tmp_path, name):
         assert failed == []
     else:
         assert failed, f"mutant {name} passed every pin"
+
+
+# Python-level mutants of the skipped-product bound: a copy of
+# oracle.skipped_bound with one planted error, swapped in for the pin battery
+# of tests/test_oracle_bound.py.
+BOUND_MUTANTS = {
+    "bound_sums_every_candidate": ("term = np.where(is_kept, 0.0, na * nb)", "term = na * nb"),
+    "bound_inverted_is_kept": ("is_kept = np.isin(ck, kk)", "is_kept = ~np.isin(ck, kk)"),
+    "bound_squared_norms": ("na = np.sqrt(A.sq[", "na = (A.sq["),
+    "bound_sum_not_squares": ("return float(np.sqrt(np.sum(beta * beta)))", "return float(np.sum(beta))"),
+}
+
+
+def _bound_mutant(mutation):
+    import inspect
+    import textwrap
+
+    src = textwrap.dedent(inspect.getsource(oracle.skipped_bound))
+    old, new = mutation
+    assert src.count(old) == 1, old
+    ns = dict(vars(oracle))
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), ns)
+    return ns["skipped_bound"]
+
+
+@pytest.mark.parametrize("name", ["unmodified"] + sorted(BOUND_MUTANTS))
+def test_bound_pins_reject_each_mutant(monkeypatch, name):
+    from test_oracle_bound import bound_battery
+
+    if name != "unmodified":
+        monkeypatch.setattr(oracle, "skipped_bound", _bound_mutant(BOUND_MUTANTS[name]))
+    failed = bound_battery()
+    if name == "unmodified":
+        assert failed == []
+    else:
+        assert failed, f"mutant {name} passed every pin of the bound"
