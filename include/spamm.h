@@ -372,8 +372,10 @@ SPAMM_API spamm_status spamm_gather_leaves(spamm_ctx ctx, spamm_mat m, int64_t n
  * overlaps on the GPU race: order them on one stream or synchronise between
  * them.  Each call writes every scratch entry it reads before reading it.
  * Errors: SPAMM_E_CAPACITY if nleaves > SPAMM_NOALLOC_MAX_LEAVES,
- * SPAMM_E_INVALID_ARG (bs not 32/64/128/256, nleaves < 0, NULL pointer),
- * SPAMM_E_CUDA (set-up or launch failed). */
+ * SPAMM_E_INVALID_ARG (bs not 32/64/128/256, nleaves < 0, NULL pointer,
+ * payload not 16-byte aligned, sq_out or total_out not 8-byte aligned; these
+ * are checked on the host before anything is enqueued), SPAMM_E_CUDA (set-up
+ * or launch failed). */
 SPAMM_API spamm_status spamm_leaf_sqnorms_noalloc(const double* payload, int64_t nleaves, int bs, double* sq_out,
                                                   double* total_out, void* cuda_stream);
 

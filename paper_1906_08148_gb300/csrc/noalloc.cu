@@ -88,6 +88,11 @@ extern "C" spamm_status spamm_leaf_sqnorms_noalloc(const double* payload, int64_
   if (bs != 32 && bs != 64 && bs != 128 && bs != 256) return SPAMM_E_INVALID_ARG;
   if (nleaves < 0 || !total_out || (nleaves > 0 && (!payload || !sq_out))) return SPAMM_E_INVALID_ARG;
   if (nleaves > SPAMM_NOALLOC_MAX_LEAVES) return SPAMM_E_CAPACITY;
+  // the kernel reads the payload in 16-byte pairs and writes 8-byte results:
+  // a misaligned pointer is refused here, before anything reaches the GPU
+  if (nleaves > 0 && (reinterpret_cast<uintptr_t>(payload) % 16 != 0 || reinterpret_cast<uintptr_t>(sq_out) % 8 != 0))
+    return SPAMM_E_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(total_out) % 8 != 0) return SPAMM_E_INVALID_ARG;
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) {
     cudaGetLastError();

@@ -386,13 +386,29 @@ def spamm_gather_leaves(ctx: Context, m: Matrix, bi, bj):
 
 def spamm_leaf_sqnorms_noalloc(payload, nleaves: int, bs: int, sq_out, total_out, stream=None) -> int:
     """Allocation-free leaf norms: raw device pointers (ints) or CUDA tensors in,
-    the C status code out (OK = 0).  See include/spamm.h."""
-    def addr(x):
+    the C status code out (OK = 0).  See include/spamm.h.
+
+    Tensors must be contiguous CUDA float64 tensors holding at least
+    nleaves * bs * bs (payload), nleaves (sq_out) and 1 (total_out) elements;
+    anything else raises ValueError before the library is called.  Raw
+    pointers are passed through unchecked (the library refuses misaligned ones)."""
+    need = {"payload": int(nleaves) * int(bs) * int(bs), "sq_out": int(nleaves), "total_out": 1}
+
+    def addr(name, x):
         if x is None:
             return None
-        return ctypes.c_void_p(x.data_ptr() if _is_torch(x) else int(x))
+        if _is_torch(x):
+            if not x.is_cuda or str(x.dtype) != "torch.float64":
+                raise ValueError(f"{name} must be a CUDA float64 tensor")
+            if not x.is_contiguous():
+                raise ValueError(f"{name} must be contiguous")
+            if x.numel() < need[name]:
+                raise ValueError(f"{name} holds {x.numel()} elements, fewer than {need[name]}")
+            return ctypes.c_void_p(x.data_ptr())
+        return ctypes.c_void_p(int(x))
     s = stream.cuda_stream if (stream is not None and hasattr(stream, "cuda_stream")) else stream
-    return load().spamm_leaf_sqnorms_noalloc(addr(payload), int(nleaves), int(bs), addr(sq_out), addr(total_out),
+    return load().spamm_leaf_sqnorms_noalloc(addr("payload", payload), int(nleaves), int(bs),
+                                              addr("sq_out", sq_out), addr("total_out", total_out),
                                               ctypes.c_void_p(s or 0))
 
 

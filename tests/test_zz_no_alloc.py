@@ -44,7 +44,9 @@ def test_noalloc_matches_the_allocating_entry_points(S, bs, p):
         assert st == S.OK, st
         torch.cuda.synchronize()
         got = sq.cpu().numpy()
-        assert np.all(np.abs(got - sq_ref) <= REL_NORM * sq_ref), call
+        # the same per-leaf arithmetic and order as the library's norm pass: identical bits
+        assert np.array_equal(got, sq_ref), call
+        # the total adds the partial sums in another order than the quadtree's parents
         assert abs(float(total.item()) - total_ref) <= REL_NORM * total_ref, call
 
 
@@ -65,3 +67,28 @@ def test_noalloc_second_call_with_fewer_leaves_and_limits(S):
             assert np.allclose(sq.cpu().numpy()[:nl], ref[:nl], rtol=1e-13)
     assert S.spamm_leaf_sqnorms_noalloc(payload, S.NOALLOC_MAX_LEAVES + 1, 32, sq, total, None) == S.E_CAPACITY
     assert S.spamm_leaf_sqnorms_noalloc(payload, 10, 48, sq, total, None) == S.E_INVALID_ARG
+
+
+def test_noalloc_refuses_misaligned_or_wrong_buffers_on_the_host(S):
+    """Misaligned raw pointers get INVALID_ARG from the library's host-side
+    check (nothing is enqueued); wrong tensors are refused by the binding."""
+    import torch
+    pay = torch.zeros(4 * 32 * 32 + 2, dtype=torch.float64, device="cuda")
+    sq = torch.zeros(8, dtype=torch.float64, device="cuda")
+    total = torch.zeros(2, dtype=torch.float64, device="cuda")
+    base = pay.data_ptr()
+    assert base % 16 == 0
+    assert S.spamm_leaf_sqnorms_noalloc(base + 8, 4, 32, sq.data_ptr(), total.data_ptr(), None) == S.E_INVALID_ARG
+    assert S.spamm_leaf_sqnorms_noalloc(base, 4, 32, sq.data_ptr() + 4, total.data_ptr(), None) == S.E_INVALID_ARG
+    assert S.spamm_leaf_sqnorms_noalloc(base, 4, 32, sq.data_ptr(), total.data_ptr() + 4, None) == S.E_INVALID_ARG
+    torch.cuda.synchronize()
+    assert float(sq.abs().sum().item()) == 0.0  # nothing ran
+    with pytest.raises(ValueError):
+        S.spamm_leaf_sqnorms_noalloc(pay.float(), 4, 32, sq, total)
+    with pytest.raises(ValueError):
+        S.spamm_leaf_sqnorms_noalloc(pay.cpu(), 4, 32, sq, total)
+    with pytest.raises(ValueError):
+        S.spamm_leaf_sqnorms_noalloc(pay[:100], 4, 32, sq, total)
+    with pytest.raises(ValueError):
+        S.spamm_leaf_sqnorms_noalloc(pay[: 4 * 1024 * 2].view(-1, 2)[:, 0], 4, 32, sq, total)
+    assert S.spamm_leaf_sqnorms_noalloc(pay, 4, 32, sq, total) == S.OK
