@@ -55,7 +55,7 @@ def parse_args():
     ap.add_argument("--config", default="lattice65536", choices=sorted(CONFIGS))
     ap.add_argument("--mode", default="combined", choices=["truncate", "spamm", "combined"])
     ap.add_argument("--tau", type=float, default=1e-6)
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16_split", "fp16_scaled", "auto"],
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16_split", "bf16_split4", "fp16_scaled", "auto"],
                     help="auto: the autotuner's choice per request (served stream only)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
@@ -74,7 +74,7 @@ def parse_args():
     ap.add_argument("--sweep", action="store_true", help="the three methods at equal accuracy on --config")
     ap.add_argument("--sweep-taus", type=float, nargs="+", default=[1e-4, 1e-6, 1e-8])
     ap.add_argument("--sigmas", type=float, nargs="+", default=[1e-2, 1e-4, 1e-6])
-    ap.add_argument("--sweep-precs", nargs="+", default=["fp64", "bf16_split", "fp16_scaled"])
+    ap.add_argument("--sweep-precs", nargs="+", default=["fp64", "bf16_split", "bf16_split4", "fp16_scaled"])
     ap.add_argument("--block-sparse", action="store_true", help="random block-sparse sweep over fill-in")
     ap.add_argument("--bsp-n", type=int, default=2048)
     ap.add_argument("--bsp-bs", type=int, nargs="+", default=[32, 64, 128, 256])
@@ -748,7 +748,7 @@ def precision_forms(S, ctx, GA, GB, args, stream, torch):
     ref = S.spamm_multiply(ctx, GA, GB, args.tau, args.mode, "fp64")
     nref = S.spamm_frob_norm(ctx, ref)
     out = {}
-    for prec in ("bf16_split", "fp16_scaled"):
+    for prec in ("bf16_split", "bf16_split4", "fp16_scaled"):
         C = S.spamm_multiply(ctx, GA, GB, args.tau, args.mode, prec)  # untimed first run of the form
         dev = S.spamm_error(ctx, ref, C) / nref
         C.close()

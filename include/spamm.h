@@ -88,18 +88,38 @@ typedef enum {
   SPAMM_TRUNC_ERROR_CONTROL = 2
 } spamm_trunc_rule;
 
-/* Arithmetic of the leaf products.  FP64: plain double precision on the GPU.
- * BF16_SPLIT: each operand split into three bfloat16 terms, the six products
- * with term-index sum <= 2 on the tensor cores, FP32 accumulation.
- * FP16_SCALED: per-leaf power-of-two scaling, two float16 terms, FP32
- * accumulation.  Norms, the tau test and errors are always FP64.
- * Range of the two tensor-core forms: operand elements are rounded to FP32
- * first (below 2^-126 they count as 0), and the output leaves are summed in
- * FP32, so output elements must lie within the FP32 range (about 1e-38 ..
- * 3e38, relative precision lost towards the bottom); the FP16 form's per-leaf
- * scale exponents are clamped to [-120, 120].  A power-of-two rescaling of
+/* Arithmetic of the leaf products (the paper computes in FP64; the other
+ * forms run the leaf products on the tensor cores).  Norms, the tau test and
+ * errors are always FP64.
+ * FP64: plain double precision.
+ * BF16_SPLIT / BF16_SPLIT4: an error-free split taken straight from the FP64
+ * elements.  Each leaf is scaled by a power of two (largest |a| in [1, 2));
+ * each row of an A leaf and each column of a B leaf is written as 3 (SPLIT)
+ * or 4 (SPLIT4) bfloat16 slices on a grid set by the line's largest element:
+ * x = sum_s d_s 2^(e - 8 - 9 s) + r, |d_s| <= 256, |r| <= 2^(e - 9 S) with
+ * |x| < 2^e on the line.  The slice products with index sum < S are formed
+ * on the tensor cores; for each output row and column the products of one
+ * index sum are integers on a common grid, so a 64-term sum of them is exact
+ * in the FP32 accumulator (sums 0, and 1 for SPLIT4, get accumulators of
+ * their own; the smaller rest shares one).  Each leaf product is then added
+ * into a two-float (hi + lo) FP32 accumulator with an error-free TwoSum, and
+ * the output leaf is hi + lo in FP64.  Relative error about 1e-8 (SPLIT) and
+ * 1e-10 (SPLIT4) of |A||B|, from the dropped digits.
+ * FP16_SCALED: per-leaf power-of-two scaling, two float16 terms of the
+ * element rounded to FP32, FP32 accumulation: about 2e-7 relative, fastest.
+ * Range of the tensor-core forms: operand elements below 2^-1022 count as 0,
+ * digits whose unit falls below 2^-126 after the leaf scale are dropped, the
+ * per-leaf scale exponents are clamped to [-120, 120], so elements must be
+ * below about 2^100 in magnitude, and the output leaves are summed in FP32,
+ * so output elements must lie within the FP32 range (about 1e-38 .. 3e38,
+ * relative precision lost towards the bottom).  A power-of-two rescaling of
  * the inputs within that range rescales the result exactly. */
-typedef enum { SPAMM_PREC_FP64 = 0, SPAMM_PREC_BF16_SPLIT = 1, SPAMM_PREC_FP16_SCALED = 2 } spamm_prec;
+typedef enum {
+  SPAMM_PREC_FP64 = 0,
+  SPAMM_PREC_BF16_SPLIT = 1,
+  SPAMM_PREC_FP16_SCALED = 2,
+  SPAMM_PREC_BF16_SPLIT4 = 3
+} spamm_prec;
 
 /* Synthetic matrix with exponential decay (Definition 1 with c, alpha):
  *   a_ij = c u_ij exp(-alpha d(i,j)),  u_ij ~ U[-1,1) symmetric, seeded;

@@ -329,7 +329,8 @@ size_t held_bytes(const spamm_plan_s& p) {
 }
 
 void check_form(spamm_prec prec, int bs) {
-  need(prec == SPAMM_PREC_FP64 || prec == SPAMM_PREC_BF16_SPLIT || prec == SPAMM_PREC_FP16_SCALED,
+  need(prec == SPAMM_PREC_FP64 || prec == SPAMM_PREC_BF16_SPLIT || prec == SPAMM_PREC_FP16_SCALED ||
+           prec == SPAMM_PREC_BF16_SPLIT4,
        "unknown precision form");
   if (prec == SPAMM_PREC_FP64 && bs > 256)
     fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32, 64, 128 and 256");
@@ -476,10 +477,8 @@ std::vector<spamm_mat> execute_plans(spamm_ctx ctx, const std::vector<spamm_plan
     CK(cudaEventRecordWithFlags(ev.e[0], ctx->stream, evflags));
     if (prec == SPAMM_PREC_FP64)
       gemm_fp64_batch(ctx, bs, batch);
-    else if (prec == SPAMM_PREC_BF16_SPLIT)
-      gemm_bf16_batch(ctx, batch);
     else
-      gemm_fp16_batch(ctx, batch);
+      gemm_tc_batch(ctx, prec, batch);
     CK(cudaEventRecordWithFlags(ev.e[1], ctx->stream, evflags));
     for (int64_t r = 0; r < np; ++r) fill_iota_i64(ctx, P<int64_t>(outp[r]->slot), outp[r]->nleaves);
     propagate_norms_batch(ctx, nlv);

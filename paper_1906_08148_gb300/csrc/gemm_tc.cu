@@ -1,16 +1,25 @@
-// gemm_tc.cu -- kernel (c), tensor-core forms (bs = 64): BF16 three-term split
-// and FP16 with per-leaf power-of-two scaling, FP32 accumulation, with the
-// C-leaf norms of kernel (d) in the epilogue.
+// gemm_tc.cu -- kernel (c), tensor-core forms (bs = 64): BF16 error-free
+// slice splits (3 or 4 slices) and FP16 with per-leaf power-of-two scaling,
+// with the C-leaf norms of kernel (d) in the epilogue.
 //
 // Each leaf product of Algorithm 1 ("C = AB" at the lowest level) is a real
-// 64 x 64 x 64 contraction on tcgen05.  Operands are split (prep.cu, layout in
-// tcforms.cuh) into low-precision terms, each the rounding of what the
-// previous terms left:
-//   BF16 split : a = a0 + a1 + a2, b = b0 + b1 + b2 (bf16); the six products
-//                with term-index sum <= 2 are formed.
+// 64 x 64 x 64 contraction on tcgen05.  Operands are split at plan time
+// (prep.cu, layout in tcforms.cuh):
+//   BF16 split : every row of an A leaf and column of a B leaf as S = 3 or 4
+//                BF16 slices on a grid set by the line's largest element
+//                (slices.cuh); the slice products with index sum < S are
+//                formed.  For one output element the products of one index
+//                sum are integers on a common grid, so the K = 64 sum of
+//                index sum 0 (and 1 for S = 4) is exact in its own FP32
+//                accumulator; the smaller rest shares one accumulator.
 //   FP16 scaled: a' = a 2^eA with max|a'| in [2^14, 2^15) per leaf,
-//                a' = h0 + h1 (f16), likewise b'; products h0 g0, h0 g1, h1 g0,
-//                scaled back by 2^-(eA + eB).
+//                a' = h0 + h1 (f16), likewise b'; products h0 g0, h0 g1, h1 g0
+//                into one accumulator.
+// Every step's accumulators are scaled back by the step's power of two
+// (exact) and drained into registers: the FP16 form adds them to one FP32
+// accumulator per output element; the BF16 forms keep a two-float (hi + lo)
+// accumulator, adding each exact accumulator with an error-free TwoSum and
+// the rest into lo, and write hi + lo in FP64.
 //
 // Quads.  The four output leaves (2I + h, 2J + c) of a quadtree node one level
 // above the leaves are computed together: at each k the A operand of term s is
@@ -23,21 +32,23 @@
 // whole tile, but its quadrant is discarded by the epilogue; an operand leaf no
 // kept product of the step needs is not loaded (its stale contents reach only
 // discarded quadrants: each output element depends on one A row and one B
-// column).  All term products of a step accumulate, smallest first, into one
-// fresh 128 x 128 TMEM accumulator; four accumulators rotate, and the epilogue
-// drains each step into FP32 registers with round-to-nearest adds (scale
-// applied per step), which keeps the error of long k runs at the level of one
-// step.
+// column).  The 4-slice form stages each step in two K-halves (64 KB each,
+// three in flight) so that its 128 KB of operands per step still pipeline.
+// Accumulators are 128 x 128 FP32 slots of TMEM; four slots rotate, one per
+// accumulator of each step in order, so the MMAs of the next step start as
+// soon as the epilogue has drained the slots they reuse.
 //
 // Warp roles (one CTA per SM, persistent; quads are claimed one at a time
 // from a global counter in Morton order, so the quads in flight on all SMs
 // form one narrow window whose A rows and B columns are shared in L2):
 //   warp 0     TMA producer: claims the next quad for all roles (a ring of 4
-//              in shared memory), ring of NS stages, 8 KB 1-D bulk copies of
+//              in shared memory), ring of NS stages, 1-D bulk copies of
 //              pre-swizzled term tiles, mbarriers.
 //   warp 1     allocates 512 TMEM columns and issues the MMAs of each step.
-//   warps 2-9  epilogue: warps 2-5 column 0, warps 6-9 column 1; TMEM lane =
-//              output row; writes the FP64 output leaves and their squared norms.
+//   warps 2-3  idle (they fill the first warpgroup, see the register split)
+//   warps 4-11 epilogue: warps 4-7 column 0, warps 8-11 column 1; TMEM lane =
+//              output row (warp w reads lanes 32 (w mod 4) ..); writes the FP64
+//              output leaves and their squared norms.
 // No atomics on C: one CTA owns each output quad; k runs in ascending order.
 // Every wait is bounded; on timeout the CTA sets the error word and leaves.
 #include "internal.cuh"
@@ -47,33 +58,117 @@
 namespace spamm {
 
 // ------------------------------------------------------------------- GEMM
-constexpr int kQuadThreads = 320;
-constexpr int kQuadBufs = 4;  // rotating TMEM accumulators of 128 FP32 columns
+// Three warpgroups: warpgroup 0 holds the producer (warp 0) and the MMA issuer
+// (warp 1; warps 2-3 idle), warpgroups 1-2 the epilogue (warps 4-11).  The
+// launch gives every thread 168 registers (384 x 168 = 64512 of 65536); the
+// control warpgroup then gives up 112 of them per thread and the epilogue
+// takes 56 more, enough for its two-float accumulators: 128 x 56 + 256 x 224
+// = 64512, the launch total, so the increase never waits.
+constexpr int kQuadThreads = 384;
+constexpr uint32_t kLaunchRegs = 168, kCtlRegs = 56, kEpiRegs = 224;
+static_assert(128 * kCtlRegs + 256 * kEpiRegs == kQuadThreads * kLaunchRegs, "register split must match the launch");
+static_assert(kQuadThreads * kLaunchRegs <= 65536, "launch registers exceed the register file");
+constexpr int kQuadBufs = 4;  // rotating TMEM accumulator slots of 128 FP32 columns
 constexpr int kQuadQ = 4;     // ring of claimed quads shared by the three roles
+
+// One stage: two A and two B leaves, every term of a step (whole-K forms) or
+// of one K-half of it (the 4-slice form).  A region: term s at s * 2 * TILE =
+// [A(2I,k)_s; A(2I+1,k)_s] (128 rows); B region at TERMS * 2 * TILE, term t at
+// t * 2 * TILE = [B(k,2J)_t; B(k,2J+1)_t] (128 rows n).  Both are 128-row
+// K-major operands in the form's swizzle.
 template <int PREC>
-__host__ __device__ constexpr uint32_t quad_stage_bytes() {
-  return 4 * leaf_bytes<PREC>();  // two A and two B leaves, every term
-}
-template <int PREC>
-constexpr size_t quad_smem_bytes() {
-  return 1024 + (size_t)FormCfg<PREC>::NS * quad_stage_bytes<PREC>();
-}
+struct QuadLayout {
+  using Cfg = FormCfg<PREC>;
+  static constexpr uint32_t TILE = Cfg::KHALF ? kHalfTerm : kTerm;
+  static constexpr int SPS = Cfg::KHALF ? 2 : 1;  // stages per step
+  static constexpr int KS = Cfg::KHALF ? 2 : 4;   // K = 16 MMAs per stage
+  static constexpr uint32_t BREG = (uint32_t)Cfg::TERMS * 2 * TILE;
+  static constexpr uint32_t STAGE = 2 * BREG;
+  static constexpr size_t SMEM = 1024 + (size_t)Cfg::NS * STAGE;
+  __device__ static uint64_t desc(uint32_t saddr) {
+    return Cfg::KHALF ? sw64_kmajor_desc(saddr) : sw128_kmajor_desc(saddr);
+  }
+};
 
 double quad_step_flops(spamm_prec prec) {
-  const int terms = prec == SPAMM_PREC_BF16_SPLIT ? 3 : 2;
+  const int terms = prec == SPAMM_PREC_BF16_SPLIT ? 3 : (prec == SPAMM_PREC_BF16_SPLIT4 ? 4 : 2);
   return (double)(terms * (terms + 1) / 2) * 2.0 * 128.0 * 128.0 * 64.0;
 }
 
-// Stage layout: A region, term s at s * 16 KB = [A(2I,k)_s; A(2I+1,k)_s]
-// (128 rows of 64 k); B region at TERMS * 16 KB, term t at t * 16 KB =
-// [B(k,2J)_t; B(k,2J+1)_t] (128 rows n of 64 k).  Both are 128-row K-major
-// SW128 operands.
+// The MMAs of accumulator `acc` for one stage: term products (i, g - i) with
+// index sum g = acc (g from acc to TERMS - 1 for the last accumulator, the
+// largest sums first so the smallest products are added first), the first
+// of them overwriting the slot when `fresh`.
+template <int PREC, int ACC>
+__device__ __forceinline__ void issue_acc(uint32_t d, uint32_t a_s, uint32_t b_s, uint32_t idesc, bool fresh) {
+  using Cfg = FormCfg<PREC>;
+  using Lay = QuadLayout<PREC>;
+  constexpr int GLO = ACC, GHI = ACC < Cfg::NACC - 1 ? ACC : Cfg::TERMS - 1;
+  uint32_t accumulate = fresh ? 0u : 1u;
+#pragma unroll
+  for (int g = GHI; g >= GLO; --g) {
+#pragma unroll
+    for (int i = g; i >= 0; --i) {
+#pragma unroll
+      for (int ks = 0; ks < Lay::KS; ++ks) {
+        umma_f16(d, Lay::desc(a_s + (uint32_t)i * 2 * Lay::TILE + 32 * ks),
+                 Lay::desc(b_s + (uint32_t)(g - i) * 2 * Lay::TILE + 32 * ks), idesc, accumulate);
+        accumulate = 1u;
+      }
+    }
+  }
+}
+
+// Empty asm statements that read and write their registers: placed before a
+// group of FP64 conversions they keep the compiler from hoisting the
+// conversions of later groups (asm statements stay in order), which bounds
+// the registers live beside the two-float accumulators.
+__device__ __forceinline__ void pin2(uint64_t* x) { asm volatile("" : "+l"(x[0]), "+l"(x[1])); }
+__device__ __forceinline__ void pin4d(double* x) {
+  asm volatile("" : "+d"(x[0]), "+d"(x[1]), "+d"(x[2]), "+d"(x[3]));
+}
+
+// (hi, lo) += x sc for two adjacent output elements at once, with an
+// error-free TwoSum of hi and x sc (x sc is exact: sc is a power of two) in
+// the packed FP32x2 instructions, each lane rounding like the scalar
+// round-to-nearest operation: hi + lo gains x sc up to the rounding of lo.
+// hi2, lo2 hold (hi, lo) of elements 2q and 2q + 1; v0, v1 are the
+// accumulator's FP32 bits of the two elements, sc2 the scale twice.
+__device__ __forceinline__ void two_sum_x2(uint64_t& hi2, uint64_t& lo2, uint32_t v0, uint32_t v1, uint64_t sc2) {
+  asm("{\n\t.reg .b64 x, s, bp, t1, t2, t3, e;\n\t"
+      "mov.b64 x, {%2, %3};\n\t"
+      "mul.rn.f32x2 x, x, %4;\n\t"
+      "add.rn.f32x2 s, %0, x;\n\t"
+      "sub.rn.f32x2 bp, s, %0;\n\t"
+      "sub.rn.f32x2 t1, s, bp;\n\t"
+      "sub.rn.f32x2 t2, %0, t1;\n\t"
+      "sub.rn.f32x2 t3, x, bp;\n\t"
+      "add.rn.f32x2 e, t2, t3;\n\t"
+      "add.rn.f32x2 %1, %1, e;\n\t"
+      "mov.b64 %0, s;\n\t}"
+      : "+l"(hi2), "+l"(lo2)
+      : "r"(v0), "r"(v1), "l"(sc2));
+}
+// lo2 += (v0, v1) sc2, packed.
+__device__ __forceinline__ void fma_x2(uint64_t& lo2, uint32_t v0, uint32_t v1, uint64_t sc2) {
+  asm("{\n\t.reg .b64 x;\n\t"
+      "mov.b64 x, {%1, %2};\n\t"
+      "fma.rn.f32x2 %0, x, %3, %0;\n\t}"
+      : "+l"(lo2)
+      : "r"(v0), "r"(v1), "l"(sc2));
+}
+__device__ __forceinline__ float2 unpack2(uint64_t x) {
+  return make_float2(__uint_as_float((uint32_t)x), __uint_as_float((uint32_t)(x >> 32)));
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(kQuadThreads, 1)
     gemm_quad_kernel(BatchDev batch, unsigned long long* __restrict__ work, int* __restrict__ err) {
   using Cfg = FormCfg<PREC>;
-  constexpr int NS = Cfg::NS, TERMS = Cfg::TERMS, NB = kQuadBufs;
-  constexpr uint32_t LEAF = leaf_bytes<PREC>(), STAGE = quad_stage_bytes<PREC>(), BREG = 2 * LEAF;
+  using Lay = QuadLayout<PREC>;
+  constexpr int NS = Cfg::NS, TERMS = Cfg::TERMS, NACC = Cfg::NACC, NB = kQuadBufs, SPS = Lay::SPS;
+  constexpr uint32_t LEAF = leaf_bytes<PREC>(), STAGE = Lay::STAGE, BREG = Lay::BREG, TILE = Lay::TILE;
+  static_assert(NACC <= NB - 1, "the next step needs a free accumulator slot");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full[NS], empty[NS], tfull[NB], tempty[NB], qfull[kQuadQ], qempty[kQuadQ];
@@ -108,11 +203,12 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
   tc_fence_after();
   const uint32_t tbase = tmem_base;
   volatile int* abortp = &abort_flag;
-
+  if (warp < 4) {
+    regs_dec<kCtlRegs>();  // every warp of warpgroup 0, at this one instruction
   if (warp == 0) {
     // ---------------- TMA producer; claims the quads (Morton order, first come first served) for all roles
     if (lane == 0) {
-      int64_t t = 0;
+      int64_t t = 0;  // stages filled
       bool stop = false;
       for (int64_t c = 0; !stop; ++c) {
         const int qs = (int)(c % kQuadQ);
@@ -133,39 +229,43 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
         int64_t j = pl.qstart[Q];
         const int4* rec = reinterpret_cast<const int4*>(pl.qsteps);  // word 2j: a0, a1, b0, b1 of step j
         int4 nx = j < j1 ? __ldg(rec + 2 * j) : make_int4(-1, -1, -1, -1);
-        for (; j < j1; ++j) {
+        for (; j < j1 && !stop; ++j) {
           const int4 ab = nx;
           if (j + 1 < j1) nx = __ldg(rec + 2 * (j + 1));  // next step's leaves, in flight during the wait
-          const int s = (int)(t % NS);
-          if (t >= NS && !mbar_wait_or_abort(&empty[s], (uint32_t)(((t / NS) - 1) & 1), abortp)) {
-            atomicOr(err, DEV_ERR_TIMEOUT);
-            *abortp = 1;
-            stop = true;
-            break;
-          }
-          uint8_t* st = smem + s * STAGE;
           const uint32_t nload = (uint32_t)((ab.x >= 0) + (ab.y >= 0) + (ab.z >= 0) + (ab.w >= 0));
-          mbar_arrive_expect_tx(&full[s], nload * LEAF);
 #pragma unroll
-          for (int term = 0; term < TERMS; ++term) {
-            uint8_t* sa = st + term * 2 * kTerm;
-            uint8_t* sb = st + BREG + term * 2 * kTerm;
-            if (ab.x >= 0) bulk_g2s(sa, pl.termsA + (int64_t)ab.x * LEAF + term * kTerm, kTerm, &full[s]);
-            if (ab.y >= 0) bulk_g2s(sa + kTerm, pl.termsA + (int64_t)ab.y * LEAF + term * kTerm, kTerm, &full[s]);
-            if (ab.z >= 0) bulk_g2s(sb, pl.termsB + (int64_t)ab.z * LEAF + term * kTerm, kTerm, &full[s]);
-            if (ab.w >= 0) bulk_g2s(sb + kTerm, pl.termsB + (int64_t)ab.w * LEAF + term * kTerm, kTerm, &full[s]);
+          for (int h = 0; h < SPS; ++h) {
+            const int s = (int)(t % NS);
+            if (t >= NS && !mbar_wait_or_abort(&empty[s], (uint32_t)(((t / NS) - 1) & 1), abortp)) {
+              atomicOr(err, DEV_ERR_TIMEOUT);
+              *abortp = 1;
+              stop = true;
+              break;
+            }
+            uint8_t* st = smem + s * STAGE;
+            mbar_arrive_expect_tx(&full[s], nload * TERMS * TILE);
+#pragma unroll
+            for (int term = 0; term < TERMS; ++term) {
+              uint8_t* sa = st + term * 2 * TILE;
+              uint8_t* sb = st + BREG + term * 2 * TILE;
+              const int64_t off = Cfg::KHALF ? (int64_t)(h * TERMS + term) * kHalfTerm : (int64_t)term * kTerm;
+              if (ab.x >= 0) bulk_g2s(sa, pl.termsA + (int64_t)ab.x * LEAF + off, TILE, &full[s]);
+              if (ab.y >= 0) bulk_g2s(sa + TILE, pl.termsA + (int64_t)ab.y * LEAF + off, TILE, &full[s]);
+              if (ab.z >= 0) bulk_g2s(sb, pl.termsB + (int64_t)ab.z * LEAF + off, TILE, &full[s]);
+              if (ab.w >= 0) bulk_g2s(sb + TILE, pl.termsB + (int64_t)ab.w * LEAF + off, TILE, &full[s]);
+            }
+            ++t;
           }
-          ++t;
         }
       }
       // leave no bulk copy in flight: the last fill of every stage has landed
       for (int64_t k = (t > NS ? t - NS : 0); k < t; ++k) mbar_wait_bounded(&full[k % NS], (uint32_t)((k / NS) & 1));
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer: every term product of a step into accumulator t % NB
+    // ---------------- MMA issuer: the accumulators of step number n are slots (NACC n + a) % NB
     if (lane == 0) {
       constexpr uint32_t idesc = umma_idesc_f16(Cfg::AB, 128, 128);
-      int64_t t = 0;
+      int64_t t = 0, u = 0;  // stages consumed, accumulator units started
       bool stop = false;
       for (int64_t c = 0; !stop; ++c) {
         const int qs = (int)(c % kQuadQ);
@@ -181,51 +281,64 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
         const PlanDev& pl = batch.plans[r];
         const int64_t Q = un - batch.ubegin[r];
         const int64_t nstep = pl.qstart[Q + 1] - pl.qstart[Q];
-        for (int64_t j = 0; j < nstep; ++j) {
-          const int s = (int)(t % NS);
-          const int b = (int)(t % NB);
-          if (!mbar_wait_or_abort(&full[s], (uint32_t)((t / NS) & 1), abortp) ||
-              (t >= NB && !mbar_wait_or_abort(&tempty[b], (uint32_t)(((t / NB) - 1) & 1), abortp))) {
-            atomicOr(err, DEV_ERR_TIMEOUT);
-            *abortp = 1;
-            stop = true;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t d = tbase + (uint32_t)b * 128u;
-          const uint32_t a_s = smem_u32(smem + s * STAGE), b_s = a_s + BREG;
-          uint32_t accumulate = 0u;
-          // term products (i, sum - i), smallest term-index sum first
+        for (int64_t j = 0; j < nstep && !stop; ++j) {
 #pragma unroll
-          for (int sum = TERMS - 1; sum >= 0; --sum) {
-#pragma unroll
-            for (int i = sum; i >= 0; --i) {
-#pragma unroll
-              for (int ks = 0; ks < 4; ++ks) {
-                umma_f16(d, sw128_kmajor_desc(a_s + i * 2 * kTerm + 32 * ks),
-                         sw128_kmajor_desc(b_s + (sum - i) * 2 * kTerm + 32 * ks), idesc, accumulate);
-                accumulate = 1u;
-              }
+          for (int h = 0; h < SPS; ++h) {
+            const int s = (int)(t % NS);
+            if (!mbar_wait_or_abort(&full[s], (uint32_t)((t / NS) & 1), abortp)) {
+              stop = true;
+              break;
             }
+            tc_fence_after();
+            const uint32_t a_s = smem_u32(smem + s * STAGE), b_s = a_s + BREG;
+#pragma unroll
+            for (int a = 0; a < NACC; ++a) {
+              const int64_t un_a = u + a;
+              const int b = (int)(un_a % NB);
+              if (h == 0 && un_a >= NB) {
+                if (!mbar_wait_or_abort(&tempty[b], (uint32_t)(((un_a / NB) - 1) & 1), abortp)) {
+                  stop = true;
+                  break;
+                }
+                tc_fence_after();
+              }
+              const uint32_t d = tbase + (uint32_t)b * 128u;
+              if (a == 0) issue_acc<PREC, 0>(d, a_s, b_s, idesc, h == 0);
+              if constexpr (NACC > 1) if (a == 1) issue_acc<PREC, (NACC > 1 ? 1 : 0)>(d, a_s, b_s, idesc, h == 0);
+              if constexpr (NACC > 2) if (a == 2) issue_acc<PREC, (NACC > 2 ? 2 : 0)>(d, a_s, b_s, idesc, h == 0);
+              if (h == SPS - 1) umma_commit(&tfull[b]);
+            }
+            if (stop) break;
+            umma_commit(&empty[s]);
+            ++t;
           }
-          umma_commit(&empty[s]);
-          umma_commit(&tfull[b]);
-          ++t;
+          if (!stop) u += NACC;
+        }
+        if (stop) {
+          atomicOr(err, DEV_ERR_TIMEOUT);
+          *abortp = 1;
         }
       }
-      // leave no MMA in flight: the last accumulator has been written
-      if (t > 0) mbar_wait_bounded(&tfull[(t - 1) % NB], (uint32_t)(((t - 1) / NB) & 1));
+      // leave no MMA in flight: everything issued before the last commit has completed
+      if (t > 0) mbar_wait_bounded(&empty[(t - 1) % NS], (uint32_t)(((t - 1) / NS) & 1));
     }
+  }
   } else {
-    // ---------------- epilogue: warps 2..9; column c = (warp - 2) / 4; TMEM lane = output row
-    const int col = (warp - 2) >> 2;
+    regs_inc<kEpiRegs>();
+    // ---------------- epilogue: warps 4..11; column c = (warp - 4) / 4; TMEM lane = output row
+    const int col = (warp - 4) >> 2;
     const int quarter = warp & 3;
     const int lrow = 32 * quarter + lane;
     const int half = lrow >> 6, row = lrow & 63;
     const int child = 2 * half + col;  // warp-uniform
-    const int te = threadIdx.x - 64;   // 0..255
-    int64_t t = 0;
-    float acc[64];
+    const int te = threadIdx.x - 128;  // 0..255
+    const uint32_t taddr0 = tbase + ((uint32_t)(32 * quarter) << 16) + 64u * (uint32_t)col;
+    int64_t u = 0;  // accumulator units drained
+    // FP16: one FP32 accumulator per element; BF16 splits: (hi, lo) pairs of
+    // adjacent elements packed for the FP32x2 instructions
+    constexpr int NHI = NACC == 1 ? 64 : 1, NPK = NACC == 1 ? 1 : 32;
+    float hi[NHI];
+    uint64_t hi2[NPK], lo2[NPK];
     for (int64_t c = 0;; ++c) {
       // one thread takes the next claimed quad for all 256 (-2: the wait gave up)
       if (te == 0) {
@@ -251,33 +364,60 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
       const int64_t Q = un - batch.ubegin[r];
       const int32_t g[4] = {pl.quads[4 * Q], pl.quads[4 * Q + 1], pl.quads[4 * Q + 2], pl.quads[4 * Q + 3]};
 #pragma unroll
-      for (int c = 0; c < 64; ++c) acc[c] = 0.f;
+      for (int i = 0; i < NHI; ++i) hi[i] = 0.f;
+#pragma unroll
+      for (int i = 0; i < NPK; ++i) hi2[i] = lo2[i] = 0ull;
       const int64_t j1 = pl.qstart[Q + 1];
       int64_t j = pl.qstart[Q];
       float sc_next = j < j1 ? __ldg(&pl.qsteps[j].scale[child]) : 0.f;
-      for (; j < j1; ++j) {
+      bool failed = false;
+      for (; j < j1 && !failed; ++j) {
         const float sc = sc_next;
         if (j + 1 < j1) sc_next = __ldg(&pl.qsteps[j + 1].scale[child]);
-        const int b = (int)(t % NB);
-        bool ok = true;
-        if (lane == 0) ok = mbar_wait_or_abort(&tfull[b], (uint32_t)((t / NB) & 1), abortp);
-        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-        ++t;
-        if (!ok) {
-          // the epilogue still runs the barrier sequence below, then stops together
-          atomicOr(err, DEV_ERR_TIMEOUT);
-          *abortp = 1;
-          break;
-        }
-        tc_fence_after();
-        if (sc != 0.f) {  // this warp's child has a kept product at this k
-          float v[64];
-          tmem_ld64(tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)b * 128u + 64u * (uint32_t)col, v);
+        // one accumulator at a time, in the order the MMAs commit them; a
+        // runtime loop, so the code holds one copy of each update kind
+#pragma unroll 1
+        for (int a = 0; a < NACC; ++a) {
+          const int b = (int)(u % NB);
+          bool ok = true;
+          if (lane == 0) ok = mbar_wait_or_abort(&tfull[b], (uint32_t)((u / NB) & 1), abortp);
+          ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+          ++u;
+          if (!ok) {
+            // the epilogue still runs the barrier sequence below, then stops together
+            atomicOr(err, DEV_ERR_TIMEOUT);
+            *abortp = 1;
+            failed = true;
+            break;
+          }
+          tc_fence_after();
+          if (sc != 0.f) {  // this warp's child has a kept product at this k
+            const bool exact = a < NACC - 1;  // an exact accumulator: TwoSum into (hi, lo)
+            const uint64_t sc2 = ((uint64_t)__float_as_uint(sc) << 32) | __float_as_uint(sc);
+            // four 16-column chunks; chunk hh + 1 is in flight while chunk hh is added
+            const uint32_t ta = taddr0 + (uint32_t)b * 128u;
+            uint32_t buf[2][16];
+            tmem_ld16_async(ta, buf[0]);
 #pragma unroll
-          for (int i = 0; i < 64; ++i) acc[i] = fmaf(v[i], sc, acc[i]);
+            for (int hh = 0; hh < 4; ++hh) {
+              uint32_t* v = buf[hh & 1];
+              tmem_wait16(v);
+              if (hh + 1 < 4) tmem_ld16_async(ta + 16u * (hh + 1), buf[(hh + 1) & 1]);
+              if constexpr (NACC == 1) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) hi[16 * hh + i] = fmaf(__uint_as_float(v[i]), sc, hi[16 * hh + i]);
+              } else if (exact) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) two_sum_x2(hi2[8 * hh + i], lo2[8 * hh + i], v[2 * i], v[2 * i + 1], sc2);
+              } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) fma_x2(lo2[8 * hh + i], v[2 * i], v[2 * i + 1], sc2);
+              }
+            }
+          }
+          tc_fence_before();
+          mbar_arrive(&tempty[b]);
         }
-        tc_fence_before();
-        mbar_arrive(&tempty[b]);
       }
       // output row `row` of leaf g[child]: FP64, and its squared norm
       const int gl = g[child];
@@ -285,11 +425,27 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
       if (gl >= 0) {
         double2* out = reinterpret_cast<double2*>(pl.cpool + (int64_t)gl * 4096 + row * 64);
 #pragma unroll
-        for (int c = 0; c < 64; c += 2) {
-          const double x = (double)acc[c], y = (double)acc[c + 1];
-          out[c >> 1] = make_double2(x, y);
-          s2 = __fma_rn(x, x, s2);
-          s2 = __fma_rn(y, y, s2);
+        for (int q = 0; q < 64; q += 4) {
+          double x[4];
+          if constexpr (NACC == 1) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x[i] = (double)hi[q + i];
+          } else {
+            // one group of four at a time: the FP64 conversions are not hoisted
+            pin2(hi2 + q / 2);
+            pin2(lo2 + q / 2);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+              const float2 h = unpack2(hi2[q / 2 + i]), l = unpack2(lo2[q / 2 + i]);
+              x[2 * i] = (double)h.x + (double)l.x;
+              x[2 * i + 1] = (double)h.y + (double)l.y;
+            }
+          }
+          out[q >> 1] = make_double2(x[0], x[1]);
+          out[(q >> 1) + 1] = make_double2(x[2], x[3]);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) s2 = __fma_rn(x[i], x[i], s2);
+          if constexpr (NACC > 1) pin4d(x);
         }
       }
 #pragma unroll
@@ -324,7 +480,13 @@ static unsigned gemm_grid(spamm_ctx ctx, int64_t nunits) {
 template <int PREC>
 static void launch_quads(spamm_ctx ctx, const BatchDev& b) {
   if (b.nunits == 0) return;
-  const size_t smem = quad_smem_bytes<PREC>();
+  const size_t smem = QuadLayout<PREC>::SMEM;
+  // the register split in the kernel assumes exactly kLaunchRegs per thread at
+  // launch: with fewer, the epilogue's increase could never be granted
+  cudaFuncAttributes attr;
+  CK(cudaFuncGetAttributes(&attr, gemm_quad_kernel<PREC>));
+  if (attr.numRegs != (int)kLaunchRegs || attr.maxThreadsPerBlock < kQuadThreads)
+    fail(SPAMM_E_CUDA, "tensor-core kernel built with an unexpected register count; refusing to launch");
   CK(cudaFuncSetAttribute(gemm_quad_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   unsigned long long* work = ctx->d_scratch + 9;  // quad claim counter
   CK(cudaMemsetAsync(work, 0, sizeof(unsigned long long), ctx->stream));
@@ -332,7 +494,13 @@ static void launch_quads(spamm_ctx ctx, const BatchDev& b) {
   CK_LAUNCH("gemm_quad_kernel");
 }
 
-void gemm_bf16_batch(spamm_ctx ctx, const BatchDev& b) { launch_quads<SPAMM_PREC_BF16_SPLIT>(ctx, b); }
-void gemm_fp16_batch(spamm_ctx ctx, const BatchDev& b) { launch_quads<SPAMM_PREC_FP16_SCALED>(ctx, b); }
+void gemm_tc_batch(spamm_ctx ctx, spamm_prec prec, const BatchDev& b) {
+  switch (prec) {
+    case SPAMM_PREC_BF16_SPLIT: launch_quads<SPAMM_PREC_BF16_SPLIT>(ctx, b); break;
+    case SPAMM_PREC_BF16_SPLIT4: launch_quads<SPAMM_PREC_BF16_SPLIT4>(ctx, b); break;
+    case SPAMM_PREC_FP16_SCALED: launch_quads<SPAMM_PREC_FP16_SCALED>(ctx, b); break;
+    default: fail(SPAMM_E_INVALID_ARG, "not a tensor-core precision form");
+  }
+}
 
 }  // namespace spamm

@@ -238,13 +238,14 @@ int fp64_units_per_leaf(int bs);
 // (stable), for the FP64 kernel's unit claiming; an empty buffer when the
 // leaves are small enough that the claiming tail does not matter.
 BufP fp64_unit_order(spamm_ctx ctx, const TaskList& T, int bs);
-void gemm_fp16_batch(spamm_ctx ctx, const BatchDev& b);
-void gemm_bf16_batch(spamm_ctx ctx, const BatchDev& b);
-// Operand terms of a leaf set for a tensor form (role 0: used as A, 1: as B).
+// The tensor-core forms' persistent quad kernel (gemm_tc.cu).
+void gemm_tc_batch(spamm_ctx ctx, spamm_prec prec, const BatchDev& b);
+// Operand terms of a leaf set for a tensor form (role 0: used as A, 1: as B),
+// and each leaf's power-of-two scale exponent.
 void prep_terms(spamm_mat M, spamm_prec prec, int role, BufP* terms, BufP* expo, spamm_ctx on = nullptr);
 // Step list of every quad of T for the tensor-core kernel; returns the step count.
 // codeA: Morton codes of A's leaves (the k of a task is the column of its A
-// leaf); expA/expB: FP16 scale exponents (null: no scaling).
+// leaf); expA/expB: the leaves' scale exponents (null: no scaling).
 int64_t build_quad_steps(spamm_ctx ctx, const TaskList& T, const uint32_t* codeA, const int32_t* expA,
                          const int32_t* expB, BufP* qstart, BufP* qsteps);
 // Tensor-core flops one quad step executes (every term product over the full 128 x 128 tile).

@@ -24,8 +24,9 @@ MODE_TRUNCATE, MODE_SPAMM, MODE_COMBINED = 0, 1, 2
 MODES = {"truncate": MODE_TRUNCATE, "spamm": MODE_SPAMM, "combined": MODE_COMBINED}
 TRUNC_BLOCK_FROB, TRUNC_ELEMENT, TRUNC_ERROR_CONTROL = 0, 1, 2
 RULES = {"block": TRUNC_BLOCK_FROB, "element": TRUNC_ELEMENT, "error": TRUNC_ERROR_CONTROL}
-PREC_FP64, PREC_BF16_SPLIT, PREC_FP16_SCALED = 0, 1, 2
-PRECS = {"fp64": PREC_FP64, "bf16_split": PREC_BF16_SPLIT, "fp16_scaled": PREC_FP16_SCALED}
+PREC_FP64, PREC_BF16_SPLIT, PREC_FP16_SCALED, PREC_BF16_SPLIT4 = 0, 1, 2, 3
+PRECS = {"fp64": PREC_FP64, "bf16_split": PREC_BF16_SPLIT, "fp16_scaled": PREC_FP16_SCALED,
+         "bf16_split4": PREC_BF16_SPLIT4}
 MAX_LEVELS = 17
 
 # every entry point of include/spamm.h
