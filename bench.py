@@ -578,6 +578,16 @@ def run_passes(args, cfg):
         ms.append(e0.elapsed_time(e1))
     norm_ms = statistics.median(ms[1:])
     norm_bytes = nl * (bs * bs * 8 + 8)
+    # the library's own norm pass (leaf_sqnorm_kernel) runs inside a build from
+    # device-resident leaves; its time is read from the ncu launch list
+    bi, bj, pay_h, _ = S.spamm_to_blocks(ctx, GA)
+    dbi, dbj = torch.from_numpy(bi).cuda(), torch.from_numpy(bj).cuda()
+    dpay = torch.from_numpy(pay_h).cuda()
+    del pay_h
+    for _ in range(2):
+        S.spamm_from_blocks(ctx, cfg["n"], bs, dbi, dbj, dpay).close()
+    torch.cuda.synchronize()
+    del dbi, dbj, dpay
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = float(peaks.get("hbm_gbs", 6800.0))

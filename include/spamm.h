@@ -160,6 +160,8 @@ typedef struct {
   int64_t n_steps;       /* leaf-GEMM steps: FP64 = n_kept; tensor forms = k steps of output quads */
   double executed_flops; /* flops the leaf-GEMM kernel executes: FP64 = kept_flops; tensor forms =
                             n_steps x every term product over a 128 x 128 x 64 tile */
+  int64_t terms_shared;  /* tensor forms: 1 if A and B were one symmetric matrix and one set of
+                            operand terms served both roles (see spamm_set_symmetric), else 0 */
 } spamm_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -347,6 +349,19 @@ SPAMM_API spamm_status spamm_error(spamm_ctx ctx, spamm_mat X, spamm_mat Y, doub
 
 /* Shape of a handle: any output pointer may be NULL. */
 SPAMM_API spamm_status spamm_mat_info(spamm_mat m, int64_t* n, int32_t* bs, int32_t* levels, int64_t* nleaves);
+
+/* Mark m as symmetric (symmetric != 0) or not.  spamm_generate marks its
+ * matrices (the decay generators are symmetric in (i, j)); truncation keeps
+ * the mark.  When one marked handle is both operands of a tensor-core
+ * multiply (X times X, the squarings of a purification chain), the operand
+ * terms of X are built once and serve both roles: B's leaf (k, j) uses the
+ * terms of leaf (j, k), which are exactly its own B terms for a symmetric X,
+ * halving the memory of the terms; if some leaf's transpose is absent from
+ * the leaf set (possible after truncation when two norms straddle tau by an
+ * ulp), the terms are built separately as for any A and B.  The result is
+ * then X X^T, so the mark must only be set on matrices equal to their
+ * transpose.  Errors: SPAMM_E_INVALID_ARG (m NULL). */
+SPAMM_API spamm_status spamm_set_symmetric(spamm_mat m, int symmetric);
 
 /* Dense copy of M into `out` (row-major, leading dimension ld >= n). */
 SPAMM_API spamm_status spamm_to_dense(spamm_ctx ctx, spamm_mat m, double* out, int64_t ld, int on_device);

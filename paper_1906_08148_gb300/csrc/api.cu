@@ -310,6 +310,7 @@ struct spamm_plan_s {
   TaskList T;
   BufP poolA, slotA, poolB, slotB, termsA, termsB, expA, expB;
   BufP qstart, qsteps;  // tensor forms: the quad step list
+  BufP bmap;            // tensor forms, symmetric X times X: B leaf -> A leaf whose terms serve it
   BufP uorder;          // FP64 form: unit -> output leaf, longest first (empty: identity)
   int64_t nsteps = 0;
   std::vector<Level> cskel;  // output quadtree structure (codes, child links; no norms)
@@ -322,9 +323,16 @@ namespace {
 
 size_t held_bytes(const spamm_plan_s& p) {
   size_t b = 0;
-  for (const BufP* x : {&p.T.gcode, &p.T.gstart, &p.T.ta, &p.T.tb, &p.T.quads, &p.qstart, &p.qsteps, &p.slotA, &p.slotB, &p.termsA,
-                        &p.termsB, &p.expA, &p.expB, &p.uorder})
-    if (*x) b += (*x)->bytes;
+  std::vector<const Buf*> seen;
+  for (const BufP* x : {&p.T.gcode, &p.T.gstart, &p.T.ta, &p.T.tb, &p.T.quads, &p.qstart, &p.qsteps, &p.slotA,
+                        &p.slotB, &p.termsA, &p.termsB, &p.expA, &p.expB, &p.uorder, &p.bmap}) {
+    if (!*x) continue;
+    bool dup = false;  // shared buffers (symmetric operands) count once
+    for (const Buf* q : seen) dup = dup || q == x->get();
+    if (dup) continue;
+    seen.push_back(x->get());
+    b += (*x)->bytes;
+  }
   return b;
 }
 
@@ -374,9 +382,19 @@ spamm_plan make_plan(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_
     p->uorder = fp64_unit_order(ctx, p->T, p->bs);
   } else {
     prep_terms(At, prec, 0, &p->termsA, &p->expA, ctx);
-    prep_terms(Bt, prec, 1, &p->termsB, &p->expB, ctx);
+    // X times X with X symmetric: the B operand of leaf (k, j) is the transpose
+    // of leaf (j, k), whose A terms are exactly the B terms of (k, j) (rows of
+    // (j, k) are columns of (k, j), with the same grid), so one set of terms
+    // serves both roles, if every leaf's transpose is present
+    if (Bt == At && At->symmetric && transpose_map(At, &p->bmap, ctx) == 0) {
+      p->termsB = p->termsA;
+      p->expB = p->expA;
+    } else {
+      p->bmap.reset();
+      prep_terms(Bt, prec, 1, &p->termsB, &p->expB, ctx);
+    }
     p->nsteps = build_quad_steps(ctx, p->T, P<uint32_t>(At->lv[At->L].code), P<int32_t>(p->expA),
-                                 P<int32_t>(p->expB), &p->qstart, &p->qsteps);
+                                 P<int32_t>(p->expB), P<int32_t>(p->bmap), &p->qstart, &p->qsteps);
   }
   CK(cudaEventRecord(ev.e[3], ctx->stream));
   sync_and_check(ctx);
@@ -404,6 +422,7 @@ void fill_stats(const spamm_plan_s& p, spamm_stats* st) {
   st->kept_flops = 2.0 * (double)p.bs * p.bs * p.bs * (double)p.T.ntasks;
   st->n_steps = p.prec == SPAMM_PREC_FP64 ? p.T.ntasks : p.nsteps;
   st->executed_flops = p.prec == SPAMM_PREC_FP64 ? st->kept_flops : (double)p.nsteps * quad_step_flops(p.prec);
+  st->terms_shared = p.bmap ? 1 : 0;
   st->ms_truncate = p.ms_truncate;
   st->ms_tasks = p.ms_tasks;
   st->ms_prep = p.ms_prep;
@@ -679,6 +698,12 @@ spamm_status spamm_error(spamm_ctx ctx, spamm_mat X, spamm_mat Y, double* out) {
     if (X->n != Y->n || X->bs != Y->bs) fail(SPAMM_E_SHAPE, "X and Y differ in n or bs");
     *out = error_fro(X, Y);
   });
+}
+
+spamm_status spamm_set_symmetric(spamm_mat m, int symmetric) {
+  if (!m) return SPAMM_E_INVALID_ARG;
+  m->symmetric = symmetric != 0;
+  return SPAMM_OK;
 }
 
 spamm_status spamm_mat_info(spamm_mat m, int64_t* n, int32_t* bs, int32_t* levels, int64_t* nleaves) {

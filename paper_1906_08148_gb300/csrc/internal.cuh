@@ -125,6 +125,7 @@ struct spamm_mat_s {
   int64_t nleaves = 0;
   spamm::BufP pool;  // double payload, bs*bs per slot
   spamm::BufP slot;  // int64 per leaf: payload slot of leaf m (leaves in Morton order)
+  int symmetric = 0;  // the matrix equals its transpose (set by the generator or the caller)
   std::vector<spamm::Level> lv;  // levels 0..L
 };
 
@@ -246,8 +247,14 @@ void prep_terms(spamm_mat M, spamm_prec prec, int role, BufP* terms, BufP* expo,
 // Step list of every quad of T for the tensor-core kernel; returns the step count.
 // codeA: Morton codes of A's leaves (the k of a task is the column of its A
 // leaf); expA/expB: the leaves' scale exponents (null: no scaling).
+// bmap (may be null): for B's leaf q, the index of the leaf whose terms serve
+// as its B operand (a symmetric matrix times itself uses A's terms of the
+// transposed leaf); the step list then refers to that index.
 int64_t build_quad_steps(spamm_ctx ctx, const TaskList& T, const uint32_t* codeA, const int32_t* expA,
-                         const int32_t* expB, BufP* qstart, BufP* qsteps);
+                         const int32_t* expB, const int32_t* bmap, BufP* qstart, BufP* qsteps);
+// For every leaf (k, j) of M, the index of leaf (j, k) in M (-1 if absent);
+// returns the number of absent ones (synchronises).
+int64_t transpose_map(spamm_mat M, BufP* map, spamm_ctx on = nullptr);
 // Tensor-core flops one quad step executes (every term product over the full 128 x 128 tile).
 double quad_step_flops(spamm_prec prec);
 }  // namespace spamm

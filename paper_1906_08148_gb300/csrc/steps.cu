@@ -46,8 +46,9 @@ struct QuadMerge {
 __global__ void quad_steps_kernel(int64_t nquads, const int32_t* __restrict__ quads, const int64_t* __restrict__ gstart,
                                   const int32_t* __restrict__ ta, const int32_t* __restrict__ tb,
                                   const uint32_t* __restrict__ codeA, const int32_t* __restrict__ expA,
-                                  const int32_t* __restrict__ expB, uint64_t* __restrict__ count,
-                                  const uint64_t* __restrict__ qstart, QuadStep* __restrict__ out) {
+                                  const int32_t* __restrict__ expB, const int32_t* __restrict__ bmap,
+                                  uint64_t* __restrict__ count, const uint64_t* __restrict__ qstart,
+                                  QuadStep* __restrict__ out) {
   for (int64_t Q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; Q < nquads; Q += (int64_t)gridDim.x * blockDim.x) {
     const int32_t g[4] = {quads[4 * Q], quads[4 * Q + 1], quads[4 * Q + 2], quads[4 * Q + 3]};
     QuadMerge m(g, gstart);
@@ -63,6 +64,10 @@ __global__ void quad_steps_kernel(int64_t nquads, const int32_t* __restrict__ qu
         st.a[1] = (has & 4u) ? ta[q[2]] : ((has & 8u) ? ta[q[3]] : -1);
         st.b[0] = (has & 1u) ? tb[q[0]] : ((has & 4u) ? tb[q[2]] : -1);
         st.b[1] = (has & 2u) ? tb[q[1]] : ((has & 8u) ? tb[q[3]] : -1);
+        if (bmap) {
+          if (st.b[0] >= 0) st.b[0] = bmap[st.b[0]];
+          if (st.b[1] >= 0) st.b[1] = bmap[st.b[1]];
+        }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           float sc = 0.f;
@@ -70,7 +75,7 @@ __global__ void quad_steps_kernel(int64_t nquads, const int32_t* __restrict__ qu
             sc = 1.f;
             if (expA) {
               // 2^-(eA + eB) as a product of two normal powers of two (|e| <= 120)
-              const int ea = expA[ta[q[c]]], eb = expB[tb[q[c]]];
+              const int ea = expA[ta[q[c]]], eb = expB[bmap ? bmap[tb[q[c]]] : tb[q[c]]];
               sc = __int_as_float((127 - ea) << 23) * __int_as_float((127 - eb) << 23);
             }
           }
@@ -84,8 +89,42 @@ __global__ void quad_steps_kernel(int64_t nquads, const int32_t* __restrict__ qu
   }
 }
 
+// Leaf (k, j) of M -> index of leaf (j, k): binary search over M's
+// Morton-sorted leaf codes; misses are counted in *missing.
+__global__ void transpose_map_kernel(int64_t n, const uint32_t* __restrict__ code, int32_t* __restrict__ map,
+                                     unsigned long long* missing) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t want = morton2(code_col(code[q]), code_row(code[q]));
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (code[mid] < want)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    const bool hit = code[lo] == want;
+    map[q] = hit ? (int32_t)lo : -1;
+    if (!hit) atomicAdd(missing, 1ull);
+  }
+}
+
+int64_t transpose_map(spamm_mat M, BufP* map, spamm_ctx on) {
+  spamm_ctx ctx = on ? on : M->ctx;
+  const int64_t n = M->nleaves;
+  *map = alloc_n<int32_t>(ctx, n);
+  if (n == 0) return 0;
+  unsigned long long* missing = ctx->d_scratch + 10;
+  CK(cudaMemsetAsync(missing, 0, sizeof(unsigned long long), ctx->stream));
+  const int64_t want = (n + 255) / 256, cap = (int64_t)ctx->num_sms * 16;
+  transpose_map_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, ctx->stream>>>(
+      n, P<uint32_t>(M->lv[M->L].code), P<int32_t>(*map), missing);
+  CK_LAUNCH("transpose_map_kernel");
+  return (int64_t)read_scalar(ctx, reinterpret_cast<const uint64_t*>(missing));
+}
+
 int64_t build_quad_steps(spamm_ctx ctx, const TaskList& T, const uint32_t* codeA, const int32_t* expA,
-                         const int32_t* expB, BufP* qstart, BufP* qsteps) {
+                         const int32_t* expB, const int32_t* bmap, BufP* qstart, BufP* qsteps) {
   const int64_t nq = T.ngroups > 0 ? T.nquads : 0;
   *qstart = alloc_n<uint64_t>(ctx, nq + 1);
   *qsteps = nullptr;
@@ -97,14 +136,14 @@ int64_t build_quad_steps(spamm_ctx ctx, const TaskList& T, const uint32_t* codeA
   const int64_t want = (nq + 255) / 256, cap = (int64_t)ctx->num_sms * 16;
   const unsigned grid = (unsigned)(want < cap ? want : cap);
   quad_steps_kernel<<<grid, 256, 0, ctx->stream>>>(nq, P<int32_t>(T.quads), P<int64_t>(T.gstart), P<int32_t>(T.ta),
-                                                   P<int32_t>(T.tb), codeA, expA, expB, P<uint64_t>(cnt), nullptr,
-                                                   nullptr);
+                                                   P<int32_t>(T.tb), codeA, expA, expB, bmap, P<uint64_t>(cnt),
+                                                   nullptr, nullptr);
   CK_LAUNCH("quad_steps_kernel(count)");
   scan_exclusive_u64(ctx, P<uint64_t>(cnt), P<uint64_t>(*qstart), nq, P<uint64_t>(*qstart) + nq);
   const int64_t total = (int64_t)read_scalar(ctx, P<uint64_t>(*qstart) + nq);
   *qsteps = alloc_n<QuadStep>(ctx, total);
   quad_steps_kernel<<<grid, 256, 0, ctx->stream>>>(nq, P<int32_t>(T.quads), P<int64_t>(T.gstart), P<int32_t>(T.ta),
-                                                   P<int32_t>(T.tb), codeA, expA, expB, nullptr,
+                                                   P<int32_t>(T.tb), codeA, expA, expB, bmap, nullptr,
                                                    P<uint64_t>(*qstart), P<QuadStep>(*qsteps));
   CK_LAUNCH("quad_steps_kernel(write)");
   return total;

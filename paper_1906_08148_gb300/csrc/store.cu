@@ -53,13 +53,17 @@ __device__ __forceinline__ void warp_leaf_sumsq(Get get, int bs, int lane, doubl
   *bad_out = __any_sync(0xffffffffu, bad);
 }
 
+// Block b takes leaves [64 b, 64 b + 64), each of its 8 warps every 8th of
+// them (a grid of about nleaves / 64 blocks spreads evenly over the SMs;
+// larger grids stride by whole blocks).
+constexpr int64_t kNormLeavesPerBlock = 64;
 __global__ void leaf_sqnorm_kernel(const double* __restrict__ pool, const int64_t* __restrict__ slot, int64_t m,
                                    int bs, double* __restrict__ sq, uint8_t* __restrict__ nonzero, int check_finite,
                                    int* err) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwb = blockDim.x >> 5;
   const int64_t e = (int64_t)bs * bs;
-  for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < m; q += nw) {
+  for (int64_t q0 = (int64_t)blockIdx.x * kNormLeavesPerBlock; q0 < m; q0 += (int64_t)gridDim.x * kNormLeavesPerBlock)
+  for (int64_t q = q0 + warp; q < q0 + kNormLeavesPerBlock && q < m; q += nwb) {
     const double2* src = reinterpret_cast<const double2*>(pool + (slot ? slot[q] : q) * e);
     double s;
     bool nz, bad;
@@ -75,7 +79,8 @@ __global__ void leaf_sqnorm_kernel(const double* __restrict__ pool, const int64_
 void leaf_sqnorms(spamm_ctx ctx, const double* pool, const int64_t* slot, int64_t nleaves, int bs, double* sq,
                   uint8_t* nonzero, int check_finite) {
   if (nleaves <= 0) return;
-  leaf_sqnorm_kernel<<<grid_for(ctx, nleaves, kThreads / 32), kThreads, 0, ctx->stream>>>(
+  const int64_t nblk = (nleaves + kNormLeavesPerBlock - 1) / kNormLeavesPerBlock;
+  leaf_sqnorm_kernel<<<(unsigned)(nblk < (1ll << 30) ? nblk : (1ll << 30)), kThreads, 0, ctx->stream>>>(
       pool, slot, nleaves, bs, sq, nonzero, check_finite, ctx->d_err);
   CK_LAUNCH("leaf_sqnorm_kernel");
 }
@@ -334,6 +339,7 @@ __global__ void block_keep_kernel(const double* __restrict__ sq, int64_t n, doub
 spamm_mat truncate_block(spamm_mat in, double tau, spamm_ctx on) {
   spamm_ctx ctx = on ? on : in->ctx;
   spamm_mat out = new_mat(ctx, in->n, in->bs);
+  out->symmetric = in->symmetric;
   out->pool = in->pool;
   const int64_t n = in->nleaves;
   BufP keep = alloc_n<uint8_t>(ctx, n);
@@ -382,6 +388,7 @@ __global__ void drop_prefix_kernel(const int64_t* __restrict__ idx, int64_t n, c
 spamm_mat truncate_error_controlled(spamm_mat in, double tau, spamm_ctx on) {
   spamm_ctx ctx = on ? on : in->ctx;
   spamm_mat out = new_mat(ctx, in->n, in->bs);
+  out->symmetric = in->symmetric;
   out->pool = in->pool;
   const int64_t n = in->nleaves;
   BufP keep = alloc_n<uint8_t>(ctx, n);
@@ -426,6 +433,7 @@ spamm_mat truncate_element(spamm_mat in, double tau) {
   spamm_ctx ctx = in->ctx;
   const int64_t n = in->nleaves, e = (int64_t)in->bs * in->bs;
   spamm_mat out = new_mat(ctx, in->n, in->bs);
+  out->symmetric = in->symmetric;
   out->pool = alloc_n<double>(ctx, n * e);
   BufP sq = alloc_n<double>(ctx, n), nz = alloc_n<uint8_t>(ctx, n);
   if (n > 0) {
@@ -675,7 +683,9 @@ spamm_mat build_generated(spamm_ctx ctx, const spamm_gen_params* gp, int bs, dou
   el.p.cutoff = gp->cutoff;
   el.p.seed = gp->seed;
   el.bs = bs;
-  return build_from_elements(ctx, gp->n, bs, el, tau, rule);
+  spamm_mat m = build_from_elements(ctx, gp->n, bs, el, tau, rule);
+  m->symmetric = 1;  // u_ij and the decay law are symmetric in (i, j)
+  return m;
 }
 
 // COO: sort (leaf code, in-leaf offset) keys stably, sum runs of equal keys

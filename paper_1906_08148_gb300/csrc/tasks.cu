@@ -52,9 +52,15 @@ __global__ void child_norms_kernel(int64_t n, const int4* __restrict__ child, co
 }
 
 // mask bit (2*c + ck) for child group c = 2*ci + cj and child k-index ck;
-// na / nb: the children's norms of the pair's A and B nodes.
+// na / nb: the children's norms of the pair's A and B nodes.  The product is
+// the FP64 round-to-nearest product of the two norms; the comparisons use its
+// bits (non-negative doubles order like their bit patterns), because this part
+// issues FP64 instructions at two per clock per SM.  The borderline test
+// |prod - tau| <= 1e-12 tau is evaluated in FP64 only for products within
+// 2^14 units in the last place of tau (1e-12 relative is about 4500 of them).
 __device__ __forceinline__ unsigned child_mask(const int4& ca, const int4& cb, const double4& na, const double4& nb,
                                                double tau, int test, bool leaf, long long* cand, long long* border) {
+  const long long tb = __double_as_longlong(tau);
   unsigned m = 0;
 #pragma unroll
   for (int ci = 0; ci < 2; ++ci)
@@ -68,8 +74,10 @@ __device__ __forceinline__ unsigned child_mask(const int4& ca, const int4& cb, c
         bool keep = true;
         if (test) {
           const double prod = __dmul_rn(comp4d(na, 2 * ci + ck), comp4d(nb, 2 * ck + cj));
-          keep = prod >= tau;
-          if (leaf && fabs(prod - tau) <= 1e-12 * tau) ++*border;
+          const long long pb = __double_as_longlong(prod);
+          keep = pb >= tb;  // prod >= tau for prod, tau >= 0
+          const long long dist = pb > tb ? pb - tb : tb - pb;
+          if (leaf && dist <= (1ll << 14) && fabs(prod - tau) <= 1e-12 * tau) ++*border;
         }
         if (keep) m |= 1u << (2 * (2 * ci + cj) + ck);
       }

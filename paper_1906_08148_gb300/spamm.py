@@ -37,6 +37,7 @@ ENTRY_POINTS = (
     "spamm_to_blocks", "spamm_gather_leaves", "spamm_level_norms", "spamm_leaf_sqnorms_noalloc",
     "spamm_plan_create", "spamm_plan_info", "spamm_execute", "spamm_plan_release", "spamm_set_gemm_sms",
     "spamm_set_exec_graph", "spamm_add", "spamm_identity", "spamm_trace", "spamm_check_timeout_path", "spamm_trim",
+    "spamm_set_symmetric",
 )
 NOALLOC_MAX_LEAVES = 1 << 24
 
@@ -60,7 +61,7 @@ class Stats(ctypes.Structure):
                 ("bs", ctypes.c_int32), ("kept_flops", ctypes.c_double), ("ms_truncate", ctypes.c_double),
                 ("ms_tasks", ctypes.c_double), ("ms_gemm", ctypes.c_double), ("ms_cnorm", ctypes.c_double),
                 ("n_launches", ctypes.c_int64), ("ms_prep", ctypes.c_double), ("n_steps", ctypes.c_int64),
-                ("executed_flops", ctypes.c_double)]
+                ("executed_flops", ctypes.c_double), ("terms_shared", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         L = self.levels
@@ -69,7 +70,8 @@ class Stats(ctypes.Structure):
                 "n_a_leaves": self.n_a_leaves, "n_b_leaves": self.n_b_leaves, "levels": L, "bs": self.bs,
                 "kept_flops": self.kept_flops, "ms_truncate": self.ms_truncate, "ms_tasks": self.ms_tasks,
                 "ms_gemm": self.ms_gemm, "ms_cnorm": self.ms_cnorm, "n_launches": self.n_launches,
-                "ms_prep": self.ms_prep, "n_steps": self.n_steps, "executed_flops": self.executed_flops}
+                "ms_prep": self.ms_prep, "n_steps": self.n_steps, "executed_flops": self.executed_flops,
+                "terms_shared": self.terms_shared}
 
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -109,6 +111,7 @@ def load(path: str = LIB_PATH):
         "spamm_frob_norm": [vp, vp, pf64],
         "spamm_error": [vp, vp, vp, pf64],
         "spamm_mat_info": [vp, pi64, pi32, pi32, pi64],
+        "spamm_set_symmetric": [vp, ctypes.c_int],
         "spamm_to_dense": [vp, vp, vp, i64, ctypes.c_int],
         "spamm_to_blocks": [vp, vp, vp, vp, vp, vp, i64, ctypes.c_int],
         "spamm_level_norms": [vp, vp, ctypes.c_int, vp, vp, i64, pi64],
@@ -196,6 +199,10 @@ class Matrix:
         _check(self.ctx.handle, load().spamm_mat_info(self.handle, ctypes.byref(n), ctypes.byref(bs),
                                                       ctypes.byref(L), ctypes.byref(m)))
         return {"n": n.value, "bs": bs.value, "levels": L.value, "nleaves": m.value}
+
+    def set_symmetric(self, symmetric: bool = True):
+        """spamm_set_symmetric: mark (or unmark) the matrix as equal to its transpose."""
+        _check(self.ctx.handle, load().spamm_set_symmetric(self.handle, int(bool(symmetric))))
 
     def close(self):
         if self.handle:

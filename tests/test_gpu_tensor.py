@@ -193,3 +193,38 @@ def test_tensor_error_below_truncation_error_16384(S, ctx, prec, taus):
         print(f"{prec} n={n} tau={tau}: arithmetic error {arith:.3e} vs truncation error {trunc:.3e}")
         assert arith < trunc
         C.close()
+
+
+@pytest.mark.parametrize("prec", TC)
+def test_symmetric_square_shares_terms(S, ctx, prec):
+    """X times X for a symmetric X (the squarings of a purification chain):
+    one set of operand terms serves both roles (B's leaf (k, j) uses the
+    terms of leaf (j, k)); the output is bit-identical to building the B
+    terms separately, and the plan holds fewer bytes.  A leaf set without
+    every transpose falls back to separate terms."""
+    p = synth.lattice_3d(4096, alpha=0.9, seed=4)
+    X = S.spamm_generate(ctx, p, 64)
+    tau = 1e-6
+    shared, st1 = S.spamm_multiply(ctx, X, X, tau, "combined", prec, stats=True)
+    pl1 = S.spamm_plan_create(ctx, X, X, tau, "combined", prec)
+    X.set_symmetric(False)
+    plain, st0 = S.spamm_multiply(ctx, X, X, tau, "combined", prec, stats=True)
+    pl0 = S.spamm_plan_create(ctx, X, X, tau, "combined", prec)
+    assert st1["terms_shared"] == 1 and st0["terms_shared"] == 0
+    assert pl1.info()["plan_bytes"] < pl0.info()["plan_bytes"]
+    a, b = S.spamm_to_blocks(ctx, shared), S.spamm_to_blocks(ctx, plain)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+    # the mark on a leaf set that lacks a transpose: separate terms, the product A A
+    rng = np.random.default_rng(9)
+    D = np.zeros((256, 256))
+    D[:64, :64] = rng.uniform(-1, 1, (64, 64))
+    D[64:128, :64] = rng.uniform(-1, 1, (64, 64))  # leaf (1, 0) without (0, 1)
+    G = S.spamm_from_dense(ctx, D, 64)
+    G.set_symmetric(True)
+    C, st = S.spamm_multiply(ctx, G, G, 0.0, "spamm", prec, stats=True)
+    assert st["terms_shared"] == 0
+    M = oracle.from_dense(D, 64)
+    ref, ikj = oracle.multiply(M, M, 0.0, oracle.SPAMM)
+    bnd = oracle.to_dense(oracle.LeafMatrix(256, 64, ref.bi, ref.bj, tcbound.bound(prec, M, M, ikj, ref)))
+    assert np.all(np.abs(S.spamm_to_dense(ctx, C) - D @ D) <= bnd)
