@@ -39,6 +39,9 @@ FP64_PEAK_GFLOPS = 1258.6  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (DFMA 
 CONFIGS = {
     "lattice65536": dict(n=65536, kind=1, alpha=1.0, bs=64, seeds=(1, 2),
                          desc="3-D lattice 64x32x32 Morton, alpha=1.0, A!=B seeds 1,2, 64x64 leaves"),
+    "lattice262144": dict(n=262144, kind=1, alpha=0.8, bs=64, seeds=(1, 1),
+                          desc="3-D lattice 64x64x64 Morton, alpha=0.8, X times X (A = B, seed 1), 64x64 leaves, "
+                               "inputs truncated while generated (precision-form configuration)"),
     "lattice16384": dict(n=16384, kind=1, alpha=1.0, bs=64, seeds=(1, 2),
                          desc="3-D lattice 32x32x16 Morton, alpha=1.0, A!=B seeds 1,2, 64x64 leaves (profiling size)"),
     "model2048": dict(n=2048, kind=0, alpha=0.05, bs=32, seeds=(1, 1),
@@ -54,9 +57,19 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="lattice65536", choices=sorted(CONFIGS))
     ap.add_argument("--mode", default="combined", choices=["truncate", "spamm", "combined"])
-    ap.add_argument("--tau", type=float, default=1e-6)
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "bf16_split", "bf16_split4", "fp16_scaled", "auto"],
-                    help="auto: the autotuner's choice per request (served stream only)")
+    ap.add_argument("--tau", type=float, default=None,
+                    help="default: chosen for --sigma from the accuracy table (equal-accuracy headline), else 1e-6")
+    ap.add_argument("--prec", default=None, choices=["fp64", "bf16_split", "bf16_split4", "fp16_scaled", "auto"],
+                    help="default: the fastest form whose arithmetic error stays below the truncation error "
+                         "(equal-accuracy headline), else fp64; auto: the autotuner's choice per request "
+                         "(served stream only)")
+    ap.add_argument("--sigma", type=float, default=1e-4,
+                    help="target ||AB - C||_F of the equal-accuracy headline")
+    ap.add_argument("--pc-taus", type=float, nargs="+", default=[1e-5, 1e-7],
+                    help="taus of the precision-form configuration (--config lattice262144)")
+    ap.add_argument("--pc-samples", type=int, default=256,
+                    help="output leaves compared between each form and FP64 (precision-form configuration)")
+    ap.add_argument("--pc-no-fp64", action="store_true", help="precision-form configuration without the FP64 runs")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -67,7 +80,8 @@ def parse_args():
     ap.add_argument("--serve-nmax", type=int, default=32768)
     ap.add_argument("--serve-batch", type=int, default=32)
     ap.add_argument("--serve-alpha", type=float, nargs=2, default=[0.8, 1.2])
-    ap.add_argument("--serve-graph", action="store_true", help="execute each batch as a captured CUDA graph")
+    ap.add_argument("--serve-slice-ms", type=float, default=25.0,
+                    help="target duration of one launch of the served stream (continuous batching slices)")
     ap.add_argument("--no-forms", action="store_true", help="skip the tensor-form comparison in the bench line")
     ap.add_argument("--form-steps", type=int, default=5)
     ap.add_argument("--model-problem", action="store_true", help="the paper's 1-D model problem sweep")
@@ -100,6 +114,89 @@ def parse_args():
     ap.add_argument("--mp-tau-lo", type=int, default=4, help="largest tau = 10^-lo")
     ap.add_argument("--mp-tau-hi", type=int, default=12, help="smallest tau = 10^-hi")
     return ap.parse_args()
+
+
+# ----------------------------------------------------- equal-accuracy choice
+ACCURACY = os.path.join(ROOT, "tests", "golden", "accuracy.json")
+TC_FORMS = ("fp16_scaled", "bf16_split", "bf16_split4")
+
+
+def accuracy_entry(workload, mode, tau):
+    """The oracle's sampled ||AB - C||_F (estimate and 95 % interval) for a
+    workload, method and tau, from the committed table; None if absent."""
+    if not os.path.exists(ACCURACY):
+        return None
+    w = json.load(open(ACCURACY)).get("workloads", {}).get(workload)
+    if not w:
+        return None
+    return w["errors"].get("%s %g" % (mode, tau))
+
+
+def tau_for_sigma(workload, mode, sigma, taus=(1e-4, 1e-6, 1e-8)):
+    """Largest tau of the grid whose error (upper end of its interval) meets
+    sigma: the paper's rule for comparing methods at equal accuracy (Section
+    5.3)."""
+    for t in sorted(taus, reverse=True):
+        e = accuracy_entry(workload, mode, t)
+        if e is not None and e["high"] <= sigma:
+            return t
+    return None
+
+
+def resolve_defaults(args):
+    """No --prec, no --tau and no other mode on a workload the accuracy table
+    covers: the equal-accuracy headline (tau from --sigma, the form chosen on
+    the GPU).  Otherwise tau defaults to 1e-6 and the form to FP64."""
+    special = any((args.serve, args.sweep, args.model_problem, args.block_sparse, args.chain, args.sp2,
+                   args.passes))
+    args.headline = (not special and args.prec is None and args.tau is None
+                     and tau_for_sigma(args.config, args.mode, args.sigma) is not None)
+    if args.headline:
+        args.tau = tau_for_sigma(args.config, args.mode, args.sigma)
+    if args.tau is None:
+        args.tau = 1e-6
+    if args.prec is None and not args.headline:
+        args.prec = "fp64"
+
+
+def equal_accuracy_choice(S, ctx, GA, GB, args, stream, torch):
+    """At the tau chosen for sigma, the FP64 product and every tensor-core
+    form, each timed once with CUDA events (after an untimed run of the form):
+    a form is admissible if its arithmetic error ||C_form - C_fp64||_F stays
+    below the lower end of the method's truncation-error interval and the two
+    together stay within sigma.  The fastest admissible form is chosen (FP64
+    if none is)."""
+    trunc = accuracy_entry(args.config, args.mode, args.tau)
+
+    def timed(prec):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        C, st = S.spamm_multiply(ctx, GA, GB, args.tau, args.mode, prec, stats=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        return C, st, {"ms_per_step": ms, "kept_gflops": st["kept_flops"] / ms / 1e6,
+                       "mults_per_s": st["n_kept"] / ms * 1e3, "ms_gemm": st["ms_gemm"]}
+
+    ref, st_ref, fp64 = timed("fp64")
+    forms = {"fp64": dict(fp64, arith_error=0.0, admissible=trunc["high"] <= args.sigma)}
+    for prec in TC_FORMS:
+        S.spamm_multiply(ctx, GA, GB, args.tau, args.mode, prec).close()
+        C, st, rec = timed(prec)
+        arith = S.spamm_error(ctx, ref, C)
+        C.close()
+        rec.update(arith_error=arith, admissible=bool(arith <= trunc["low"] and trunc["high"] + arith <= args.sigma))
+        forms[prec] = rec
+    ref.close()
+    ok = [p for p in TC_FORMS if forms[p]["admissible"]]
+    chosen = min(ok, key=lambda p: forms[p]["ms_per_step"]) if ok else "fp64"
+    return chosen, {"sigma": args.sigma, "tau": args.tau, "method": args.mode, "truncation_error": trunc,
+                    "forms": forms, "chosen": chosen,
+                    "rule": "largest tau of {1e-4, 1e-6, 1e-8} whose sampled ||AB - C||_F (95 % upper end) meets "
+                            "sigma; a tensor form is admissible if ||C_form - C_fp64||_F is below the lower end "
+                            "of that error's interval and the two add up to at most sigma; the fastest admissible "
+                            "form is timed"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -278,7 +375,7 @@ def run_served(args):
         return reqs
 
     def serve(reqs):
-        srv = Server(max_batch=args.serve_batch, exec_sms=144, graph=args.serve_graph)
+        srv = Server(max_batch=args.serve_batch, exec_sms=144, slice_ms=args.serve_slice_ms)
         srv.start()
         ids = [srv.submit(r) for r in reqs]
         for i in ids:
@@ -301,7 +398,7 @@ def run_served(args):
             "config": {"workload": "served_stream", "requests": args.serve_requests, "inputs": args.serve_inputs,
                        "n_range": [4096, args.serve_nmax], "alpha": list(args.serve_alpha), "tau": taus,
                        "method": "combined", "forms": forms, "arrivals": "Poisson at 0.9 x saturated capacity",
-                       "exec_graph": bool(args.serve_graph)},
+                       "slice_ms": args.serve_slice_ms},
             "saturated": sat, "loaded": load, "p50_s": load["p50_s"], "p99_s": load["p99_s"],
             "kept_gflops": load["kept_gflops"]}
     print(json.dumps(line), flush=True)
@@ -621,6 +718,7 @@ def aggregate_ranks(ms_local, flops_local, kept_local, dist=None):
 def main():
     args = parse_args()
     cfg = CONFIGS[args.config]
+    resolve_defaults(args)
     if args.impl == "reference":
         return run_reference(args, cfg)
     if args.serve:
@@ -639,6 +737,8 @@ def main():
         return run_sp2(args)
     if args.passes:
         return run_passes(args, cfg)
+    if args.config == "lattice262144":
+        return run_precision_config(args, cfg)
 
     import numpy as np
     import torch
@@ -669,6 +769,9 @@ def main():
     bs = cfg["bs"]
     GA = S.spamm_generate(ctx, pa, bs)
     GB = GA if pb == pa else S.spamm_generate(ctx, pb, bs)
+    choice = None
+    if args.headline:
+        args.prec, choice = equal_accuracy_choice(S, ctx, GA, GB, args, stream, torch)
 
     def step():
         C, st = S.spamm_multiply(ctx, GA, GB, args.tau, args.mode, args.prec, stats=True)
@@ -729,7 +832,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.prec == "fp64" else args.prec, "data": "synthetic",
             "config": {"workload": args.config, "desc": cfg["desc"], "n": cfg["n"], "bs": bs, "method": args.mode,
-                       "tau": args.tau, "precision": args.prec, "l2": ("inputs (%.1f GB of leaves) larger than L2" % in_gb) if flush is None
+                       "tau": args.tau, "precision": args.prec,
+                       "sigma": args.sigma if args.headline else None, "l2": ("inputs (%.1f GB of leaves) larger than L2" % in_gb) if flush is None
                        else "L2 flushed before every step (256 MB write, outside the step's events)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "mults_per_s": mults,
@@ -737,7 +841,13 @@ def main():
             "n_a_leaves": stats[-1]["n_a_leaves"], "n_b_leaves": stats[-1]["n_b_leaves"],
             "c_frob": nrm, "phase_ms": phases, "latency": latency, "roofline": roof,
             "gpu_launches": None, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "precision_forms": forms,
+            "equal_accuracy": choice,
         }
+        if choice is not None:
+            fp = choice["forms"]["fp64"]
+            choice["vs_fp64"] = {"kept_gflops": value / fp["kept_gflops"],
+                                 "mults_per_s": mults / fp["mults_per_s"],
+                                 "note": "this line's timed steps against one timed FP64 step at the same tau"}
         line["gpu_launches"] = int(sum(s["n_launches"] for s in stats))
         if forms:
             for f in forms.values():
@@ -747,6 +857,133 @@ def main():
         m.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_precision_config(args, cfg):
+    """The precision-form configuration: X times X for the 64^3 lattice
+    (n = 262144, alpha = 0.8, X symmetric, 64 x 64 leaves), combined, at each
+    tau of --pc-taus.  X is generated with the block rule applied while
+    generating (the same leaves as truncating the full matrix, which would not
+    fit).  Each tensor form: plan (one set of operand terms for both roles,
+    X being symmetric), release X, execute: --warmup untimed and --steps timed
+    executions (CUDA events), output leaves sampled for the comparison with
+    FP64; the FP64 form then runs the same multiply once (timed), where it
+    fits.  A step is the plan's phases (truncation, task list, operand terms,
+    device-timed by the library) plus one execution.  A form is admissible at tau if its error against FP64 on the
+    sampled leaves, scaled to the whole output, stays below the lower end of
+    the oracle's sampled truncation error (tests/golden/accuracy.json).  The
+    line's value is the fastest admissible form at the smallest tau."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_1906_08148_gb300 import spamm as S
+
+    stream = torch.cuda.current_stream()
+    ctx = S.Context(0, stream=stream)
+    p = synth.DecayParams(n=cfg["n"], kind=cfg["kind"], alpha=cfg["alpha"], seed=cfg["seeds"][0])
+    bs, nb = cfg["bs"], cfg["n"] // cfg["bs"]
+    rng = np.random.default_rng(3)
+    # sampled output leaves: the diagonal band and scattered positions near it
+    ii = rng.integers(0, nb, args.pc_samples)
+    jj = np.clip(ii + rng.integers(-40, 41, args.pc_samples), 0, nb - 1)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    per_tau = {}
+    with ClockSampler(0) as clk:
+        for tau in args.pc_taus:
+            trunc = accuracy_entry("lattice262144_square", "combined", tau)
+            rec = {"truncation_error": trunc, "forms": {}}
+            samples = {}
+            for prec in TC_FORMS + (() if args.pc_no_fp64 else ("fp64",)):
+                X = S.spamm_generate(ctx, p, bs, tau)
+                nx = X.info()["nleaves"]
+                try:
+                    plan = S.spamm_plan_create(ctx, X, X, tau, "combined", prec)
+                except S.SpammError as e:
+                    X.close()
+                    rec["forms"][prec] = {"admission": "refused: %s" % e}
+                    continue
+                if prec != "fp64":
+                    X.close()  # the plan keeps the operand terms only
+                info = plan.info()
+                out = {"x_leaves": nx, "plan_gb": info["plan_bytes"] / 1e9, "exec_gb": info["exec_bytes"] / 1e9}
+                try:
+                    steps = 1 if prec == "fp64" else args.steps
+                    for _ in range(0 if prec == "fp64" else args.warmup):
+                        (C,) = S.spamm_execute(ctx, [plan])
+                        C.close()
+                    ms, st = [], None
+                    for _ in range(steps):
+                        e0, e1 = ev(), ev()
+                        e0.record(stream)
+                        (C,), (st,) = S.spamm_execute(ctx, [plan], stats=True)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        ms.append(e0.elapsed_time(e1))
+                        last = C
+                        if len(ms) < steps:
+                            C.close()
+                    samples[prec], found = S.spamm_gather_leaves(ctx, last, ii, jj)
+                    samples[prec] = np.where(found[:, None, None], samples[prec], 0.0)
+                    cn = S.spamm_frob_norm(ctx, last)
+                    last.close()
+                except S.SpammError as e:
+                    out["admission"] = "refused at execution: %s" % e
+                    rec["forms"][prec] = out
+                    plan.close()
+                    if prec == "fp64":
+                        X.close()
+                    continue
+                plan.close()
+                if prec == "fp64":
+                    X.close()
+                # a step: the plan's phases (truncation, task list, operand terms; device-timed by the
+                # library when the plan was made) plus one execution (CUDA events)
+                msx = st["ms_truncate"] + st["ms_tasks"] + st["ms_prep"] + statistics.median(ms)
+                out.update({"admission": "ran", "ms_per_step": msx, "ms_execute": statistics.median(ms),
+                            "ms_gemm": st["ms_gemm"], "ms_truncate": st["ms_truncate"],
+                            "ms_prep": st["ms_prep"], "ms_tasks": st["ms_tasks"], "n_kept": st["n_kept"],
+                            "n_steps": st["n_steps"], "n_c_leaves": st["n_c_leaves"],
+                            "terms_shared": st["terms_shared"], "c_frob": cn,
+                            "kept_gflops": st["kept_flops"] / msx / 1e6, "mults_per_s": st["n_kept"] / msx * 1e3,
+                            "roofline": roofline(prec, bs, st["n_kept"], st["ms_gemm"], st["executed_flops"])})
+                rec["forms"][prec] = out
+            ref = samples.get("fp64")
+            for prec, f in rec["forms"].items():
+                if prec == "fp64" or prec not in samples or ref is None:
+                    continue
+                num = float(np.sqrt(np.sum((samples[prec] - ref) ** 2)))
+                den = float(np.sqrt(np.sum(ref ** 2)))
+                rel = num / den if den > 0 else 0.0
+                arith = rel * rec["forms"]["fp64"]["c_frob"]
+                f["arith_rel_sampled"] = rel
+                f["arith_error_est"] = arith
+                f["admissible"] = bool(trunc is not None and arith <= trunc["low"])
+            per_tau["%g" % tau] = rec
+    tau0 = "%g" % min(args.pc_taus)
+    forms0 = per_tau[tau0]["forms"]
+    ok = [k for k, f in forms0.items() if k != "fp64" and f.get("admissible")]
+    chosen = min(ok, key=lambda k: forms0[k]["ms_per_step"]) if ok else (
+        "fp64" if forms0.get("fp64", {}).get("admission") == "ran" else None)
+    ch = forms0.get(chosen, {}) if chosen else {}
+    fp = forms0.get("fp64", {})
+    cpu = None if args.no_cpu else cpu_baseline(cfg, "combined", min(args.pc_taus), args.cpu_seconds)
+    line = {"metric": "kept-block GFLOP/s", "value": ch.get("kept_gflops"), "unit": "GFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ch.get("ms_per_step"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if chosen == "fp64" else chosen, "data": "synthetic",
+            "config": {"workload": "lattice262144", "desc": cfg["desc"], "n": cfg["n"], "bs": bs,
+                       "method": "combined", "tau": min(args.pc_taus), "precision": chosen,
+                       "l2": "inputs far larger than L2", "parallelism": "single"},
+            "mults_per_s": ch.get("mults_per_s"), "roofline": ch.get("roofline"),
+            "vs_fp64": ({"kept_gflops": ch["kept_gflops"] / fp["kept_gflops"]}
+                        if chosen and chosen != "fp64" and fp.get("admission") == "ran" else None),
+            "per_tau": per_tau, "clocks": clk.summary(), "cpu_baseline": cpu,
+            "e2e": None, "e2e_note": "not run for this configuration (host staging of 100-250 GB per step)",
+            "gpu_launches": None}
+    print(json.dumps(line), flush=True)
 
 
 def precision_forms(S, ctx, GA, GB, args, stream, torch):

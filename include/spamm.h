@@ -291,6 +291,48 @@ SPAMM_API spamm_status spamm_execute(spamm_ctx ctx, int64_t nplans, const spamm_
 
 SPAMM_API spamm_status spamm_plan_release(spamm_plan p);
 
+/* ---------------------------------------- sliced execution (continuous batching) */
+
+typedef struct spamm_job_s* spamm_job;
+
+/* The execute phase of a plan, cut into slices that later requests can join:
+ * spamm_job_begin allocates the plan's output (spamm_plan_info's exec_bytes)
+ * and returns a job whose work units -- output leaves (their 64 x 64
+ * sub-tiles for bs 128 and 256) in the FP64 form, quads of output leaves in
+ * the tensor forms -- run in later spamm_run calls, in the plan's claiming
+ * order.  Each output leaf is computed whole by one unit, with its products
+ * in ascending k, so the result does not depend on how the units were cut
+ * into launches: it is bit-identical to spamm_execute of the same plan.  The
+ * plan must outlive the job.  Errors: INVALID_ARG, OOM, CUDA. */
+SPAMM_API spamm_status spamm_job_begin(spamm_ctx ctx, spamm_plan plan, spamm_job* out);
+
+/* Units of the job, how many have run, and the same as work: kept leaf
+ * products (FP64) or quad steps (tensor forms).  Any pointer may be NULL. */
+SPAMM_API spamm_status spamm_job_info(spamm_job job, int64_t* units, int64_t* units_done, double* work,
+                                      double* work_done);
+
+/* ONE persistent leaf-product launch over the next units of `njobs` jobs (one
+ * precision form and leaf size, on this device): job r contributes the
+ * following units whose work adds up to at most work_budget[r] (at least one
+ * unit, one whole leaf in the FP64 form, at most what is left; a finished job
+ * contributes nothing).  Returns once the launch has completed; units_run[r]
+ * (may be NULL) receives the units job r ran, *ms_gemm (may be NULL) the
+ * launch's device time.  A server calls this in a loop, adding new jobs
+ * between calls, so requests that arrive while others run share the next
+ * launches with them.  Errors: INVALID_ARG (mixed forms, sizes or devices),
+ * CUDA, TIMEOUT. */
+SPAMM_API spamm_status spamm_run(spamm_ctx ctx, int64_t njobs, const spamm_job* jobs, const double* work_budget,
+                                 int64_t* units_run, double* ms_gemm);
+
+/* Once every unit of the job has run: the output's leaf slots and quadtree
+ * norms (kernel (d)); *C receives the product.  `stats` (may be NULL) is
+ * filled as spamm_execute fills it, ms_gemm summing the launches the job took
+ * part in.  Errors: BUSY (units left), INVALID_ARG (already finished), CUDA. */
+SPAMM_API spamm_status spamm_job_finish(spamm_ctx ctx, spamm_job job, spamm_mat* C, spamm_stats* stats);
+
+/* Releases a job; an unfinished job's output is freed with it. */
+SPAMM_API spamm_status spamm_job_release(spamm_job job);
+
 /* Run the persistent leaf-product launches of `ctx` on at most `nsms` SMs
  * (0 = all), leaving the others to kernels on other streams, e.g. planning
  * the next requests while a batch executes. */

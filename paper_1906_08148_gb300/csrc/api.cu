@@ -1,4 +1,5 @@
 // api.cu -- the extern "C" entry points of libspamm (declared in spamm.h).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -428,6 +429,84 @@ void fill_stats(const spamm_plan_s& p, spamm_stats* st) {
   st->ms_prep = p.ms_prep;
 }
 
+// The output of one plan (its leaves, slots, norms and quadtree levels, the
+// FP64 sub-tile partial norms) and the device view of the plan over all its
+// work units: output leaves (or their 64 x 64 sub-tiles) for the FP64 kernel,
+// quads of output leaves for the tensor-core kernel.
+struct PlanOut {
+  std::unique_ptr<spamm_mat_s> C;
+  BufP part;
+  PlanDev dev{};
+  int64_t units = 0;
+};
+
+PlanOut make_output(spamm_ctx ctx, const spamm_plan_s& p) {
+  PlanOut o;
+  const int bs = p.bs;
+  const int64_t e = (int64_t)bs * bs;
+  o.C.reset(new_mat(ctx, p.n, bs));
+  spamm_mat Cm = o.C.get();
+  Cm->lv = p.cskel;
+  Cm->nleaves = p.T.ngroups;
+  Cm->pool = alloc_n<double>(ctx, p.T.ngroups * e);
+  Cm->slot = alloc_n<int64_t>(ctx, p.T.ngroups);
+  Cm->lv[Cm->L].sq = alloc_n<double>(ctx, p.T.ngroups);
+  alloc_level_norms(Cm);
+  PlanDev& d = o.dev;
+  d.gstart = P<int64_t>(p.T.gstart);
+  d.ta = P<int32_t>(p.T.ta);
+  d.tb = P<int32_t>(p.T.tb);
+  d.quads = P<int32_t>(p.T.quads);
+  d.poolA = P<double>(p.poolA);
+  d.slotA = P<int64_t>(p.slotA);
+  d.poolB = P<double>(p.poolB);
+  d.slotB = P<int64_t>(p.slotB);
+  d.termsA = P<uint8_t>(p.termsA);
+  d.termsB = P<uint8_t>(p.termsB);
+  d.qstart = P<int64_t>(p.qstart);
+  d.qsteps = P<QuadStep>(p.qsteps);
+  d.cpool = P<double>(Cm->pool);
+  d.csq = P<double>(Cm->lv[Cm->L].sq);
+  d.uorder = P<int64_t>(p.uorder);
+  const int64_t per_leaf = p.prec == SPAMM_PREC_FP64 ? fp64_units_per_leaf(bs) : 1;
+  if (per_leaf > 1) {
+    o.part = alloc_n<double>(ctx, p.T.ngroups * per_leaf);
+    d.csq_part = P<double>(o.part);
+  }
+  o.units = p.T.ngroups == 0 ? 0 : (p.prec == SPAMM_PREC_FP64 ? p.T.ngroups * per_leaf : p.T.nquads);
+  return o;
+}
+
+// The plan's view from work unit `first` on (FP64: a whole number of leaves):
+// the kernels number the units of a launch from 0 within each plan, so a
+// slice is the same plan with its per-unit arrays advanced.
+PlanDev slice_view(const spamm_plan_s& p, const PlanDev& d, int64_t first) {
+  PlanDev v = d;
+  if (first == 0) return v;
+  if (p.prec == SPAMM_PREC_FP64) {
+    const int64_t leaf0 = first / fp64_units_per_leaf(p.bs);
+    if (v.uorder) {
+      v.uorder += leaf0;  // leaves in claiming order; outputs indexed by the leaf itself
+    } else {
+      v.gstart += leaf0;
+      v.cpool += leaf0 * (int64_t)p.bs * p.bs;
+      v.csq += leaf0;
+      if (v.csq_part) v.csq_part += leaf0 * fp64_units_per_leaf(p.bs);
+    }
+  } else {
+    v.qstart += first;  // quads; their output leaves are named in quads[] itself
+    v.quads += 4 * first;
+  }
+  return v;
+}
+
+void launch_gemm(spamm_ctx ctx, spamm_prec prec, int bs, const BatchDev& batch) {
+  if (prec == SPAMM_PREC_FP64)
+    gemm_fp64_batch(ctx, bs, batch);
+  else
+    gemm_tc_batch(ctx, prec, batch);
+}
+
 // One persistent launch over all plans, then every output's parent norms (one
 // launch per level for the whole batch).  Buffers are allocated and the plan
 // table uploaded first, so the launch sequence has no host synchronisation;
@@ -442,47 +521,15 @@ std::vector<spamm_mat> execute_plans(spamm_ctx ctx, const std::vector<spamm_plan
       fail(SPAMM_E_INVALID_ARG, "a batch needs one device, one precision form and one leaf size");
   Events ev;
   const unsigned long long launches0 = g_kernel_launches;
-  const int64_t e = (int64_t)bs * bs;
-  std::vector<std::unique_ptr<spamm_mat_s>> outs;
+  std::vector<PlanOut> pout;
   std::vector<spamm_mat> outp;
   std::vector<PlanDev> host(np);
   std::vector<int64_t> ubegin(np + 1, 0);
-  std::vector<BufP> parts;  // FP64 sub-tile partial norms, alive until the launches below are queued
   for (int64_t r = 0; r < np; ++r) {
-    const spamm_plan_s& p = *plans[r];
-    outs.emplace_back(new_mat(ctx, p.n, bs));
-    spamm_mat Cm = outs.back().get();
-    outp.push_back(Cm);
-    Cm->lv = p.cskel;
-    Cm->nleaves = p.T.ngroups;
-    Cm->pool = alloc_n<double>(ctx, p.T.ngroups * e);
-    Cm->slot = alloc_n<int64_t>(ctx, p.T.ngroups);
-    Cm->lv[Cm->L].sq = alloc_n<double>(ctx, p.T.ngroups);
-    alloc_level_norms(Cm);
-    PlanDev& d = host[r];
-    d.gstart = P<int64_t>(p.T.gstart);
-    d.ta = P<int32_t>(p.T.ta);
-    d.tb = P<int32_t>(p.T.tb);
-    d.quads = P<int32_t>(p.T.quads);
-    d.poolA = P<double>(p.poolA);
-    d.slotA = P<int64_t>(p.slotA);
-    d.poolB = P<double>(p.poolB);
-    d.slotB = P<int64_t>(p.slotB);
-    d.termsA = P<uint8_t>(p.termsA);
-    d.termsB = P<uint8_t>(p.termsB);
-    d.qstart = P<int64_t>(p.qstart);
-    d.qsteps = P<QuadStep>(p.qsteps);
-    d.cpool = P<double>(Cm->pool);
-    d.csq = P<double>(Cm->lv[Cm->L].sq);
-    d.uorder = P<int64_t>(p.uorder);
-    // work units: output leaves (or their sub-tiles) for the FP64 kernel, quads of output leaves for the tensor-core kernel
-    const int64_t per_leaf = prec == SPAMM_PREC_FP64 ? fp64_units_per_leaf(bs) : 1;
-    if (per_leaf > 1) {
-      parts.push_back(alloc_n<double>(ctx, p.T.ngroups * per_leaf));
-      d.csq_part = P<double>(parts.back());
-    }
-    const int64_t units = p.T.ngroups == 0 ? 0 : (prec == SPAMM_PREC_FP64 ? p.T.ngroups * per_leaf : p.T.nquads);
-    ubegin[r + 1] = ubegin[r] + units;
+    pout.push_back(make_output(ctx, *plans[r]));
+    outp.push_back(pout.back().C.get());
+    host[r] = pout.back().dev;
+    ubegin[r + 1] = ubegin[r] + pout.back().units;
   }
   BufP dplans = alloc_n<PlanDev>(ctx, np), dub = alloc_n<int64_t>(ctx, np + 1);
   CK(cudaMemcpyAsync(P<PlanDev>(dplans), host.data(), np * sizeof(PlanDev), cudaMemcpyHostToDevice, ctx->stream));
@@ -494,10 +541,7 @@ std::vector<spamm_mat> execute_plans(spamm_ctx ctx, const std::vector<spamm_plan
 
   auto sequence = [&](unsigned evflags) {
     CK(cudaEventRecordWithFlags(ev.e[0], ctx->stream, evflags));
-    if (prec == SPAMM_PREC_FP64)
-      gemm_fp64_batch(ctx, bs, batch);
-    else
-      gemm_tc_batch(ctx, prec, batch);
+    launch_gemm(ctx, prec, bs, batch);
     CK(cudaEventRecordWithFlags(ev.e[1], ctx->stream, evflags));
     for (int64_t r = 0; r < np; ++r) fill_iota_i64(ctx, P<int64_t>(outp[r]->slot), outp[r]->nleaves);
     propagate_norms_batch(ctx, nlv);
@@ -540,7 +584,7 @@ std::vector<spamm_mat> execute_plans(spamm_ctx ctx, const std::vector<spamm_plan
   *ms_cnorm = elapsed_ms(ev.e[1], ev.e[2]);
   *launches = (int64_t)(g_kernel_launches - launches0);
   std::vector<spamm_mat> res;
-  for (auto& o : outs) res.push_back(o.release());
+  for (auto& o : pout) res.push_back(o.C.release());
   return res;
 }
 
@@ -575,6 +619,170 @@ spamm_status spamm_plan_release(spamm_plan p) {
   spamm_ctx ctx = p->ctx;
   cudaSetDevice(ctx->device);
   delete p;
+  ctx->live_handles--;
+  return SPAMM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ sliced execution
+struct spamm_job_s {
+  spamm_ctx ctx = nullptr;
+  spamm_plan plan = nullptr;
+  PlanOut out;
+  int64_t done = 0;            // units run so far (a prefix of the claiming order)
+  int nq = 1;                  // units per output leaf (FP64 sub-tiles), slices hold whole leaves
+  std::vector<double> wpre;    // work of units [0, u): kept products (FP64) or quad steps
+  double ms_gemm = 0.0;        // launches this job took part in
+  int64_t launches = 0;
+};
+
+namespace {
+
+// Host copy of the work per unit in claiming order, as a prefix sum.
+void job_work_prefix(spamm_job j) {
+  const spamm_plan_s& p = *j->plan;
+  spamm_ctx ctx = j->ctx;
+  const int64_t u = j->out.units;
+  j->wpre.assign(u + 1, 0.0);
+  if (u == 0) return;
+  if (p.prec == SPAMM_PREC_FP64) {
+    const int64_t ng = p.T.ngroups;
+    std::vector<int64_t> gs(ng + 1), ord;
+    CK(cudaMemcpyAsync(gs.data(), P<int64_t>(p.T.gstart), (ng + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    if (p.uorder) {
+      ord.resize(ng);
+      CK(cudaMemcpyAsync(ord.data(), P<int64_t>(p.uorder), ng * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+    }
+    sync_and_check(ctx);
+    for (int64_t x = 0; x < u; ++x) {
+      const int64_t li = x / j->nq, g = ord.empty() ? li : ord[li];
+      j->wpre[x + 1] = j->wpre[x] + (double)(gs[g + 1] - gs[g]) / j->nq;
+    }
+  } else {
+    std::vector<int64_t> qs(u + 1);
+    CK(cudaMemcpyAsync(qs.data(), P<int64_t>(p.qstart), (u + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    sync_and_check(ctx);
+    for (int64_t x = 0; x < u; ++x) j->wpre[x + 1] = j->wpre[x] + (double)(qs[x + 1] - qs[x]);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+spamm_status spamm_job_begin(spamm_ctx ctx, spamm_plan plan, spamm_job* out) {
+  if (!ctx || !plan || !out) return SPAMM_E_INVALID_ARG;
+  *out = nullptr;
+  return guarded(ctx, [&] {
+    if (plan->ctx->device != ctx->device) fail(SPAMM_E_INVALID_ARG, "the plan lives on another device");
+    std::unique_ptr<spamm_job_s> j(new spamm_job_s());
+    j->ctx = ctx;
+    j->plan = plan;
+    j->nq = plan->prec == SPAMM_PREC_FP64 ? fp64_units_per_leaf(plan->bs) : 1;
+    j->out = make_output(ctx, *plan);
+    job_work_prefix(j.get());
+    ctx->live_handles++;
+    *out = j.release();
+  });
+}
+
+spamm_status spamm_job_info(spamm_job job, int64_t* units, int64_t* units_done, double* work, double* work_done) {
+  if (!job) return SPAMM_E_INVALID_ARG;
+  if (units) *units = job->out.units;
+  if (units_done) *units_done = job->done;
+  if (work) *work = job->wpre.back();
+  if (work_done) *work_done = job->wpre[job->done];
+  return SPAMM_OK;
+}
+
+spamm_status spamm_run(spamm_ctx ctx, int64_t njobs, const spamm_job* jobs, const double* work_budget,
+                       int64_t* units_run, double* ms_gemm) {
+  if (!ctx || njobs <= 0 || !jobs || !work_budget) return SPAMM_E_INVALID_ARG;
+  return guarded(ctx, [&] {
+    const spamm_prec prec = jobs[0] ? jobs[0]->plan->prec : SPAMM_PREC_FP64;
+    const int bs = jobs[0] ? jobs[0]->plan->bs : 0;
+    std::vector<PlanDev> host;
+    std::vector<int64_t> ubegin(1, 0), take(njobs, 0);
+    for (int64_t r = 0; r < njobs; ++r) {
+      spamm_job j = jobs[r];
+      need(j != nullptr, "NULL job");
+      if (j->plan->prec != prec || j->plan->bs != bs || j->ctx->device != ctx->device)
+        fail(SPAMM_E_INVALID_ARG, "one launch needs one device, one precision form and one leaf size");
+      const int64_t c = j->done, left = j->out.units - c;
+      if (left == 0) continue;
+      // the units from c on whose work fits the budget, at least one leaf's worth
+      const double lim = j->wpre[c] + (work_budget[r] > 0 ? work_budget[r] : 0.0);
+      int64_t n = (int64_t)(std::upper_bound(j->wpre.begin() + c + 1, j->wpre.end(), lim) - j->wpre.begin()) - 1 - c;
+      n = std::max<int64_t>(n, 1);
+      n = (n + j->nq - 1) / j->nq * j->nq;
+      n = std::min(n, left);
+      take[r] = n;
+      host.push_back(slice_view(*j->plan, j->out.dev, c));
+      ubegin.push_back(ubegin.back() + n);
+    }
+    double ms = 0.0;
+    if (!host.empty()) {
+      const int64_t np = (int64_t)host.size();
+      BufP dplans = alloc_n<PlanDev>(ctx, np), dub = alloc_n<int64_t>(ctx, np + 1);
+      CK(cudaMemcpyAsync(P<PlanDev>(dplans), host.data(), np * sizeof(PlanDev), cudaMemcpyHostToDevice,
+                         ctx->stream));
+      CK(cudaMemcpyAsync(P<int64_t>(dub), ubegin.data(), (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                         ctx->stream));
+      BatchDev batch{P<PlanDev>(dplans), P<int64_t>(dub), (int)np, ubegin.back()};
+      Events ev;
+      CK(cudaEventRecord(ev.e[0], ctx->stream));
+      launch_gemm(ctx, prec, bs, batch);
+      CK(cudaEventRecord(ev.e[1], ctx->stream));
+      sync_and_check(ctx);
+      ms = elapsed_ms(ev.e[0], ev.e[1]);
+    }
+    for (int64_t r = 0; r < njobs; ++r) {
+      jobs[r]->done += take[r];
+      if (take[r] > 0) {
+        jobs[r]->ms_gemm += ms;
+        jobs[r]->launches++;
+      }
+      if (units_run) units_run[r] = take[r];
+    }
+    if (ms_gemm) *ms_gemm = ms;
+  });
+}
+
+spamm_status spamm_job_finish(spamm_ctx ctx, spamm_job job, spamm_mat* C, spamm_stats* stats) {
+  if (!ctx || !job || !C) return SPAMM_E_INVALID_ARG;
+  *C = nullptr;
+  return guarded(ctx, [&] {
+    if (job->done != job->out.units) fail(SPAMM_E_BUSY, "the job has units that have not run");
+    if (!job->out.C) fail(SPAMM_E_INVALID_ARG, "the job was already finished");
+    spamm_mat Cm = job->out.C.get();
+    Events ev;
+    CK(cudaEventRecord(ev.e[0], ctx->stream));
+    fill_iota_i64(ctx, P<int64_t>(Cm->slot), Cm->nleaves);
+    std::vector<NormBatchLevel> nlv;
+    BufP ntab = norm_batch_tables(ctx, {Cm}, &nlv);
+    propagate_norms_batch(ctx, nlv);
+    CK(cudaEventRecord(ev.e[1], ctx->stream));
+    sync_and_check(ctx);
+    if (stats) {
+      fill_stats(*job->plan, stats);
+      stats->ms_gemm = job->ms_gemm;
+      stats->ms_cnorm = elapsed_ms(ev.e[0], ev.e[1]);
+      stats->n_launches = job->launches;
+    }
+    job->out.part.reset();
+    *C = registered(job->out.C.release());
+  });
+}
+
+spamm_status spamm_job_release(spamm_job job) {
+  if (!job) return SPAMM_E_INVALID_ARG;
+  spamm_ctx ctx = job->ctx;
+  cudaSetDevice(ctx->device);
+  delete job;
   ctx->live_handles--;
   return SPAMM_OK;
 }

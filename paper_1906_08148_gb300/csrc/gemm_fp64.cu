@@ -178,7 +178,8 @@ __global__ void leaf_norm_from_parts_kernel(BatchDev batch, int nq) {
     const int64_t u = x * nq;
     const int r = plan_of(batch.ubegin, batch.nplans, u);
     const PlanDev& pl = batch.plans[r];
-    const int64_t g = (u - batch.ubegin[r]) / nq;
+    const int64_t li = (u - batch.ubegin[r]) / nq;  // leaf position in claiming order
+    const int64_t g = pl.uorder ? pl.uorder[li] : li;
     double t = 0.0;
     for (int k = 0; k < nq; ++k) t += pl.csq_part[g * nq + k];
     pl.csq[g] = t;

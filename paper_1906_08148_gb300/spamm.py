@@ -37,7 +37,8 @@ ENTRY_POINTS = (
     "spamm_to_blocks", "spamm_gather_leaves", "spamm_level_norms", "spamm_leaf_sqnorms_noalloc",
     "spamm_plan_create", "spamm_plan_info", "spamm_execute", "spamm_plan_release", "spamm_set_gemm_sms",
     "spamm_set_exec_graph", "spamm_add", "spamm_identity", "spamm_trace", "spamm_check_timeout_path", "spamm_trim",
-    "spamm_set_symmetric",
+    "spamm_set_symmetric", "spamm_job_begin", "spamm_job_info", "spamm_run", "spamm_job_finish",
+    "spamm_job_release",
 )
 NOALLOC_MAX_LEAVES = 1 << 24
 
@@ -112,6 +113,11 @@ def load(path: str = LIB_PATH):
         "spamm_error": [vp, vp, vp, pf64],
         "spamm_mat_info": [vp, pi64, pi32, pi32, pi64],
         "spamm_set_symmetric": [vp, ctypes.c_int],
+        "spamm_job_begin": [vp, vp, ctypes.POINTER(vp)],
+        "spamm_job_info": [vp, pi64, pi64, pf64, pf64],
+        "spamm_run": [vp, i64, ctypes.POINTER(vp), pf64, pi64, pf64],
+        "spamm_job_finish": [vp, vp, ctypes.POINTER(vp), ctypes.POINTER(Stats)],
+        "spamm_job_release": [vp],
         "spamm_to_dense": [vp, vp, vp, i64, ctypes.c_int],
         "spamm_to_blocks": [vp, vp, vp, vp, vp, vp, i64, ctypes.c_int],
         "spamm_level_norms": [vp, vp, ctypes.c_int, vp, vp, i64, pi64],
@@ -470,6 +476,59 @@ def spamm_execute(ctx: Context, plans, stats: bool = False):
     _check(ctx.handle, load().spamm_execute(ctx.handle, n, arr, outs, sts))
     Cs = [Matrix(ctx, ctypes.c_void_p(outs[i])) for i in range(n)]
     return (Cs, [s.as_dict() for s in sts]) if stats else Cs
+
+
+class Job:
+    """The execute phase of a plan in slices (spamm_job_begin): its units run in spamm_run calls."""
+
+    def __init__(self, ctx: Context, handle: ctypes.c_void_p, plan: "Plan"):
+        self.ctx = ctx
+        self.handle = handle
+        self.plan = plan  # the plan must outlive the job
+
+    def info(self) -> dict:
+        u, d, w, wd = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        _check(self.ctx.handle, load().spamm_job_info(self.handle, ctypes.byref(u), ctypes.byref(d),
+                                                      ctypes.byref(w), ctypes.byref(wd)))
+        return {"units": u.value, "units_done": d.value, "work": w.value, "work_done": wd.value}
+
+    def close(self):
+        if self.handle:
+            load().spamm_job_release(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spamm_job_begin(ctx: Context, plan: "Plan") -> Job:
+    out = ctypes.c_void_p()
+    _check(ctx.handle, load().spamm_job_begin(ctx.handle, plan.handle, ctypes.byref(out)))
+    return Job(ctx, out, plan)
+
+
+def spamm_run(ctx: Context, jobs, work_budget):
+    """One launch over the next units of every job (work_budget: one number or one per job);
+    returns (units run per job, ms of the launch)."""
+    n = len(jobs)
+    arr = (ctypes.c_void_p * n)(*[j.handle for j in jobs])
+    wb = [float(work_budget)] * n if np.isscalar(work_budget) else [float(w) for w in work_budget]
+    budget = (ctypes.c_double * n)(*wb)
+    ran = (ctypes.c_int64 * n)()
+    ms = ctypes.c_double()
+    _check(ctx.handle, load().spamm_run(ctx.handle, n, arr, budget, ran, ctypes.byref(ms)))
+    return [int(x) for x in ran], ms.value
+
+
+def spamm_job_finish(ctx: Context, job: Job, stats: bool = False):
+    out = ctypes.c_void_p()
+    st = Stats()
+    _check(ctx.handle, load().spamm_job_finish(ctx.handle, job.handle, ctypes.byref(out), ctypes.byref(st)))
+    C = Matrix(ctx, out)
+    return (C, st.as_dict()) if stats else C
 
 
 def spamm_set_gemm_sms(ctx: Context, nsms: int):

@@ -110,5 +110,13 @@ def test_every_mode_parses(monkeypatch, argv):
 def test_defaults_are_one_gpu_the_bench_workload_and_three_warmups(monkeypatch):
     monkeypatch.setattr("sys.argv", ["bench.py"])
     a = bench.parse_args()
-    assert a.gpus == 1 and a.warmup >= 3 and a.config == "lattice65536" and a.prec == "fp64"
+    assert a.gpus == 1 and a.warmup >= 3 and a.config == "lattice65536"
     assert a.impl != "reference"
+    # no form and no tau given: the equal-accuracy headline, tau from the committed oracle table
+    bench.resolve_defaults(a)
+    assert a.headline and a.prec is None and a.tau == bench.tau_for_sigma("lattice65536", "combined", a.sigma)
+    # an explicit tau or form: a plain line, FP64 unless named
+    monkeypatch.setattr("sys.argv", ["bench.py", "--tau", "1e-6"])
+    b = bench.parse_args()
+    bench.resolve_defaults(b)
+    assert not b.headline and b.prec == "fp64" and b.tau == 1e-6

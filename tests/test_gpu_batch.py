@@ -189,3 +189,44 @@ def test_graph_and_batch_with_subtile_units(S, ctx, bs):
         # the leaf norms are the norms of the leaves
         bi, bj, pay, sq = S.spamm_to_blocks(ctx, E)
         assert np.allclose(sq, np.sum(pay ** 2, axis=(1, 2)), rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("prec,bs", [("fp64", 64), ("fp64", 32), ("fp64", 128), ("fp64", 256), ("bf16_split", 64),
+                                     ("bf16_split4", 64), ("fp16_scaled", 64)])
+def test_sliced_jobs_equal_one_execute_bitwise(S, ctx, prec, bs):
+    """Sliced execution (spamm_job_begin / spamm_run / spamm_job_finish):
+    several jobs run their units in many small launches, a job joining
+    while others are half done; every output is bit-identical (leaves,
+    norms, quadtree) to executing its plan in one launch."""
+    reqs = [(4096, 0.9, 1e-6, "combined"), (2048, 0.7, 1e-4, "spamm"), (4096, 0.6, 1e-8, "combined")]
+    plans = []
+    for n, alpha, tau, mode in reqs:
+        GA, GB = _inputs(S, ctx, n, alpha, bs)
+        plans.append(S.spamm_plan_create(ctx, GA, GB, tau, mode, prec))
+    ref = [S.spamm_execute(ctx, [p])[0] for p in plans]
+    jobs = [S.spamm_job_begin(ctx, plans[0]), S.spamm_job_begin(ctx, plans[1])]
+    launches = 0
+    while any(j.info()["units_done"] < j.info()["units"] for j in jobs) or len(jobs) < len(plans):
+        ran, ms = S.spamm_run(ctx, jobs, [j.info()["work"] / 7.0 + 1.0 for j in jobs])
+        launches += 1
+        if launches == 2:
+            jobs.append(S.spamm_job_begin(ctx, plans[2]))  # joins while the first two are under way
+        assert launches < 100
+    assert launches >= 4
+    for j, C0, p in zip(jobs, ref, plans):
+        C, st = S.spamm_job_finish(ctx, j, stats=True)
+        assert st["n_kept"] == p.info()["n_kept"] and st["n_launches"] >= 2
+        a, b = S.spamm_to_blocks(ctx, C0), S.spamm_to_blocks(ctx, C)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+        L = C.info()["levels"]
+        for t in range(L + 1):
+            assert np.array_equal(S.spamm_level_norms(ctx, C0, t)[1], S.spamm_level_norms(ctx, C, t)[1])
+        j.close()
+    # a job with units left cannot be finished
+    j = S.spamm_job_begin(ctx, plans[0])
+    S.spamm_run(ctx, [j], [1.0])
+    with pytest.raises(S.SpammError) as err:
+        S.spamm_job_finish(ctx, j)
+    assert err.value.status == S.E_BUSY
+    j.close()
