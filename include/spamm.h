@@ -346,6 +346,13 @@ SPAMM_API spamm_status spamm_set_gemm_sms(spamm_ctx ctx, int nsms);
  * timing events only.  Results are identical either way.  Default 0. */
 SPAMM_API spamm_status spamm_set_exec_graph(spamm_ctx ctx, int enable);
 
+/* Graph mode keeps the last instantiated graph in the context and, for the
+ * next batch, updates it in place (cudaGraphExecUpdate: new kernel
+ * parameters and events) when the captured sequence has the same topology,
+ * instantiating a new one only when it does not.  Counts of both since the
+ * context was created; either pointer may be NULL. */
+SPAMM_API spamm_status spamm_exec_graph_info(spamm_ctx ctx, int64_t* instantiations, int64_t* updates);
+
 /* Parity hook: the kept leaf triples of spamm_multiply(A, B, tau, mode) as
  * (i, k, j) int32 triples (3 per triple, host memory), grouped by C leaf in
  * Morton order of (i, j), k ascending within a group.  *count receives the

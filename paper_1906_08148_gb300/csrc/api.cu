@@ -145,6 +145,7 @@ spamm_status spamm_destroy(spamm_ctx ctx) {
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_scratch);
   cudaFreeHost(ctx->h_pinned);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   delete ctx;
   return SPAMM_OK;
@@ -343,8 +344,8 @@ void check_form(spamm_prec prec, int bs) {
        "unknown precision form");
   if (prec == SPAMM_PREC_FP64 && bs > 256)
     fail(SPAMM_E_UNSUPPORTED, "FP64 leaf products are built for bs = 32, 64, 128 and 256");
-  if (prec != SPAMM_PREC_FP64 && bs != 64)
-    fail(SPAMM_E_UNSUPPORTED, "tensor-core precision forms are built for bs = 64");
+  if (prec != SPAMM_PREC_FP64 && bs != 64 && bs != 128)
+    fail(SPAMM_E_UNSUPPORTED, "tensor-core precision forms are built for bs = 64 and 128");
 }
 
 spamm_plan make_plan(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_mode mode, spamm_prec prec) {
@@ -394,8 +395,12 @@ spamm_plan make_plan(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_
       p->bmap.reset();
       prep_terms(Bt, prec, 1, &p->termsB, &p->expB, ctx);
     }
-    p->nsteps = build_quad_steps(ctx, p->T, P<uint32_t>(At->lv[At->L].code), P<int32_t>(p->expA),
-                                 P<int32_t>(p->expB), P<int32_t>(p->bmap), &p->qstart, &p->qsteps);
+    if (p->bs == 128)
+      p->nsteps = build_leaf128_steps(ctx, p->T, P<int32_t>(p->expA), P<int32_t>(p->expB), P<int32_t>(p->bmap),
+                                      &p->qstart, &p->qsteps);
+    else
+      p->nsteps = build_quad_steps(ctx, p->T, P<uint32_t>(At->lv[At->L].code), P<int32_t>(p->expA),
+                                   P<int32_t>(p->expB), P<int32_t>(p->bmap), &p->qstart, &p->qsteps);
   }
   CK(cudaEventRecord(ev.e[3], ctx->stream));
   sync_and_check(ctx);
@@ -473,7 +478,11 @@ PlanOut make_output(spamm_ctx ctx, const spamm_plan_s& p) {
     o.part = alloc_n<double>(ctx, p.T.ngroups * per_leaf);
     d.csq_part = P<double>(o.part);
   }
-  o.units = p.T.ngroups == 0 ? 0 : (p.prec == SPAMM_PREC_FP64 ? p.T.ngroups * per_leaf : p.T.nquads);
+  d.tc_bs = bs;
+  o.units = p.T.ngroups == 0 ? 0
+            : p.prec == SPAMM_PREC_FP64 ? p.T.ngroups * per_leaf
+            : bs == 128 ? p.T.ngroups
+                        : p.T.nquads;
   return o;
 }
 
@@ -566,16 +575,31 @@ std::vector<spamm_mat> execute_plans(spamm_ctx ctx, const std::vector<spamm_plan
     const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
     ctx->stream = run;
     CK(ce);
-    const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    // the instantiated graph of the previous batch is updated in place when
+    // the new one has the same topology (new kernel parameters and events);
+    // otherwise it is replaced
+    bool updated = false;
+    if (ctx->graph_exec) {
+      cudaGraphExecUpdateResultInfo info;
+      updated = cudaGraphExecUpdate(ctx->graph_exec, g, &info) == cudaSuccess;
+      if (!updated) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+      }
+    }
+    cudaError_t ie = cudaSuccess;
+    if (!updated) ie = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
     cudaGraphDestroy(g);
+    if (ie != cudaSuccess) ctx->graph_exec = nullptr;
     CK(ie);
+    ge = ctx->graph_exec;
+    ctx->graph_updates += updated ? 1 : 0;
+    ctx->graph_instantiations += updated ? 0 : 1;
     const cudaError_t le = cudaGraphLaunch(ge, ctx->stream);
-    if (le != cudaSuccess) cudaGraphExecDestroy(ge);
     CK(le);
     ++g_kernel_launches;  // the graph launch itself; its kernels were counted at capture
-    const cudaError_t se = cudaStreamSynchronize(ctx->stream);
-    cudaGraphExecDestroy(ge);
-    CK(se);
+    CK(cudaStreamSynchronize(ctx->stream));
   } else {
     sequence(cudaEventRecordDefault);
   }
@@ -798,6 +822,13 @@ spamm_status spamm_set_gemm_sms(spamm_ctx ctx, int nsms) {
 spamm_status spamm_set_exec_graph(spamm_ctx ctx, int enable) {
   if (!ctx) return SPAMM_E_INVALID_ARG;
   ctx->exec_graph = enable != 0;
+  return SPAMM_OK;
+}
+
+spamm_status spamm_exec_graph_info(spamm_ctx ctx, int64_t* instantiations, int64_t* updates) {
+  if (!ctx) return SPAMM_E_INVALID_ARG;
+  if (instantiations) *instantiations = ctx->graph_instantiations;
+  if (updates) *updates = ctx->graph_updates;
   return SPAMM_OK;
 }
 

@@ -1,4 +1,4 @@
-// gemm_tc.cu -- kernel (c), tensor-core forms (bs = 64): BF16 error-free
+// gemm_tc.cu -- kernel (c), tensor-core forms (bs = 64 and 128): BF16 error-free
 // slice splits (3 or 4 slices) and FP16 with per-leaf power-of-two scaling,
 // with the C-leaf norms of kernel (d) in the epilogue.
 //
@@ -20,6 +20,10 @@
 // accumulator per output element; the BF16 forms keep a two-float (hi + lo)
 // accumulator, adding each exact accumulator with an error-free TwoSum and
 // the rest into lo, and write hi + lo in FP64.
+//
+// 128 x 128 leaves.  A unit is one output leaf; its four 64 x 64 quadrants
+// are the children, and every kept product runs as two K-half steps over the
+// tile-split operand terms (prep.cu, steps.cu): the same steps and MMAs.
 //
 // Quads.  The four output leaves (2I + h, 2J + c) of a quadtree node one level
 // above the leaves are computed together: at each k the A operand of term s is
@@ -362,7 +366,10 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
       const int r = plan_of(batch.ubegin, batch.nplans, un);
       const PlanDev& pl = batch.plans[r];
       const int64_t Q = un - batch.ubegin[r];
-      const int32_t g[4] = {pl.quads[4 * Q], pl.quads[4 * Q + 1], pl.quads[4 * Q + 2], pl.quads[4 * Q + 3]};
+      // children: four output leaves (64-leaves), or the four quadrants of output leaf Q (128-leaves)
+      const bool big = pl.tc_bs == 128;
+      const int32_t g[4] = {big ? (int32_t)Q : pl.quads[4 * Q], big ? (int32_t)Q : pl.quads[4 * Q + 1],
+                            big ? (int32_t)Q : pl.quads[4 * Q + 2], big ? (int32_t)Q : pl.quads[4 * Q + 3]};
 #pragma unroll
       for (int i = 0; i < NHI; ++i) hi[i] = 0.f;
 #pragma unroll
@@ -423,7 +430,8 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
       const int gl = g[child];
       double s2 = 0.0;
       if (gl >= 0) {
-        double2* out = reinterpret_cast<double2*>(pl.cpool + (int64_t)gl * 4096 + row * 64);
+        double2* out = reinterpret_cast<double2*>(big ? pl.cpool + (int64_t)gl * 16384 + (64 * half + row) * 128 + 64 * col
+                                                      : pl.cpool + (int64_t)gl * 4096 + row * 64);
 #pragma unroll
         for (int q = 0; q < 64; q += 4) {
           double x[4];
@@ -453,7 +461,15 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
       if (lane == 0) red[col][quarter] = s2;
       if (te == 0) epi_stop = *abortp;
       named_barrier(1, 256);
-      if (te < 4) {
+      if (big) {
+        // one output leaf: its quadrants' squared norms added in quadrant order
+        if (te == 0 && g[0] >= 0) {
+          double t = 0.0;
+          for (int hh = 0; hh < 2; ++hh)
+            for (int cc = 0; cc < 2; ++cc) t += red[cc][2 * hh] + red[cc][2 * hh + 1];
+          pl.csq[g[0]] = t;
+        }
+      } else if (te < 4) {
         const int cc = te & 1, hh = te >> 1;  // child 2 hh + cc: its rows are quarters 2 hh, 2 hh + 1
         if (g[2 * hh + cc] >= 0) pl.csq[g[2 * hh + cc]] = red[cc][2 * hh] + red[cc][2 * hh + 1];
       }

@@ -114,6 +114,8 @@ struct spamm_ctx_s {
   int gemm_sm_limit = 0;                     // 0: leaf GEMM may use every SM
   int exec_graph = 0;                        // run the execute phase as a captured CUDA graph
   cudaStream_t capture_stream = nullptr;     // created on first graph capture
+  cudaGraphExec_t graph_exec = nullptr;      // the last execute graph, updated in place for the next batch
+  int64_t graph_instantiations = 0, graph_updates = 0;
   int live_handles = 0;
 };
 
@@ -213,6 +215,7 @@ struct PlanDev {
   double* csq;
   const int64_t* uorder;  // FP64 form: output leaf at each claiming position (longest first), or null for identity
   double* csq_part;       // FP64 form, leaves split into sub-tile units: partial squared norms [leaf][sub-tile]
+  int32_t tc_bs;          // tensor forms: 64 (units are quads of output leaves) or 128 (units are output leaves)
 };
 struct BatchDev {
   const PlanDev* plans;
@@ -241,8 +244,10 @@ int fp64_units_per_leaf(int bs);
 BufP fp64_unit_order(spamm_ctx ctx, const TaskList& T, int bs);
 // The tensor-core forms' persistent quad kernel (gemm_tc.cu).
 void gemm_tc_batch(spamm_ctx ctx, spamm_prec prec, const BatchDev& b);
+// 64 x 64 operand tiles per leaf of the tensor forms (bs 64: 1, bs 128: 4).
+inline int tc_tiles_per_leaf(int bs) { return (bs / 64) * (bs / 64); }
 // Operand terms of a leaf set for a tensor form (role 0: used as A, 1: as B),
-// and each leaf's power-of-two scale exponent.
+// and each tile's power-of-two scale exponent.
 void prep_terms(spamm_mat M, spamm_prec prec, int role, BufP* terms, BufP* expo, spamm_ctx on = nullptr);
 // Step list of every quad of T for the tensor-core kernel; returns the step count.
 // codeA: Morton codes of A's leaves (the k of a task is the column of its A
@@ -252,6 +257,10 @@ void prep_terms(spamm_mat M, spamm_prec prec, int role, BufP* terms, BufP* expo,
 // transposed leaf); the step list then refers to that index.
 int64_t build_quad_steps(spamm_ctx ctx, const TaskList& T, const uint32_t* codeA, const int32_t* expA,
                          const int32_t* expB, const int32_t* bmap, BufP* qstart, BufP* qsteps);
+// The same for 128 x 128 leaves: one unit per output leaf, two K-half steps
+// per kept product (T.gstart doubled), on the tile-split operand terms.
+int64_t build_leaf128_steps(spamm_ctx ctx, const TaskList& T, const int32_t* expA, const int32_t* expB,
+                            const int32_t* bmap, BufP* qstart, BufP* qsteps);
 // For every leaf (k, j) of M, the index of leaf (j, k) in M (-1 if absent);
 // returns the number of absent ones (synchronises).
 int64_t transpose_map(spamm_mat M, BufP* map, spamm_ctx on = nullptr);

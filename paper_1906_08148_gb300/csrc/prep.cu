@@ -12,8 +12,9 @@
 namespace spamm {
 
 // Thread <-> element mapping shared by both kernels: one CTA of 256 threads
-// per leaf; a thread owns two 16-byte chunks of the K-major term tiles (8
-// consecutive k of one tile row) and loads their 16 FP64 elements first.
+// per 64 x 64 tile of a leaf; a thread owns two 16-byte chunks of the
+// K-major term tiles (8 consecutive k of one tile row) and loads their 16
+// FP64 elements first.
 // role 0 (A): tile row = leaf row (t >> 3) + 32 j, k = leaf columns 8 (t & 7) ..
 // role 1 (B): tile row = leaf column t & 63, k = leaf rows 8 ((t >> 6) + 4 j) ..,
 // so the lanes of a warp read consecutive doubles of each leaf row.
@@ -26,14 +27,28 @@ struct ChunkMap {
       c8[j] = role == 0 ? (t & 7) : (t >> 6) + 4 * j;
     }
   }
-  __device__ void load(const unsigned long long* src, int role, unsigned long long (&v)[2][8]) const {
+  // src: the tile's first element; ld: the leaf's row length
+  __device__ void load(const unsigned long long* src, int ld, int role, unsigned long long (&v)[2][8]) const {
 #pragma unroll
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int e = 0; e < 8; ++e)
-        v[j][e] = role == 0 ? __ldg(src + row[j] * 64 + 8 * c8[j] + e) : __ldg(src + (8 * c8[j] + e) * 64 + row[j]);
+        v[j][e] = role == 0 ? __ldg(src + row[j] * ld + 8 * c8[j] + e) : __ldg(src + (8 * c8[j] + e) * ld + row[j]);
   }
 };
+
+// Operand tiles of a leaf.  A 64 x 64 leaf is one tile; a 128 x 128 leaf is
+// four, tile 2 r2 + kh holding rows 64 r2 .. of the leaf's row dimension for
+// the operand (A: leaf rows; B: leaf columns) and k = 64 kh ..  (A: leaf
+// columns; B: leaf rows), each split and scaled as a 64 x 64 leaf of its own,
+// so the leaf-product kernel runs a 128-leaf product as two K-half steps
+// over the four tiles of each operand.  Tile x of leaf m is at index
+// m * tiles + x of the term and exponent arrays.
+__device__ __forceinline__ const double* tile_src(const double* leaf, int bs, int role, int x) {
+  if (bs == 64) return leaf;
+  const int r2 = x >> 1, kh = x & 1;
+  return role == 0 ? leaf + (int64_t)(64 * r2) * bs + 64 * kh : leaf + (int64_t)(64 * kh) * bs + 64 * r2;
+}
 
 // ------------------------------------------------------- BF16 slices (error-free split)
 // Per leaf: the largest biased exponent of every line (A: row, B: column) and
@@ -42,18 +57,22 @@ struct ChunkMap {
 // slices are assembled in shared memory and leave as one contiguous block.
 template <int S, bool KHALF>
 __global__ void __launch_bounds__(256) prep_slices_kernel(const double* __restrict__ pool,
-                                                          const int64_t* __restrict__ slot, int64_t nleaves, int role,
-                                                          uint8_t* __restrict__ out, int32_t* __restrict__ expo) {
+                                                          const int64_t* __restrict__ slot, int64_t nleaves, int bs,
+                                                          int role, uint8_t* __restrict__ out,
+                                                          int32_t* __restrict__ expo) {
   constexpr uint32_t LEAF = (uint32_t)S * kTerm;
   __shared__ uint4 stile[LEAF / 16];
   __shared__ int s_line[4][64];  // role 1: per-column maxima of each quarter of the leaf rows
   __shared__ int s_warp[8];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const ChunkMap cm(t, role);
-  for (int64_t m = blockIdx.x; m < nleaves; m += gridDim.x) {
-    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(pool + slot[m] * 4096);
+  const int tiles = (bs / 64) * (bs / 64);
+  for (int64_t m = blockIdx.x; m < nleaves * tiles; m += gridDim.x) {
+    const int64_t leaf = m / tiles;
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(
+        tile_src(pool + slot[leaf] * (int64_t)bs * bs, bs, role, (int)(m - leaf * tiles)));
     unsigned long long v[2][8];
-    cm.load(src, role, v);
+    cm.load(src, bs, role, v);
     // largest biased exponent of each of this thread's two lines
     int em[2];
 #pragma unroll
@@ -121,19 +140,23 @@ __global__ void __launch_bounds__(256) prep_slices_kernel(const double* __restri
 // per-leaf scale 2^e folded in, max|a 2^e| in [2^14, 2^15), then split in
 // FP32: h0 = f16(a 2^e), h1 = f16(a 2^e - h0) (the residual is exact in FP32).
 __global__ void __launch_bounds__(256) prep_fp16_kernel(const double* __restrict__ pool,
-                                                        const int64_t* __restrict__ slot, int64_t nleaves, int role,
-                                                        uint8_t* __restrict__ out, int32_t* __restrict__ expo) {
+                                                        const int64_t* __restrict__ slot, int64_t nleaves, int bs,
+                                                        int role, uint8_t* __restrict__ out,
+                                                        int32_t* __restrict__ expo) {
   constexpr int TERMS = FormCfg<SPAMM_PREC_FP16_SCALED>::TERMS;
   constexpr uint32_t LEAF = leaf_bytes<SPAMM_PREC_FP16_SCALED>();
   __shared__ unsigned long long smax[8];
   __shared__ int s_shift;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const ChunkMap cm(t, role);
-  for (int64_t m = blockIdx.x; m < nleaves; m += gridDim.x) {
-    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(pool + slot[m] * 4096);
+  const int tiles = (bs / 64) * (bs / 64);
+  for (int64_t m = blockIdx.x; m < nleaves * tiles; m += gridDim.x) {
+    const int64_t leaf = m / tiles;
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(
+        tile_src(pool + slot[leaf] * (int64_t)bs * bs, bs, role, (int)(m - leaf * tiles)));
     unsigned long long v[2][8];
-    cm.load(src, role, v);
-    // largest |a| of the leaf: |x| of doubles orders like their bits without the sign
+    cm.load(src, bs, role, v);
+    // largest |a| of the tile: |x| of doubles orders like their bits without the sign
     unsigned long long mx = 0;
 #pragma unroll
     for (int j = 0; j < 2; ++j)
@@ -190,24 +213,25 @@ static uint32_t form_leaf_bytes(spamm_prec prec) {
 
 void prep_terms(spamm_mat M, spamm_prec prec, int role, BufP* terms, BufP* expo, spamm_ctx on) {
   spamm_ctx ctx = on ? on : M->ctx;
-  if (M->bs != 64) fail(SPAMM_E_UNSUPPORTED, "tensor-core precision forms are built for bs = 64");
-  const int64_t want = M->nleaves, cap = (int64_t)ctx->num_sms * 8;
-  const unsigned grid = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
-  *terms = alloc_n<uint8_t>(ctx, M->nleaves * (int64_t)form_leaf_bytes(prec));
-  *expo = alloc_n<int32_t>(ctx, M->nleaves);
+  const int bs = M->bs;
+  if (bs != 64 && bs != 128) fail(SPAMM_E_UNSUPPORTED, "tensor-core precision forms are built for bs = 64 and 128");
+  const int64_t ntiles = M->nleaves * tc_tiles_per_leaf(bs), cap = (int64_t)ctx->num_sms * 8;
+  const unsigned grid = (unsigned)(ntiles < cap ? (ntiles > 0 ? ntiles : 1) : cap);
+  *terms = alloc_n<uint8_t>(ctx, ntiles * (int64_t)form_leaf_bytes(prec));
+  *expo = alloc_n<int32_t>(ctx, ntiles);
   if (M->nleaves == 0) return;
   const double* pool = P<double>(M->pool);
   const int64_t* slot = P<int64_t>(M->slot);
   if (prec == SPAMM_PREC_BF16_SPLIT) {
-    prep_slices_kernel<3, false><<<grid, 256, 0, ctx->stream>>>(pool, slot, M->nleaves, role, P<uint8_t>(*terms),
-                                                                P<int32_t>(*expo));
+    prep_slices_kernel<3, false><<<grid, 256, 0, ctx->stream>>>(pool, slot, M->nleaves, bs, role,
+                                                                P<uint8_t>(*terms), P<int32_t>(*expo));
     CK_LAUNCH("prep_slices_kernel<3>");
   } else if (prec == SPAMM_PREC_BF16_SPLIT4) {
-    prep_slices_kernel<4, true><<<grid, 256, 0, ctx->stream>>>(pool, slot, M->nleaves, role, P<uint8_t>(*terms),
-                                                               P<int32_t>(*expo));
+    prep_slices_kernel<4, true><<<grid, 256, 0, ctx->stream>>>(pool, slot, M->nleaves, bs, role,
+                                                               P<uint8_t>(*terms), P<int32_t>(*expo));
     CK_LAUNCH("prep_slices_kernel<4>");
   } else {
-    prep_fp16_kernel<<<grid, 256, 0, ctx->stream>>>(pool, slot, M->nleaves, role, P<uint8_t>(*terms),
+    prep_fp16_kernel<<<grid, 256, 0, ctx->stream>>>(pool, slot, M->nleaves, bs, role, P<uint8_t>(*terms),
                                                     P<int32_t>(*expo));
     CK_LAUNCH("prep_fp16_kernel");
   }

@@ -123,6 +123,59 @@ int64_t transpose_map(spamm_mat M, BufP* map, spamm_ctx on) {
   return (int64_t)read_scalar(ctx, reinterpret_cast<const uint64_t*>(missing));
 }
 
+// ------------------------------------------------------ 128 x 128 leaves
+// A 128-leaf product is one unit of the tensor-core kernel: its four 64 x 64
+// quadrants (2h + c) are the unit's children, and kept product q of output
+// leaf g runs as steps 2q and 2q + 1, the two K halves kh, on operand tiles
+// 4 leaf + 2 h + kh (A) and 4 leaf + 2 c + kh (B) of the tile-split terms.
+// So the steps of leaf g start at 2 gstart[g], in the leaf's k order.
+__global__ void leaf128_steps_kernel(int64_t ntasks, const int32_t* __restrict__ ta, const int32_t* __restrict__ tb,
+                                     const int32_t* __restrict__ expA, const int32_t* __restrict__ expB,
+                                     const int32_t* __restrict__ bmap, QuadStep* __restrict__ out) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ntasks; q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t la = ta[q], lb = bmap ? bmap[tb[q]] : tb[q];
+#pragma unroll
+    for (int kh = 0; kh < 2; ++kh) {
+      QuadStep st;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        st.a[h] = 4 * la + 2 * h + kh;
+        st.b[h] = 4 * lb + 2 * h + kh;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int ea = expA[st.a[c >> 1]], eb = expB[st.b[c & 1]];
+        st.scale[c] = __int_as_float((127 - ea) << 23) * __int_as_float((127 - eb) << 23);
+      }
+      out[2 * q + kh] = st;
+    }
+  }
+}
+
+__global__ void twice_kernel(int64_t n, const int64_t* __restrict__ in, uint64_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = 2 * (uint64_t)in[i];
+}
+
+int64_t build_leaf128_steps(spamm_ctx ctx, const TaskList& T, const int32_t* expA, const int32_t* expB,
+                            const int32_t* bmap, BufP* qstart, BufP* qsteps) {
+  const int64_t ng = T.ngroups;
+  *qstart = alloc_n<uint64_t>(ctx, ng + 1);
+  *qsteps = alloc_n<QuadStep>(ctx, 2 * T.ntasks);
+  const int64_t cap = (int64_t)ctx->num_sms * 16;
+  const int64_t g1 = (ng + 1 + 255) / 256;
+  twice_kernel<<<(unsigned)(g1 < cap ? g1 : cap), 256, 0, ctx->stream>>>(ng + 1, P<int64_t>(T.gstart),
+                                                                          P<uint64_t>(*qstart));
+  CK_LAUNCH("twice_kernel");
+  if (T.ntasks > 0) {
+    const int64_t g2 = (T.ntasks + 255) / 256;
+    leaf128_steps_kernel<<<(unsigned)(g2 < cap ? g2 : cap), 256, 0, ctx->stream>>>(
+        T.ntasks, P<int32_t>(T.ta), P<int32_t>(T.tb), expA, expB, bmap, P<QuadStep>(*qsteps));
+    CK_LAUNCH("leaf128_steps_kernel");
+  }
+  return 2 * T.ntasks;
+}
+
 int64_t build_quad_steps(spamm_ctx ctx, const TaskList& T, const uint32_t* codeA, const int32_t* expA,
                          const int32_t* expB, const int32_t* bmap, BufP* qstart, BufP* qsteps) {
   const int64_t nq = T.ngroups > 0 ? T.nquads : 0;

@@ -38,7 +38,7 @@ ENTRY_POINTS = (
     "spamm_plan_create", "spamm_plan_info", "spamm_execute", "spamm_plan_release", "spamm_set_gemm_sms",
     "spamm_set_exec_graph", "spamm_add", "spamm_identity", "spamm_trace", "spamm_check_timeout_path", "spamm_trim",
     "spamm_set_symmetric", "spamm_job_begin", "spamm_job_info", "spamm_run", "spamm_job_finish",
-    "spamm_job_release",
+    "spamm_job_release", "spamm_exec_graph_info",
 )
 NOALLOC_MAX_LEAVES = 1 << 24
 
@@ -118,6 +118,7 @@ def load(path: str = LIB_PATH):
         "spamm_run": [vp, i64, ctypes.POINTER(vp), pf64, pi64, pf64],
         "spamm_job_finish": [vp, vp, ctypes.POINTER(vp), ctypes.POINTER(Stats)],
         "spamm_job_release": [vp],
+        "spamm_exec_graph_info": [vp, pi64, pi64],
         "spamm_to_dense": [vp, vp, vp, i64, ctypes.c_int],
         "spamm_to_blocks": [vp, vp, vp, vp, vp, vp, i64, ctypes.c_int],
         "spamm_level_norms": [vp, vp, ctypes.c_int, vp, vp, i64, pi64],
@@ -529,6 +530,12 @@ def spamm_job_finish(ctx: Context, job: Job, stats: bool = False):
     _check(ctx.handle, load().spamm_job_finish(ctx.handle, job.handle, ctypes.byref(out), ctypes.byref(st)))
     C = Matrix(ctx, out)
     return (C, st.as_dict()) if stats else C
+
+
+def spamm_exec_graph_info(ctx: Context) -> dict:
+    i, u = ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx.handle, load().spamm_exec_graph_info(ctx.handle, ctypes.byref(i), ctypes.byref(u)))
+    return {"instantiations": i.value, "updates": u.value}
 
 
 def spamm_set_gemm_sms(ctx: Context, nsms: int):

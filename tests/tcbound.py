@@ -3,12 +3,15 @@ FP64 product on the same kept set (a helper for the GPU tests).
 
 FP16 scaled: each operand is represented by its two terms to 2^-22 relative
 (after rounding to FP32), each leaf product is accumulated in FP32 over
-K = 64 and added into an FP32 register accumulator once per kept product:
+K = 64 and added into an FP32 register accumulator once per step (one per
+kept product, two for 128-leaves), n_k steps in all:
     |C_tc - C_fp64|_ij <= (n_k + 16) 2^-20 (|A||B|)_ij.
 
 BF16 splits with S slices (3: bf16_split, 4: bf16_split4).  For the rows r of
 A leaf (i, k) and columns c of B leaf (k, j), with l = the exponent of the
-line's largest |x| (x_max < 2^l), per kept leaf product:
+line's largest |x| (x_max < 2^l; 128-leaves are split into 64-wide K halves,
+each with its own line exponents, and the terms below add over the halves),
+per kept leaf product:
   * dropped digits and slice products (the split's residual, checked against
     exact arithmetic on the CPU in test_slices_host.py):
         64 (S + 1.01) 2^(lA_r + lB_c - 9 S);
@@ -55,23 +58,25 @@ def bound(prec, At: oracle.LeafMatrix, Bt: oracle.LeafMatrix, ikj: np.ndarray, r
     out = np.zeros_like(ref.data)
     for (r, c), q in key.items():
         out[q] = absprod.data[apos[(r, c)]]
+    nkh = At.bs // 64  # K halves: a 128-leaf product runs as two 64-deep steps
     if prec == "fp16_scaled":
         c0, e = FP16
         nk = np.zeros(ref.m)
         for i, _, j in ikj.tolist():
-            nk[key[(i, j)]] += 1
+            nk[key[(i, j)]] += nkh
         return (nk[:, None, None] + c0) * 2.0 ** -e * out + 1e-300
     S, nacc = SLICES[prec]
     trunc, acc = slice_consts(S, nacc)
     ia = {(int(r), int(c)): q for q, (r, c) in enumerate(zip(At.bi, At.bj))}
     ib = {(int(r), int(c)): q for q, (r, c) in enumerate(zip(Bt.bi, Bt.bj))}
-    la = [_line_exp(At.data[q], 1) for q in range(At.m)]
-    lb = [_line_exp(Bt.data[q], 0) for q in range(Bt.m)]
+    # line exponents per 64-wide K half: A rows over columns 64 kh.., B columns over rows 64 kh..
+    la = [[_line_exp(At.data[q][:, 64 * h:64 * h + 64], 1) for h in range(nkh)] for q in range(At.m)]
+    lb = [[_line_exp(Bt.data[q][64 * h:64 * h + 64, :], 0) for h in range(nkh)] for q in range(Bt.m)]
     ma = np.max(np.abs(At.data), axis=(1, 2))
     mb = np.max(np.abs(Bt.data), axis=(1, 2))
     b = 2.0 ** -44 * out + 2.0 ** -52 * np.abs(ref.data)
     for i, k, j in ikj.tolist():
         qa, qb = ia[(i, k)], ib[(k, j)]
-        p2 = np.exp2(la[qa][:, None] + lb[qb][None, :])
-        b[key[(i, j)]] += (trunc + acc) * p2 + 64.0 * S * 2.0 ** -116 * ma[qa] * mb[qb]
+        p2 = sum(np.exp2(la[qa][h][:, None] + lb[qb][h][None, :]) for h in range(nkh))
+        b[key[(i, j)]] += (trunc + acc) * p2 + nkh * 64.0 * S * 2.0 ** -116 * ma[qa] * mb[qb]
     return b + 1e-300

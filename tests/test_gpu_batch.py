@@ -99,7 +99,7 @@ def test_gemm_sm_limit_keeps_results(S, ctx):
     assert np.array_equal(ref[2], got[2])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16_split", "fp16_scaled"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16_split", "bf16_split4", "fp16_scaled"])
 def test_graph_execute_equals_eager(S, ctx, prec):
     """The execute phase captured as one CUDA graph gives the same leaves and
     the same norms at every quadtree level as the eager launch sequence."""
@@ -111,10 +111,16 @@ def test_graph_execute_equals_eager(S, ctx, prec):
     eager, st_e = S.spamm_execute(ctx, plans, stats=True)
     S.spamm_set_exec_graph(ctx, True)
     try:
+        g0 = S.spamm_exec_graph_info(ctx)
         graph, st_g = S.spamm_execute(ctx, plans, stats=True)
+        again, _ = S.spamm_execute(ctx, plans, stats=True)  # same topology: the graph is updated, not rebuilt
+        g1 = S.spamm_exec_graph_info(ctx)
         single = S.spamm_multiply(ctx, keep[0][0], keep[0][1], REQUESTS[0][2], REQUESTS[0][3], prec)
     finally:
         S.spamm_set_exec_graph(ctx, False)
+    assert g1["updates"] >= g0["updates"] + 1
+    for G, A in zip(graph, again):
+        assert np.array_equal(S.spamm_to_blocks(ctx, G)[2], S.spamm_to_blocks(ctx, A)[2])
     for r, (E, G) in enumerate(zip(eager, graph)):
         for a, b in zip(S.spamm_to_blocks(ctx, E), S.spamm_to_blocks(ctx, G)):
             assert np.array_equal(a, b), (prec, r)

@@ -59,14 +59,15 @@ def _check(S, ctx, GA, GB, MA, MB, tau, mode, prec):
 
 
 @pytest.mark.parametrize("prec", TC)
-@pytest.mark.parametrize("mode", ["spamm", "combined", "truncate"])
-def test_tensor_forms_within_derived_bound(S, ctx, prec, mode):
+@pytest.mark.parametrize("mode,bs", [("spamm", 64), ("combined", 64), ("truncate", 64), ("combined", 128)])
+def test_tensor_forms_within_derived_bound(S, ctx, prec, mode, bs):
     pa, pb = synth.lattice_3d(4096, alpha=0.9, seed=1), synth.lattice_3d(4096, alpha=0.9, seed=2)
-    GA, GB = S.spamm_generate(ctx, pa, 64), S.spamm_generate(ctx, pb, 64)
-    MA, MB = oracle.from_dense(synth.dense(pa), 64), oracle.from_dense(synth.dense(pb), 64)
+    GA, GB = S.spamm_generate(ctx, pa, bs), S.spamm_generate(ctx, pb, bs)
+    MA, MB = oracle.from_dense(synth.dense(pa), bs), oracle.from_dense(synth.dense(pb), bs)
     for tau in (1e-4, 1e-6):
         worst, rel, _ = _check(S, ctx, GA, GB, MA, MB, tau, mode, prec)
-        print(f"{prec} {mode} tau={tau}: rel Frobenius error vs FP64 oracle {rel:.3e}, worst/bound {worst:.3f}")
+        print(f"{prec} {mode} bs={bs} tau={tau}: rel Frobenius error vs FP64 oracle {rel:.3e}, "
+              f"worst/bound {worst:.3f}")
         assert worst <= 1.0
 
 
@@ -87,34 +88,36 @@ def test_tensor_error_below_truncation_error(S, ctx, prec):
 
 
 @pytest.mark.parametrize("prec", TC)
-def test_single_leaf_product_layout(S, ctx, prec):
-    """One 64 x 64 leaf pair with distinct entries: any operand layout or
+@pytest.mark.parametrize("bs", [64, 128])
+def test_single_leaf_product_layout(S, ctx, prec, bs):
+    """One leaf pair with distinct entries: any operand layout, tile or
     descriptor mistake shows up as an O(1) error."""
     rng = np.random.default_rng(11)
-    A = rng.uniform(-1, 1, (64, 64))
-    B = rng.uniform(-1, 1, (64, 64))
-    GA, GB = S.spamm_from_dense(ctx, A, 64), S.spamm_from_dense(ctx, B, 64)
+    A = rng.uniform(-1, 1, (bs, bs))
+    B = rng.uniform(-1, 1, (bs, bs))
+    GA, GB = S.spamm_from_dense(ctx, A, bs), S.spamm_from_dense(ctx, B, bs)
     C = S.spamm_to_dense(ctx, S.spamm_multiply(ctx, GA, GB, 0.0, "spamm", prec))
-    MA, MB = oracle.from_dense(A, 64), oracle.from_dense(B, 64)
+    MA, MB = oracle.from_dense(A, bs), oracle.from_dense(B, bs)
     ref, ikj = oracle.multiply(MA, MB, 0.0, oracle.SPAMM)
     bnd = tcbound.bound(prec, MA, MB, ikj, ref)[0]
     assert np.all(np.abs(C - A @ B) <= bnd)
 
 
 @pytest.mark.parametrize("prec", TC)
-def test_tensor_ragged_and_empty(S, ctx, prec):
+@pytest.mark.parametrize("bs", [64, 128])
+def test_tensor_ragged_and_empty(S, ctx, prec, bs):
     rng = np.random.default_rng(5)
-    n = 200  # ragged: 4 x 4 leaves, the last ones padded
+    n = 200 if bs == 64 else 330  # ragged: 4 x 4 (3 x 3) leaves, the last ones padded
     A = rng.uniform(-1, 1, (n, n)) * np.exp(-0.05 * np.abs(np.subtract.outer(np.arange(n), np.arange(n))))
-    GA = S.spamm_from_dense(ctx, A, 64)
+    GA = S.spamm_from_dense(ctx, A, bs)
     C = S.spamm_to_dense(ctx, S.spamm_multiply(ctx, GA, GA, 0.0, "spamm", prec))
-    MA = oracle.from_dense(A, 64)
+    MA = oracle.from_dense(A, bs)
     ref, ikj = oracle.multiply(MA, MA, 0.0, oracle.SPAMM)
-    bnd = oracle.to_dense(oracle.LeafMatrix(n, 64, ref.bi, ref.bj, tcbound.bound(prec, MA, MA, ikj, ref)))
+    bnd = oracle.to_dense(oracle.LeafMatrix(n, bs, ref.bi, ref.bj, tcbound.bound(prec, MA, MA, ikj, ref)))
     assert np.all(np.abs(C - A @ A) <= bnd)
     E = S.spamm_multiply(ctx, GA, GA, 1e9, "spamm", prec)
     assert E.info()["nleaves"] == 0
-    G32 = S.spamm_from_dense(ctx, A, 32)
+    G32 = S.spamm_from_dense(ctx, A, 32)  # 32 x 32 leaves: FP64 only
     with pytest.raises(S.SpammError) as err:
         S.spamm_multiply(ctx, G32, G32, 0.0, "spamm", prec)
     assert err.value.status == S.E_UNSUPPORTED
@@ -143,7 +146,8 @@ def test_power_of_two_scaling_is_exact(S, ctx, prec):
 
 
 @pytest.mark.parametrize("prec,amax", [("bf16_split", 255), ("bf16_split4", 65535)])
-def test_integer_inputs_are_exact(S, ctx, prec, amax):
+@pytest.mark.parametrize("bs", [64, 128])
+def test_integer_inputs_are_exact(S, ctx, prec, amax, bs):
     """Integer A (|a| <= amax: one digit for the 3-slice split, two for the
     4-slice split) and integer B (|b| <= 255, one digit): the split is exact,
     every slice product of index sum 0 (and 1) sums over K = 64 to at most
@@ -152,11 +156,11 @@ def test_integer_inputs_are_exact(S, ctx, prec, amax):
     nothing: C equals A B bit for bit.  The all-maximal 3-slice case puts the
     first accumulator at 64 * 255^2 = 4,161,600, next to 2^22."""
     rng = np.random.default_rng(8)
-    n = 256
+    n = 4 * bs
     for A, B in ((rng.integers(-amax, amax + 1, (n, n)).astype(np.float64),
                   rng.integers(-255, 256, (n, n)).astype(np.float64)),
                  (np.full((n, n), float(amax)), np.full((n, n), 255.0))):
-        GA, GB = S.spamm_from_dense(ctx, A, 64), S.spamm_from_dense(ctx, B, 64)
+        GA, GB = S.spamm_from_dense(ctx, A, bs), S.spamm_from_dense(ctx, B, bs)
         C = S.spamm_to_dense(ctx, S.spamm_multiply(ctx, GA, GB, 0.0, "spamm", prec))
         assert np.array_equal(C, A @ B)
 
@@ -196,14 +200,15 @@ def test_tensor_error_below_truncation_error_16384(S, ctx, prec, taus):
 
 
 @pytest.mark.parametrize("prec", TC)
-def test_symmetric_square_shares_terms(S, ctx, prec):
+@pytest.mark.parametrize("bs", [64, 128])
+def test_symmetric_square_shares_terms(S, ctx, prec, bs):
     """X times X for a symmetric X (the squarings of a purification chain):
     one set of operand terms serves both roles (B's leaf (k, j) uses the
     terms of leaf (j, k)); the output is bit-identical to building the B
     terms separately, and the plan holds fewer bytes.  A leaf set without
     every transpose falls back to separate terms."""
     p = synth.lattice_3d(4096, alpha=0.9, seed=4)
-    X = S.spamm_generate(ctx, p, 64)
+    X = S.spamm_generate(ctx, p, bs)
     tau = 1e-6
     shared, st1 = S.spamm_multiply(ctx, X, X, tau, "combined", prec, stats=True)
     pl1 = S.spamm_plan_create(ctx, X, X, tau, "combined", prec)
@@ -217,14 +222,14 @@ def test_symmetric_square_shares_terms(S, ctx, prec):
     assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
     # the mark on a leaf set that lacks a transpose: separate terms, the product A A
     rng = np.random.default_rng(9)
-    D = np.zeros((256, 256))
-    D[:64, :64] = rng.uniform(-1, 1, (64, 64))
-    D[64:128, :64] = rng.uniform(-1, 1, (64, 64))  # leaf (1, 0) without (0, 1)
-    G = S.spamm_from_dense(ctx, D, 64)
+    D = np.zeros((4 * bs, 4 * bs))
+    D[:bs, :bs] = rng.uniform(-1, 1, (bs, bs))
+    D[bs:2 * bs, :bs] = rng.uniform(-1, 1, (bs, bs))  # leaf (1, 0) without (0, 1)
+    G = S.spamm_from_dense(ctx, D, bs)
     G.set_symmetric(True)
     C, st = S.spamm_multiply(ctx, G, G, 0.0, "spamm", prec, stats=True)
     assert st["terms_shared"] == 0
-    M = oracle.from_dense(D, 64)
+    M = oracle.from_dense(D, bs)
     ref, ikj = oracle.multiply(M, M, 0.0, oracle.SPAMM)
-    bnd = oracle.to_dense(oracle.LeafMatrix(256, 64, ref.bi, ref.bj, tcbound.bound(prec, M, M, ikj, ref)))
+    bnd = oracle.to_dense(oracle.LeafMatrix(4 * bs, bs, ref.bi, ref.bj, tcbound.bound(prec, M, M, ikj, ref)))
     assert np.all(np.abs(S.spamm_to_dense(ctx, C) - D @ D) <= bnd)
