@@ -1,18 +1,28 @@
-"""Choice of precision form and leaf size per multiply request.
+"""Choice of precision form and leaf size per multiply request, and the
+work rate that sizes each launch of the served stream.
 
 A request is described by (n, alpha, tau): the size, the decay rate of its
 inputs and the threshold.  The candidates are the library's forms: FP64 leaf
 products with 32 x 32, 64 x 64 or 128 x 128 leaves, and the tensor-core
-forms (BF16 three-term split, FP16 with per-leaf scaling) with 64 x 64
-leaves.
+forms (BF16 3-slice and 4-slice error-free splits, FP16 with per-leaf
+scaling) with 64 x 64 or 128 x 128 leaves.
 
-`calibrate` measures every candidate on synthetic decay inputs at a grid of
+`calibrate` measures the candidates on synthetic decay inputs at a grid of
 (n, alpha, tau) points: the time of plan + execute, and for each tensor form
-its arithmetic error against the FP64 product at the same tau next to the
-truncation error of the method itself (against the exact FP64 product).  A
-form is admissible at a point when its arithmetic error does not exceed the
-truncation error there (the error of the result is then still dominated by
-the method's own approximation); the fastest admissible candidate wins.
+its arithmetic error ||C_form - C_ref||_F, where C_ref is the 4-slice split
+at the same tau and leaf size (its own arithmetic error, about 4e-10 of
+||C||, is far below every other form's and is measured against FP64 where
+FP64 is timed), next to the method's truncation error, estimated as
+||C_ref(tau) - C_ref(tau / 100)||_F (the error of C at tau against a product
+a hundred times more accurate; no exact product is formed, so the grid
+reaches the largest served sizes).  FP64 is timed where its expected time is
+short and otherwise estimated from its measured rate (kept products per
+second).  A form is admissible at a point when its arithmetic error does not
+exceed the truncation error there (the error of the result is then still
+dominated by the method's own approximation); the fastest admissible
+candidate wins.  Each candidate's measured work rate (kept products per ms
+for FP64, quad steps per ms for the tensor forms) is kept too: the server
+sizes its launches from it (the slice schedule).
 
 `choose` maps a request to the winner of the nearest calibrated point
 (distance in log2 n, alpha, log10 tau).  It depends only on the request and
@@ -27,7 +37,9 @@ import time
 from dataclasses import dataclass
 from typing import Iterable, List, Optional, Sequence
 
-CANDIDATES = (("fp64", 32), ("fp64", 64), ("fp64", 128), ("bf16_split", 64), ("fp16_scaled", 64))
+CANDIDATES = (("fp64", 32), ("fp64", 64), ("fp64", 128), ("bf16_split", 64), ("bf16_split", 128),
+              ("bf16_split4", 64), ("bf16_split4", 128), ("fp16_scaled", 64), ("fp16_scaled", 128))
+FP64_TIMED_MAX_S = 3.0  # FP64 is timed where it is expected to take less than this
 TABLE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 
@@ -43,9 +55,14 @@ class Point:
     alpha: float
     tau: float
     choice: Choice
-    ms: dict          # candidate "prec/bs" -> measured milliseconds
-    arith_err: dict   # tensor candidate -> ||C_form - C_fp64||_F
-    trunc_err: float  # ||AB - C_fp64||_F
+    ms: dict          # candidate "prec/bs" -> milliseconds (measured, or estimated for long FP64 runs)
+    arith_err: dict   # tensor candidate -> ||C_form - C_ref||_F
+    trunc_err: float  # ||AB - C||_F estimate, or a dict per leaf size
+    rate: dict = None       # candidate -> work per ms (kept products or quad steps)
+    estimated: tuple = ()   # candidates whose ms is estimated from a rate
+
+    def trunc(self, bs: int) -> float:
+        return self.trunc_err.get(str(bs), math.inf) if isinstance(self.trunc_err, dict) else self.trunc_err
 
     def key(self):
         return (math.log2(self.n), self.alpha, math.log10(self.tau))
@@ -55,14 +72,16 @@ def _name(prec: str, bs: int) -> str:
     return f"{prec}/{bs}"
 
 
-def decide(ms: dict, arith_err: dict, trunc_err: float) -> Choice:
-    """Fastest candidate whose arithmetic error is within the truncation error."""
+def decide(ms: dict, arith_err: dict, trunc_err) -> Choice:
+    """Fastest candidate whose arithmetic error is within the truncation error
+    (trunc_err: one number, or a dict by leaf size)."""
     best = None
     for prec, bs in CANDIDATES:
         k = _name(prec, bs)
         if k not in ms:
             continue
-        if prec != "fp64" and not (arith_err.get(k, math.inf) <= trunc_err):
+        t = trunc_err.get(str(bs), math.inf) if isinstance(trunc_err, dict) else trunc_err
+        if prec != "fp64" and not (arith_err.get(k, math.inf) <= t):
             continue
         if best is None or ms[k] < ms[best]:
             best = k
@@ -97,57 +116,106 @@ class Autotuner:
         ms = {k: v for k, v in p.ms.items() if int(k.split("/")[1]) == bs}
         return decide(ms, p.arith_err, p.trunc_err) if ms else default
 
+    def rate(self, prec: str, bs: int) -> Optional[float]:
+        """Median measured work rate (per ms) of a candidate over the table, or None."""
+        v = sorted(p.rate[_name(prec, bs)] for p in self.points if p.rate and _name(prec, bs) in p.rate)
+        return v[len(v) // 2] if v else None
+
 
 def load(path: str = TABLE_PATH) -> List[Point]:
     d = json.load(open(path))
     return [Point(p["n"], p["alpha"], p["tau"], Choice(p["choice"]["prec"], p["choice"]["bs"]), p["ms"],
-                  p["arith_err"], p["trunc_err"]) for p in d["points"]]
+                  p["arith_err"], p["trunc_err"], p.get("rate"), tuple(p.get("estimated", ())))
+            for p in d["points"]]
 
 
 def save(points: Iterable[Point], path: str = TABLE_PATH, meta: Optional[dict] = None):
     out = {"meta": meta or {}, "points": [
         {"n": p.n, "alpha": p.alpha, "tau": p.tau, "choice": {"prec": p.choice.prec, "bs": p.choice.bs},
-         "ms": p.ms, "arith_err": p.arith_err, "trunc_err": p.trunc_err} for p in points]}
+         "ms": p.ms, "arith_err": p.arith_err, "trunc_err": p.trunc_err, "rate": p.rate,
+         "estimated": list(p.estimated)} for p in points]}
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
 
 
-def calibrate(S, ctx, grid: Iterable[tuple], repeats: int = 3, mode: str = "combined") -> List[Point]:
-    """Measure every candidate at each (n, alpha, tau) of `grid` on the 3-D
+def calibrate(S, ctx, grid: Iterable[tuple], repeats: int = 2, mode: str = "combined",
+              log=None) -> List[Point]:
+    """Measure the candidates at each (n, alpha, tau) of `grid` on the 3-D
     lattice generator (seeds 1 and 2).  S: the libspamm binding module."""
     import synth
     pts = []
+    fp64_rate = {}  # leaf size -> measured kept products per second
     for n, alpha, tau in grid:
         pa, pb = synth.lattice_3d(n, alpha=alpha, seed=1), synth.lattice_3d(n, alpha=alpha, seed=2)
-        ms, res = {}, {}
-        for bs in sorted({b for _, b in CANDIDATES}):
-            GA, GB = S.spamm_generate(ctx, pa, bs), S.spamm_generate(ctx, pb, bs)
-            for prec, cbs in CANDIDATES:
-                if cbs != bs:
-                    continue
-                times = []
-                for _ in range(repeats + 1):  # the first run warms up
-                    t0 = time.perf_counter()
-                    C = S.spamm_multiply(ctx, GA, GB, tau, mode, prec)
-                    times.append(time.perf_counter() - t0)
-                    if len(times) <= repeats:
-                        C.close()
-                ms[_name(prec, bs)] = 1e3 * sorted(times[1:])[len(times[1:]) // 2]
-                if bs == 64:
-                    res[prec] = C
-                else:
-                    C.close()
-            if bs == 64:
-                X = S.spamm_multiply(ctx, GA, GB, 0.0, "spamm", "fp64")
-                trunc = S.spamm_error(ctx, X, res["fp64"])
-                arith = {_name(p, 64): S.spamm_error(ctx, res["fp64"], res[p]) for p in res if p != "fp64"}
-                X.close()
-                for C in res.values():
-                    C.close()
-            GA.close()
-            GB.close()
-        pts.append(Point(n, alpha, tau, decide(ms, arith, trunc), ms, arith, trunc))
+        ms, arith, trunc, rate, est = {}, {}, {}, {}, []
+        try:
+            _measure_point(S, ctx, pa, pb, tau, mode, repeats, fp64_rate, ms, arith, trunc, rate, est)
+        except S.SpammError as e:
+            if e.status != S.E_OOM:
+                raise
+            if log:
+                log(f"{n} {alpha} {tau}: does not fit ({e})")
+            continue
+        arith = {k: v for k, v in arith.items() if not k.startswith("fp64")}
+        # the reference's error against itself is 0: use its measured error against FP64 where known
+        for bs in {b for _, b in CANDIDATES if _ != "fp64"}:
+            k = _name("bf16_split4", bs)
+            if k + ":vs_fp64" in arith:
+                arith[k] = arith[k + ":vs_fp64"]
+        pt = Point(n, alpha, tau, decide(ms, arith, trunc), ms, arith, trunc, rate, tuple(est))
+        pts.append(pt)
+        if log:
+            log(pt)
     return pts
+
+
+def _measure_point(S, ctx, pa, pb, tau, mode, repeats, fp64_rate, ms, arith, trunc, rate, est):
+    """Every candidate at one grid point (inputs truncated while generated at
+    tau / 100, exact for the combined method at tau and at tau / 100)."""
+    for bs in sorted({b for _, b in CANDIDATES}):
+        GA, GB = S.spamm_generate(ctx, pa, bs, tau / 100.0), S.spamm_generate(ctx, pb, bs, tau / 100.0)
+        tensor = [p for p, b in CANDIDATES if b == bs and p != "fp64"]
+        ref = None
+        if tensor:
+            ref, st_ref = S.spamm_multiply(ctx, GA, GB, tau, mode, "bf16_split4", stats=True)
+            fine = S.spamm_multiply(ctx, GA, GB, tau / 100.0, mode, "bf16_split4")
+            trunc[str(bs)] = S.spamm_error(ctx, fine, ref)
+            fine.close()
+        for prec, cbs in CANDIDATES:
+            if cbs != bs:
+                continue
+            k = _name(prec, bs)
+            if prec == "fp64" and bs in fp64_rate:
+                plan = S.spamm_plan_create(ctx, GA, GB, tau, mode, "fp64")
+                nk = plan.info()["n_kept"]
+                plan.close()
+                if nk / fp64_rate[bs] > FP64_TIMED_MAX_S:
+                    ms[k] = 1e3 * nk / fp64_rate[bs]  # too long to time here: estimated from its rate
+                    est.append(k)
+                    continue
+            times, st = [], None
+            for _ in range(repeats + 1):  # the first run warms up
+                t0 = time.perf_counter()
+                C, st = S.spamm_multiply(ctx, GA, GB, tau, mode, prec, stats=True)
+                times.append(time.perf_counter() - t0)
+                if prec == "fp64" and times[-1] > FP64_TIMED_MAX_S:
+                    break
+                if len(times) <= repeats:
+                    C.close()
+            tm = sorted(times[1:])[len(times[1:]) // 2] if len(times) > 1 else times[0]
+            ms[k] = 1e3 * tm
+            rate[k] = st["n_steps"] / st["ms_gemm"] if st["ms_gemm"] > 0 else None
+            if prec == "fp64":
+                fp64_rate[bs] = st["n_kept"] / max(tm, 1e-9)
+            if ref is not None:
+                arith[k] = S.spamm_error(ctx, ref, C) if prec != "fp64" else 0.0
+                if prec == "fp64":  # the reference's own error, where FP64 ran
+                    arith[_name("bf16_split4", bs) + ":vs_fp64"] = S.spamm_error(ctx, C, ref)
+            C.close()
+        if ref is not None:
+            ref.close()
+        GA.close()
+        GB.close()
 
 
 if __name__ == "__main__":
@@ -156,8 +224,8 @@ if __name__ == "__main__":
     import sys
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--n", type=int, nargs="+", default=[4096, 16384])
-    ap.add_argument("--alpha", type=float, nargs="+", default=[0.6, 0.9, 1.2])
+    ap.add_argument("--n", type=int, nargs="+", default=[4096, 16384, 65536, 131072])
+    ap.add_argument("--alpha", type=float, nargs="+", default=[0.6, 1.2])
     ap.add_argument("--tau", type=float, nargs="+", default=[1e-4, 1e-6, 1e-8])
     ap.add_argument("--repeats", type=int, default=2)
     ap.add_argument("--out", default=TABLE_PATH)
@@ -167,9 +235,12 @@ if __name__ == "__main__":
     from paper_1906_08148_gb300 import spamm as S
     c = S.Context(0)
     grid = [(n, al, t) for n in a.n for al in a.alpha for t in a.tau]
-    pts = calibrate(S, c, grid, repeats=a.repeats)
-    save(pts, a.out, meta={"workload": "3-D lattice decay, seeds 1 and 2, combined method",
-                           "candidates": [list(x) for x in CANDIDATES], "repeats": a.repeats})
-    for p in pts:
+    def log(p):
         print(p.n, p.alpha, p.tau, p.choice, {k: round(v, 2) for k, v in p.ms.items()},
-              {k: "%.2e" % v for k, v in p.arith_err.items()}, "%.2e" % p.trunc_err)
+              {k: "%.2e" % v for k, v in p.arith_err.items()}, p.trunc_err, flush=True)
+
+    pts = calibrate(S, c, grid, repeats=a.repeats, log=log)
+    save(pts, a.out, meta={"workload": "3-D lattice decay, seeds 1 and 2, combined method",
+                           "candidates": [list(x) for x in CANDIDATES], "repeats": a.repeats,
+                           "truncation_error": "||C_ref(tau) - C_ref(tau/100)||_F, C_ref the 4-slice split",
+                           "fp64_timed_max_s": FP64_TIMED_MAX_S})

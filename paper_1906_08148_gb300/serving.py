@@ -270,6 +270,17 @@ class Server:
     def _key(r: Request):
         return (r.prec, r.stats.get("bs"))
 
+    def _first_rate(self, prec: str, bs) -> float:
+        """Work rate before any launch of a form and leaf size was measured:
+        the given guess for "prec/bs" or "prec"; an FP64 unit (a leaf
+        product) scales with bs^3, a tensor-form unit (a 128 x 128 x 64 quad
+        step) does not."""
+        bs = bs or 64
+        if f"{prec}/{bs}" in self._rate_guess:
+            return self._rate_guess[f"{prec}/{bs}"]
+        base = self._rate_guess.get(prec, 2400.0)
+        return base * (64.0 / bs) ** 3 if prec == "fp64" else base
+
     def _complete(self, r: Request, C, st: dict, err: Optional[str]):
         with self._lock:
             self._charge(-r.footprint)
@@ -308,7 +319,7 @@ class Server:
             key = keys[turn % len(keys)]
             turn += 1
             group = [r for r in active if self._key(r) == key][:self.max_batch]
-            rate = self._rate.get(key, self._rate_guess.get(key[0], 2400.0) * (64.0 / (key[1] or 64)) ** 3)
+            rate = self._rate.get(key, self._first_rate(*key))
             budget = max(1.0, rate * self.slice_ms / len(group))
             before = [self.backend.work(r.job)[1] for r in group]
             t_launch = self.now()

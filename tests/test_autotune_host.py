@@ -50,3 +50,23 @@ def test_table_round_trip(tmp_path):
     back = autotune.load(path)
     assert back[0].choice == Choice("bf16_split", 64) and math.isclose(back[0].trunc_err, 2e-6)
     assert Autotuner(path=path).choose(4096, 0.6, 1e-6) == Choice("bf16_split", 64)
+
+
+def test_truncation_error_per_leaf_size_and_rates(tmp_path):
+    """The truncation error differs by leaf size (the kept set does): each
+    candidate is judged against its own; rates round-trip and their median
+    is what the server's slices are sized from."""
+    from paper_1906_08148_gb300 import autotune
+    ms = {"fp64/64": 30.0, "fp64/128": 35.0, "bf16_split4/64": 3.0, "bf16_split4/128": 2.5}
+    arith = {"bf16_split4/64": 1e-8, "bf16_split4/128": 1e-8}
+    # the 128 kept set keeps more, its truncation error is below the form's arithmetic error
+    assert decide(ms, arith, {"64": 1e-6, "128": 5e-9}) == Choice("bf16_split4", 64)
+    assert decide(ms, arith, {"64": 1e-6, "128": 1e-6}) == Choice("bf16_split4", 128)
+    pts = [Point(4096, 1.0, 1e-6, decide(ms, arith, {"64": 1e-6, "128": 1e-6}), ms, arith, {"64": 1e-6, "128": 1e-6},
+                 {"bf16_split4/64": 50000.0 + 1000 * i}, ("fp64/128",)) for i in range(3)]
+    path = str(tmp_path / "t.json")
+    autotune.save(pts, path)
+    t = Autotuner(path=path)
+    assert t.choose(4096, 1.0, 1e-6) == Choice("bf16_split4", 128)
+    assert t.rate("bf16_split4", 64) == 51000.0 and t.rate("fp16_scaled", 64) is None
+    assert autotune.load(path)[0].estimated == ("fp64/128",)

@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 import synth
+import tcbound
 from oracle import sampled
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -35,12 +36,25 @@ def setup(S):
 
 
 def _window_check(S, ctx, C, ref, rel_tol, bound=None):
+    """Window leaves against the oracle: relative Frobenius error within
+    rel_tol, and, for a tensor form, every element within the bound derived
+    from its arithmetic (tcbound.py)."""
     gpu, found = S.spamm_gather_leaves(ctx, C, ref.bi, ref.bj)
     assert found.all(), "an oracle leaf is missing on the GPU"
     num = float(np.sum((gpu - ref.data) ** 2))
     den = float(np.sum(ref.data ** 2))
     assert np.sqrt(num) <= rel_tol * np.sqrt(den), (np.sqrt(num / den))
+    if bound is not None:
+        assert np.all(np.abs(gpu - ref.data) <= bound)
     return np.sqrt(num / den)
+
+
+def _tc_bound(prec, A_rows, B_cols, tau, ikj, ref):
+    return tcbound.bound(prec, oracle.truncate_block(A_rows, tau), oracle.truncate_block(B_cols, tau), ikj, ref)
+
+
+# relative errors of the forms on these workloads (n = 4096 lattice: 1.5e-7, 3.6e-10, 1.8e-7), with room
+REL = {"bf16_split": 1e-6, "bf16_split4": 3e-9, "fp16_scaled": 1e-6}
 
 
 @pytest.mark.parametrize("mode,tau", [("combined", 1e-6), ("spamm", 1e-6), ("truncate", 1e-4)])
@@ -64,7 +78,7 @@ def test_fullsize_fp64_window(S, setup, mode, tau):
           f"borderline {st['n_borderline']} ms_gemm {st['ms_gemm']:.1f}")
 
 
-@pytest.mark.parametrize("prec", ["bf16_split", "fp16_scaled"])
+@pytest.mark.parametrize("prec", ["bf16_split", "bf16_split4", "fp16_scaled"])
 def test_fullsize_tensor_window(S, setup, prec):
     ctx, pa, pb, GA, GB = setup
     tau = 1e-6
@@ -72,7 +86,7 @@ def test_fullsize_tensor_window(S, setup, prec):
     w = 10
     A_rows, B_cols = sampled.window_inputs(pa, pb, BS, range(w), range(w))
     ref, ikj = sampled.window_product(A_rows, B_cols, tau, oracle.COMBINED)
-    rel = _window_check(S, ctx, C, ref, 1e-4)
+    rel = _window_check(S, ctx, C, ref, REL[prec], _tc_bound(prec, A_rows, B_cols, tau, ikj, ref))
     print(f"{prec} combined tau={tau}: window rel error vs FP64 oracle {rel:.2e}")
 
 
@@ -95,7 +109,7 @@ def test_fullsize_scattered_leaves(S, setup):
             assert np.linalg.norm(g[0] - ref.data[0]) <= 1e-12 * np.linalg.norm(ref.data[0])
 
 
-@pytest.mark.parametrize("prec", ["bf16_split", "fp16_scaled"])
+@pytest.mark.parametrize("prec", ["bf16_split", "bf16_split4", "fp16_scaled"])
 def test_precision_form_config_262144(S, prec):
     """The precision-form configuration: 64 x 64 x 64 lattice (n = 262144),
     alpha = 0.8, combined tau = 1e-5.  Inputs are generated with the block
@@ -115,8 +129,8 @@ def test_precision_form_config_262144(S, prec):
     plan.close()
     w = 6
     A_rows, B_cols = sampled.window_inputs(pa, pb, BS, range(w), range(w))
-    ref, _ = sampled.window_product(A_rows, B_cols, tau, oracle.COMBINED)
-    rel = _window_check(S, ctx, C, ref, 1e-5)
+    ref, ikj = sampled.window_product(A_rows, B_cols, tau, oracle.COMBINED)
+    rel = _window_check(S, ctx, C, ref, REL[prec], _tc_bound(prec, A_rows, B_cols, tau, ikj, ref))
     print(f"{prec} n={n} alpha={alpha} tau={tau}: A {na} B {nb} leaves, kept {st['n_kept']}, "
           f"C leaves {st['n_c_leaves']}, ms_gemm {st['ms_gemm']:.1f}, window rel error vs FP64 oracle {rel:.2e}")
     C.close()
