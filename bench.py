@@ -21,6 +21,7 @@ this method has) on a bounded window of the same workload.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -70,7 +71,7 @@ def parse_args():
     ap.add_argument("--pc-samples", type=int, default=256,
                     help="output leaves compared between each form and FP64 (precision-form configuration)")
     ap.add_argument("--pc-no-fp64", action="store_true", help="precision-form configuration without the FP64 runs")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -100,12 +101,20 @@ def parse_args():
     ap.add_argument("--chain-tau", type=float, default=1e-6)
     ap.add_argument("--chain-steps", type=int, default=20)
     ap.add_argument("--chain-precs", nargs="+", default=["fp64", "fp16_scaled"])
-    ap.add_argument("--sp2", action="store_true", help="SP2 purification chain")
-    ap.add_argument("--sp2-n", type=int, default=8192)
+    ap.add_argument("--sp2", action="store_true", help="SP2 purification chain (gapped two-sublattice insulator)")
+    ap.add_argument("--sp2-n", type=int, nargs="+", default=[1048576, 524288, 262144, 131072],
+                    help="lattice sizes, tried from the largest: the chain runs at the largest one admitted")
     ap.add_argument("--sp2-alpha", type=float, default=1.0)
+    ap.add_argument("--sp2-delta", type=float, default=6.0, help="on-site term +-delta (opens the gap)")
     ap.add_argument("--sp2-tau", type=float, default=1e-6)
-    ap.add_argument("--sp2-iters", type=int, default=40)
-    ap.add_argument("--sp2-tol", type=float, default=1e-6)
+    ap.add_argument("--sp2-iters", type=int, default=20)
+    ap.add_argument("--sp2-tol", type=float, default=0.0)
+    ap.add_argument("--sp2-fp64-iters", type=int, default=2,
+                    help="FP64 products of the chain timed (the rest of the FP64 chain is not run)")
+    ap.add_argument("--sp2-probe-every", type=int, default=5)
+    ap.add_argument("--sp2-probe-rows", type=int, default=4)
+    ap.add_argument("--sp2-budget", type=float, default=0.9, help="fraction of free device memory admitted")
+    ap.add_argument("--sp2-force", action="store_true", help="run every size without the footprint estimate")
     ap.add_argument("--passes", action="store_true",
                     help="bandwidth of the norm pass and the task-list pass on the bench workload")
     ap.add_argument("--mp-n", type=int, default=40000)
@@ -588,12 +597,75 @@ def run_chain(args):
     print(json.dumps(out), flush=True)
 
 
+SP2_GROWTH = 2.0   # state leaves of the converged projector / leaves of X0
+SP2_PEAK = 6.0     # peak device bytes / (state leaves x 8 bs^2)
+
+
+def sp2_estimate(p, bs, delta, tau, rows=16):
+    """Leaves of X0 = (bI - F) / (2b) before any allocation: the generator's
+    leaves of block rows sampled evenly over the matrix whose norm / (2b)
+    reaches tau, plus the diagonal leaf, scaled to all block rows; and the
+    chain's estimated peak device footprint (the state grows by SP2_GROWTH
+    towards the projector; a product holds the previous state, its
+    untruncated square and, on the 2X - X^2 branch, the sum: SP2_PEAK times
+    the state)."""
+    import numpy as np
+
+    import synth
+    b = delta + synth.spectral_bound(p)
+    thr = 2.0 * b * tau
+    nb = -(-p.n // bs)
+    cols = np.arange(nb)
+    counts = []
+    for r in np.linspace(0, nb - 1, min(rows, nb)).astype(np.int64):
+        bnd = synth.leaf_bounds_row(p, bs, int(r), cols)
+        cand = cols[bs * bnd >= thr]
+        d = synth.leaves(p, bs, np.full(len(cand), r), cand)
+        nrm = np.sqrt(np.sum(d * d, axis=(1, 2)))
+        counts.append(int(np.count_nonzero((nrm >= thr) | (cand == r))))
+    leaves = float(np.mean(counts)) * nb
+    peak = leaves * SP2_GROWTH * SP2_PEAK * 8 * bs * bs
+    return {"x0_leaves_est": int(leaves), "peak_bytes_est": int(peak), "bound": b, "v_threshold": thr}
+
+
+def sp2_probe_rows(S, ctx, X, X2, rows, tau, n, bs):
+    """Block rows `rows` of the product X X three ways, all on the device:
+    exact (every non-zero leaf pair, FP64), the method in FP64 (combined at
+    tau) and the chain's own product X2.  Returns the sampled rows' squared
+    norms: ||exact - method||^2, ||method - X2||^2, ||exact||^2."""
+    import numpy as np
+    bi, bj, _, _ = S.spamm_to_blocks(ctx, X, payload=False)
+    sel = np.isin(bi, rows)
+    pay, _ = S.spamm_gather_leaves(ctx, X, bi[sel], bj[sel])
+    XR = S.spamm_from_blocks(ctx, n, bs, bi[sel], bj[sel], pay)
+    E = S.spamm_multiply(ctx, XR, X, 0.0, "spamm", "fp64")
+    M = S.spamm_multiply(ctx, XR, X, tau, "combined", "fp64")
+    ei, ej, _, _ = S.spamm_to_blocks(ctx, E, payload=False)
+    tp, found = S.spamm_gather_leaves(ctx, X2, ei, ej)
+    TR = S.spamm_from_blocks(ctx, n, bs, ei[found], ej[found], tp[found])
+    out = (S.spamm_error(ctx, E, M) ** 2, S.spamm_error(ctx, M, TR) ** 2, S.spamm_frob_norm(ctx, E) ** 2)
+    for m in (XR, E, M, TR):
+        m.close()
+    return out
+
+
 def run_sp2(args):
-    """SP2 purification (second-order spectral projection) of a 3-D lattice
-    decay matrix F to half filling: X0 = (b I - F) / (2 b), b an upper bound
-    of ||F||_2, then X <- X^2 or 2X - X^2 by the trace rule, every product an
-    approximate multiply; per iteration the branch, trace, ||X - X^2||_F,
-    kept products and time, for FP64 leaves and a tensor-core form."""
+    """SP2 purification (second-order spectral projection) of a gapped
+    two-sublattice insulator on the 3-D lattice: F = V + D, V the decay
+    matrix (alpha, seed 1), D the on-site term -+delta by sublattice, n_occ =
+    the -delta sites; X0 = (b I - F) / (2 b) with b = delta + the Gershgorin
+    bound of V, then X <- X^2 or 2X - X^2 by the trace rule, every product an
+    approximate multiply (combined method at tau), the state resident on the
+    device.  The sizes of --sp2-n are tried from the largest: a size whose
+    estimated footprint exceeds the free device memory is refused before
+    anything is allocated (and one that runs out of memory is recorded), the
+    chain runs at the largest admitted size.  Per form and iteration: branch,
+    traces, ||X - X^2||_F, kept products and time, device memory in use;
+    every --sp2-probe-every iterations the sampled-row errors of the product
+    (method against exact, the form against the method in FP64).  FP64 runs
+    --sp2-fp64-iters products, and the tensor form's product after as many
+    iterations is compared with it."""
+    import numpy as np
     import torch
 
     import __graft_entry__
@@ -603,24 +675,103 @@ def run_sp2(args):
     from paper_1906_08148_gb300 import spamm as S
 
     ctx = S.Context(0)
-    p = synth.lattice_3d(args.sp2_n, alpha=args.sp2_alpha, seed=1)
-    bound = synth.spectral_bound(p)
+    bs = 64
     out = {"metric": "SP2 purification chain", "unit": "s", "data": "synthetic",
-           "config": {"workload": "sp2", "n": args.sp2_n, "alpha": args.sp2_alpha, "bs": 64, "tau": args.sp2_tau,
-                      "method": "combined", "n_occ": args.sp2_n // 2, "iterations": args.sp2_iters,
-                      "bound": bound}, "forms": {}}
-    for prec in args.chain_precs:
-        F = S.spamm_generate(ctx, p, 64)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        X, hist = chain.sp2(ctx, F, args.sp2_n // 2, bound, args.sp2_tau, "combined", prec, args.sp2_iters,
-                            tol=args.sp2_tol)
-        torch.cuda.synchronize()
-        secs = time.perf_counter() - t0
-        out["forms"][prec] = {"seconds": secs, "iterations": len(hist), "final_trace": S.spamm_trace(ctx, X),
-                              "final_leaves": X.info()["nleaves"], "history": hist}
-        X.close()
-        F.close()
+           "config": {"workload": "sp2_insulator", "alpha": args.sp2_alpha, "delta": args.sp2_delta, "bs": bs,
+                      "tau": args.sp2_tau, "method": "combined", "iterations": args.sp2_iters,
+                      "fp64_iterations": args.sp2_fp64_iters, "sizes_tried": sorted(args.sp2_n, reverse=True)},
+           "admission": [], "forms": {}}
+    free0, total = torch.cuda.mem_get_info()
+    budget = args.sp2_budget * free0
+    forms = sorted(args.chain_precs, key=lambda q: q != "fp64")  # FP64 first: the forms compare with it
+    for n in sorted(args.sp2_n, reverse=True):
+        p = synth.lattice_3d(n, alpha=args.sp2_alpha, seed=1)
+        est = sp2_estimate(p, bs, args.sp2_delta, args.sp2_tau)
+        rec = {"n": n, **est, "budget_bytes": int(budget)}
+        if est["peak_bytes_est"] > budget and not args.sp2_force:
+            rec["admission"] = "refused (estimated footprint above the free device memory)"
+            out["admission"].append(rec)
+            continue
+        thr = est["v_threshold"]
+        pv = synth.DecayParams(n=n, kind=p.kind, alpha=p.alpha, seed=p.seed)
+        di, dj, dd, n_occ = synth.onsite_blocks(n, bs, args.sp2_delta)
+        nb = -(-n // bs)
+        rows = np.unique(np.linspace(nb // 8, nb - 1 - nb // 8, args.sp2_probe_rows).astype(np.int32))
+
+        def start():
+            V = S.spamm_generate(ctx, pv, bs, thr)
+            D = S.spamm_from_blocks(ctx, n, bs, di, dj, dd)
+            F = S.spamm_add(ctx, 1.0, V, 1.0, D)
+            V.close()
+            D.close()
+            return F
+
+        res, fp64_prod = {}, None
+        try:
+            for prec in forms:
+                iters = args.sp2_fp64_iters if prec == "fp64" else args.sp2_iters
+                F = start()
+                used, keep, probe_s = [], {}, [0.0]
+
+                def probe(it, X, X2, prec=prec, used=used, keep=keep, probe_s=probe_s):
+                    torch.cuda.synchronize()
+                    t_in = time.perf_counter()
+                    f, _ = torch.cuda.mem_get_info()
+                    used.append(total - f)
+                    d = {"device_bytes_in_use": int(total - f), "x_leaves": X.info()["nleaves"],
+                         "product_leaves": X2.info()["nleaves"]}
+                    if prec != "fp64" and fp64_prod is not None and it == args.sp2_fp64_iters - 1:
+                        ref = S.spamm_frob_norm(ctx, fp64_prod)
+                        d["diff_vs_fp64_chain"] = S.spamm_error(ctx, fp64_prod, X2) / ref
+                    if prec == "fp64" and it == iters - 1:
+                        keep["prod"] = S.spamm_add(ctx, 1.0, X2, 0.0, X2)
+                    if args.sp2_probe_every and (it % args.sp2_probe_every == 0 or it == iters - 1):
+                        ea, ef, ex = sp2_probe_rows(S, ctx, X, X2, rows, args.sp2_tau, n, bs)
+                        d["sampled_rows"] = rows.tolist()
+                        d["sampled_error_vs_exact"] = float(np.sqrt(ea / ex))
+                        d["sampled_form_vs_fp64_method"] = float(np.sqrt(ef / ex))
+                    torch.cuda.synchronize()
+                    probe_s[0] += time.perf_counter() - t_in
+                    return d
+
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                X, hist = chain.sp2(ctx, F, n_occ, est["bound"], args.sp2_tau, "combined", prec, iters,
+                                    tol=args.sp2_tol, probe=probe)
+                torch.cuda.synchronize()
+                secs = time.perf_counter() - t0 - probe_s[0]
+                flops = sum(h["kept_flops"] for h in hist)
+                gemm_s = sum(h["ms_gemm"] for h in hist) / 1e3
+                res[prec] = {"seconds": secs, "probe_seconds": probe_s[0], "iterations": len(hist),
+                             "kept_flops": flops,
+                             "kept_gflops_gemm": flops / gemm_s / 1e9 if gemm_s > 0 else None,
+                             "final_trace": S.spamm_trace(ctx, X), "n_occ": n_occ,
+                             "final_leaves": X.info()["nleaves"], "peak_device_bytes_sampled": max(used),
+                             "note": "seconds: the chain (products, adds, traces, ||X - X^2||_F), probes excluded",
+                             "history": hist}
+                if "prod" in keep:
+                    fp64_prod = keep["prod"]
+                X.close()
+                F.close()
+        except S.SpammError as e:
+            if e.status != S.E_OOM:
+                raise
+            rec["admission"] = "admitted; ran out of device memory (%s)" % str(e)[:160]
+            rec["partial"] = {k: {kk: v[kk] for kk in ("seconds", "iterations")} for k, v in res.items()}
+            out["admission"].append(rec)
+            res, fp64_prod = None, None
+            gc.collect()
+            S.spamm_trim(ctx)
+            continue
+        rec["admission"] = "admitted"
+        out["admission"].append(rec)
+        out["config"]["n"] = n
+        out["config"]["n_occ"] = n_occ
+        out["config"]["bound"] = est["bound"]
+        out["forms"] = res
+        if fp64_prod is not None:
+            fp64_prod.close()
+        break
     print(json.dumps(out), flush=True)
 
 
@@ -1082,11 +1233,14 @@ def run_e2e(S, ctx, GA, GB, args, bs, torch, np):
     hC = None
     times, flops, h2d, d2h = [], 0.0, 0, 0
     phase = {"from_blocks_s": 0.0, "multiply_s": 0.0, "to_blocks_s": 0.0}
+    per_step = []
     n = ia["n"]
     for it in range(args.e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         A = S.spamm_from_blocks(ctx, n, bs, hA[0], hA[1], hA[2])
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
         B = A if hB is hA else S.spamm_from_blocks(ctx, n, bs, hB[0], hB[1], hB[2])
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -1111,6 +1265,8 @@ def run_e2e(S, ctx, GA, GB, args, bs, torch, np):
         times.append(t3 - t0)
         for k, v in zip(phase, (t1 - t0, t2 - t1, t3 - t2)):
             phase[k] += v
+        per_step.append({"from_blocks_A_s": ta - t0, "from_blocks_B_s": t1 - ta, "multiply_s": t2 - t1,
+                         "to_blocks_s": t3 - t2})
         flops += st["kept_flops"]
         h2d = hA[2].nbytes + 8 * len(hA[0]) + (0 if hB is hA else hB[2].nbytes + 8 * len(hB[0]))
         d2h = 8 * nc * e + 16 * nc
@@ -1118,7 +1274,7 @@ def run_e2e(S, ctx, GA, GB, args, bs, torch, np):
             m.close()
     return {"value": flops / sum(times) / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": len(times), "ms_per_step": 1e3 * sum(times) / len(times),
-            "phases_s_per_step": {k: v / len(times) for k, v in phase.items()}}
+            "phases_s_per_step": {k: v / len(times) for k, v in phase.items()}, "per_step": per_step}
 
 
 if __name__ == "__main__":

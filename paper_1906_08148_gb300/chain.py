@@ -34,16 +34,23 @@ def square_chain(ctx, X0, steps: int, tau: float, mode: str = "combined", prec: 
 
 
 def sp2(ctx, F, n_occ: float, bound: float, tau: float, mode: str = "combined", prec: str = "fp64",
-        iters: int = 40, tol: float = 0.0):
+        iters: int = 40, tol: float = 0.0, X0=None, probe=None):
     """Returns (X, per-step history: traces of X and X^2, branch, ||X - X^2||_F,
-    kept products).  Stops early once ||X - X^2||_F <= tol."""
-    info = F.info()
-    I = S.spamm_identity(ctx, info["n"], info["bs"])
-    X = S.spamm_add(ctx, -0.5 / bound, F, 0.5, I)
-    I.close()
+    kept products).  Stops early once ||X - X^2||_F <= tol.  X0: start from
+    this matrix (released as the chain moves on) instead of (bI - F) / (2b).
+    probe(step, X, X2): called after each product, its dict (if any) is
+    added to that step's history."""
+    if X0 is None:
+        info = F.info()
+        I = S.spamm_identity(ctx, info["n"], info["bs"])
+        X = S.spamm_add(ctx, -0.5 / bound, F, 0.5, I)
+        I.close()
+    else:
+        X = X0
     hist = []
-    for _ in range(iters):
+    for it in range(iters):
         X2, st = S.spamm_multiply(ctx, X, X, tau, mode, prec, stats=True)
+        extra = probe(it, X, X2) if probe is not None else None
         t1, t2 = S.spamm_trace(ctx, X), S.spamm_trace(ctx, X2)
         idem = S.spamm_error(ctx, X, X2)
         if abs(t2 - n_occ) < abs(2.0 * t1 - t2 - n_occ):
@@ -55,6 +62,8 @@ def sp2(ctx, F, n_occ: float, bound: float, tau: float, mode: str = "combined", 
         X = Xn
         hist.append({"trace": t1, "trace_sq": t2, "branch": branch, "idempotency": idem,
                      "n_kept": st["n_kept"], "ms_gemm": st["ms_gemm"], "kept_flops": st["kept_flops"]})
+        if extra:
+            hist[-1].update(extra)
         if tol and idem <= tol:
             break
     return X, hist

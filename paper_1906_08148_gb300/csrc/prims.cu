@@ -40,6 +40,17 @@ BufP alloc_bytes(spamm_ctx ctx, size_t bytes) {
     if (!b->p) fail(SPAMM_E_OOM, "allocator returned NULL for " + std::to_string(rounded) + " bytes");
   } else {
     cudaError_t e = cudaMallocAsync(&b->p, rounded, ctx->stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (e == cudaErrorMemoryAllocation && cudaStreamIsCapturing(ctx->stream, &cap) == cudaSuccess &&
+        cap == cudaStreamCaptureStatusNone) {
+      // the pool keeps freed blocks; hand them back to the device and try once more
+      cudaGetLastError();
+      cudaMemPool_t pool;
+      if (cudaStreamSynchronize(ctx->stream) == cudaSuccess &&
+          cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess &&
+          cudaMemPoolTrimTo(pool, 0) == cudaSuccess)
+        e = cudaMallocAsync(&b->p, rounded, ctx->stream);
+    }
     if (e != cudaSuccess) {
       b->p = nullptr;
       cudaGetLastError();

@@ -198,6 +198,33 @@ def block_sparse(n: int, bs: int, fill: float, seed: int = 1):
     return bi, bj, data
 
 
+def sublattice_parity(n: int) -> np.ndarray:
+    """(x + y + z) mod 2 of the 3-D lattice points 0..n-1 (Morton order, x in
+    bit 0, y in bit 1, z in bit 2 of each coordinate triple): int8 array."""
+    i = np.arange(n, dtype=np.int64)
+    return ((i ^ (i >> 1) ^ (i >> 2)) & 1).astype(np.int8)
+
+
+def onsite_blocks(n: int, bs: int, delta: float):
+    """Diagonal on-site term of a two-sublattice insulator on the 3-D lattice:
+    -delta on the points with x + y + z even, +delta on the odd ones.  Added
+    to a decay matrix V of norm below delta it opens a gap around 0 in the
+    spectrum, so the projector onto the negative eigenvalues (the density
+    matrix at half filling) decays exponentially, as for the insulating
+    systems the paper's purification application treats.
+    Returns (bi, bj, data) of the ceil(n / bs) diagonal leaves, and the count
+    of -delta points (the number of occupied states)."""
+    par = sublattice_parity(n)
+    nb = -(-n // bs)
+    data = np.zeros((nb, bs, bs))
+    diag = np.zeros(nb * bs)
+    diag[:n] = np.where(par == 0, -delta, delta)
+    r = np.arange(bs)
+    data[:, r, r] = diag.reshape(nb, bs)
+    idx = np.arange(nb, dtype=np.int32)
+    return idx, idx.copy(), data, int(np.count_nonzero(par == 0))
+
+
 # The synthetic workloads (sizes and decay of the paper's model problem and
 # of the large chemical systems it stands in for).
 def model_1d(n=2048, alpha=0.05, seed=1) -> DecayParams:

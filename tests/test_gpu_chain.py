@@ -106,3 +106,58 @@ def test_square_chain_matches_oracle(S, ctx, prec):
     assert np.linalg.norm(D - R) <= tol * np.linalg.norm(R), np.linalg.norm(D - R) / np.linalg.norm(R)
     assert gh[0]["n_kept"] == len(oracle.multiply(X0, X0, tau, oracle.COMBINED)[1])
     assert gh[-1]["frob"] == pytest.approx(on[-1], rel=1e-12 if prec == "fp64" else 1e-5)
+
+
+def _insulator(S, ctx, n, delta, tau, bs=64):
+    """F = V + D of the gapped two-sublattice insulator, V generated with its
+    leaves below 2 b tau dropped (X0 = (bI - F) / (2b) then keeps the leaves
+    of norm >= tau); both sides start from the same leaves."""
+    p = synth.lattice_3d(n, alpha=1.0, seed=1)
+    bound = delta + synth.spectral_bound(p)
+    di, dj, dd, n_occ = synth.onsite_blocks(n, bs, delta)
+    V = S.spamm_generate(ctx, p, bs, 2.0 * bound * tau)
+    D = S.spamm_from_blocks(ctx, n, bs, di, dj, dd)
+    GF = S.spamm_add(ctx, 1.0, V, 1.0, D)
+    vi, vj, vd, _ = S.spamm_to_blocks(ctx, V)
+    OF = ochain.add(1.0, oracle.from_leaves(n, bs, vi, vj, vd), 1.0, oracle.from_leaves(n, bs, di, dj, dd))
+    V.close()
+    D.close()
+    return GF, OF, n_occ, bound
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp16_scaled", "bf16_split4"])
+def test_sp2_insulator_matches_oracle(S, ctx, prec):
+    from paper_1906_08148_gb300 import chain
+    n, delta, tau, iters = 2048, 6.0, 1e-7, 12
+    GF, OF, n_occ, bound = _insulator(S, ctx, n, delta, tau)
+    GX, gh = chain.sp2(ctx, GF, n_occ, bound, tau, "combined", prec, iters)
+    OX, oh = ochain.sp2(OF, n_occ, bound, tau, oracle.COMBINED, iters)
+    # before convergence the trace rule is decided by a margin far above any rounding
+    live = [k for k, o in enumerate(oh) if o["idempotency"] > 1e-3]
+    assert len(live) >= 6
+    assert [gh[k]["branch"] for k in live] == [oh[k]["branch"] for k in live]
+    D, R = S.spamm_to_dense(ctx, GX), oracle.to_dense(OX)
+    tol = 1e-12 if prec == "fp64" else (1e-9 if prec == "bf16_split4" else 1e-4)
+    assert np.linalg.norm(D - R) <= tol * np.linalg.norm(R), np.linalg.norm(D - R) / np.linalg.norm(R)
+    assert S.spamm_trace(ctx, GX) == pytest.approx(n_occ, rel=1e-6)
+
+
+def test_sp2_probe_rows_equal_the_oracle_rows(S, ctx):
+    """The bench's sampled-row check of a chain product (exact rows, method
+    rows in FP64, the form's rows) against the oracle's product rows."""
+    import bench
+    n, delta, tau = 2048, 6.0, 1e-7
+    GF, OF, n_occ, bound = _insulator(S, ctx, n, delta, tau)
+    I = S.spamm_identity(ctx, n, 64)
+    GX = S.spamm_add(ctx, -0.5 / bound, GF, 0.5, I)
+    OX = ochain.add(-0.5 / bound, OF, 0.5, ochain.identity(n, 64))
+    GX2 = S.spamm_multiply(ctx, GX, GX, tau, "combined", "fp16_scaled")
+    rows = np.array([3, 17], np.int32)
+    ea, ef, ex = bench.sp2_probe_rows(S, ctx, GX, GX2, rows, tau, n, 64)
+    E = oracle.to_dense(oracle.exact(OX, OX))
+    M = oracle.to_dense(oracle.multiply(OX, OX, tau, oracle.COMBINED)[0])
+    T = S.spamm_to_dense(ctx, GX2)
+    r = np.concatenate([np.arange(64 * i, 64 * i + 64) for i in rows])
+    assert ex == pytest.approx(np.sum(E[r] ** 2), rel=1e-12)
+    assert ea == pytest.approx(np.sum((E[r] - M[r]) ** 2), rel=1e-6, abs=1e-30)
+    assert ef == pytest.approx(np.sum((M[r] - T[r]) ** 2), rel=1e-3, abs=1e-30)

@@ -73,3 +73,23 @@ def test_square_chain_is_the_matrix_power():
     ref = np.linalg.matrix_power(A, 16)
     assert np.linalg.norm(oracle.to_dense(X) - ref) <= 1e-12 * np.linalg.norm(A) ** 16 * 512
     assert norms[-1] == pytest.approx(np.linalg.norm(ref), rel=1e-10)
+
+
+def test_sp2_gapped_insulator_converges_to_the_projector():
+    # two-sublattice on-site term +-delta plus a decay matrix of norm < delta:
+    # the gap lies between the n_occ = #(-delta sites) lowest eigenvalues and the rest
+    n, delta = 512, 4.0
+    p = synth.lattice_3d(n, alpha=1.0, seed=3)
+    bi, bj, dd, n_occ = synth.onsite_blocks(n, 64, delta)
+    D = oracle.to_dense(oracle.from_leaves(n, 64, bi, bj, dd))
+    assert np.array_equal(np.diag(D) < 0, synth.sublattice_parity(n) == 0)
+    F = synth.dense(p) + D
+    w, v = np.linalg.eigh(F)
+    assert w[n_occ] - w[n_occ - 1] > 1.0
+    bound = delta + synth.spectral_bound(p)
+    assert bound >= max(-w[0], w[-1])
+    FL = chain.add(1.0, oracle.from_dense(synth.dense(p), 64), 1.0, oracle.from_leaves(n, 64, bi, bj, dd))
+    X, hist = chain.sp2(FL, n_occ, bound, 0.0, oracle.SPAMM, 60)
+    P = v[:, :n_occ] @ v[:, :n_occ].T
+    assert np.linalg.norm(oracle.to_dense(X) - P) <= 1e-8 * np.sqrt(n_occ)
+    assert chain.trace(X) == pytest.approx(n_occ, abs=1e-8)
