@@ -699,18 +699,24 @@ def run_sp2(args):
         rows = np.unique(np.linspace(nb // 8, nb - 1 - nb // 8, args.sp2_probe_rows).astype(np.int32))
 
         def start():
+            """X0 = (b I - F) / (2 b), F = V + D; F itself is not kept."""
             V = S.spamm_generate(ctx, pv, bs, thr)
             D = S.spamm_from_blocks(ctx, n, bs, di, dj, dd)
             F = S.spamm_add(ctx, 1.0, V, 1.0, D)
             V.close()
             D.close()
-            return F
+            I = S.spamm_identity(ctx, n, bs)
+            X0 = S.spamm_add(ctx, -0.5 / est["bound"], F, 0.5, I)
+            F.close()
+            I.close()
+            return X0
 
         res, fp64_prod = {}, None
         try:
             for prec in forms:
                 iters = args.sp2_fp64_iters if prec == "fp64" else args.sp2_iters
-                F = start()
+                X0 = start()
+                x0_leaves = X0.info()["nleaves"]
                 used, keep, probe_s = [], {}, [0.0]
 
                 def probe(it, X, X2, prec=prec, used=used, keep=keep, probe_s=probe_s):
@@ -736,8 +742,8 @@ def run_sp2(args):
 
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                X, hist = chain.sp2(ctx, F, n_occ, est["bound"], args.sp2_tau, "combined", prec, iters,
-                                    tol=args.sp2_tol, probe=probe)
+                X, hist = chain.sp2(ctx, None, n_occ, est["bound"], args.sp2_tau, "combined", prec, iters,
+                                    tol=args.sp2_tol, X0=X0, probe=probe)
                 torch.cuda.synchronize()
                 secs = time.perf_counter() - t0 - probe_s[0]
                 flops = sum(h["kept_flops"] for h in hist)
@@ -745,14 +751,13 @@ def run_sp2(args):
                 res[prec] = {"seconds": secs, "probe_seconds": probe_s[0], "iterations": len(hist),
                              "kept_flops": flops,
                              "kept_gflops_gemm": flops / gemm_s / 1e9 if gemm_s > 0 else None,
-                             "final_trace": S.spamm_trace(ctx, X), "n_occ": n_occ,
+                             "final_trace": S.spamm_trace(ctx, X), "n_occ": n_occ, "x0_leaves": x0_leaves,
                              "final_leaves": X.info()["nleaves"], "peak_device_bytes_sampled": max(used),
                              "note": "seconds: the chain (products, adds, traces, ||X - X^2||_F), probes excluded",
                              "history": hist}
                 if "prod" in keep:
                     fp64_prod = keep["prod"]
                 X.close()
-                F.close()
         except S.SpammError as e:
             if e.status != S.E_OOM:
                 raise
