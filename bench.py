@@ -76,11 +76,15 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serve", action="store_true", help="served-stream benchmark instead of the single workload")
-    ap.add_argument("--serve-requests", type=int, default=128)
-    ap.add_argument("--serve-inputs", type=int, default=8)
-    ap.add_argument("--serve-nmax", type=int, default=32768)
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-inputs", type=int, default=12)
+    ap.add_argument("--serve-nmax", type=int, default=131072)
     ap.add_argument("--serve-batch", type=int, default=32)
-    ap.add_argument("--serve-alpha", type=float, nargs=2, default=[0.8, 1.2])
+    ap.add_argument("--serve-alpha", type=float, nargs=2, default=[0.6, 1.2])
+    ap.add_argument("--serve-input-frac", type=float, default=0.3,
+                    help="fraction of the free device memory the resident inputs may hold")
+    ap.add_argument("--serve-fp64-prefix", type=int, default=32,
+                    help="first requests of the stream also served all-FP64 for comparison (0: skip)")
     ap.add_argument("--serve-slice-ms", type=float, default=25.0,
                     help="target duration of one launch of the served stream (continuous batching slices)")
     ap.add_argument("--no-forms", action="store_true", help="skip the tensor-form comparison in the bench line")
@@ -331,12 +335,18 @@ def run_reference(args, cfg):
 # ------------------------------------------------------------- served stream
 def run_served(args):
     """Continuous batching: a Poisson stream of combined-method requests on
-    resident 3-D lattice matrices (n log-uniform, alpha uniform, tau from
-    {1e-4, 1e-6, 1e-8}), first all at once (saturated capacity), then at 0.9 x
-    that rate; p50/p99 latency from arrival to completion.  --prec auto: each
-    request's precision form and leaf size from the autotuner (a function of
-    its n, alpha and tau only); otherwise every request in --prec with 64 x 64
-    leaves."""
+    resident 3-D lattice matrices (n log-uniform in [4096, --serve-nmax],
+    alpha uniform in --serve-alpha, tau from {1e-4, 1e-6, 1e-8}), first all at
+    once (saturated capacity), then at 0.9 x that rate; p50/p99 latency from
+    arrival to completion.  --prec auto: each request's precision form and
+    leaf size from the autotuner (a function of its n, alpha and tau only),
+    with the tuner's measured work rates as the server's first slice sizes;
+    otherwise every request in --prec with 64 x 64 leaves.  The input pairs
+    are generated in order until they hold --serve-input-frac of the free
+    device memory; a pair that does not fit is left out and requests are
+    drawn from the resident ones (reported).  The first --serve-fp64-prefix
+    requests of the stream also run all at once in the chosen forms and in
+    FP64 (64 x 64 leaves): requests/s and latency of both."""
     import math
     import random
 
@@ -346,51 +356,100 @@ def run_served(args):
     import synth
     __graft_entry__.build()
     from paper_1906_08148_gb300 import spamm as S
-    from paper_1906_08148_gb300.autotune import Autotuner, Choice
+    from paper_1906_08148_gb300.autotune import CANDIDATES, Autotuner, Choice
     from paper_1906_08148_gb300.serving import Request, Server
 
     rng = random.Random(7)
     data = S.Context(0)
     taus = [1e-4, 1e-6, 1e-8]
     tuner = Autotuner() if args.prec == "auto" else None
+    guess = None
+    if tuner:
+        guess = {f"{p}/{b}": tuner.rate(p, b) for p, b in CANDIDATES if tuner.rate(p, b)}
     specs = []
     for i in range(args.serve_inputs):
         n = int(2 ** rng.uniform(math.log2(4096), math.log2(args.serve_nmax))) // 64 * 64
         alpha = rng.uniform(args.serve_alpha[0], args.serve_alpha[1])
         specs.append((n, alpha))
-    inputs = {}
+    inputs, dropped = {}, []
+    free0, _ = torch.cuda.mem_get_info()
+    input_budget = args.serve_input_frac * free0
 
-    def resident(i, bs):
+    def held():
+        return sum(m.info()["nleaves"] * 8 * m.info()["bs"] ** 2 for pair in inputs.values() for m in pair)
+
+    def make(i, bs):
         # inputs truncated at the smallest tau of the stream while generating
         # (exact for the combined method: the block rule is per leaf)
-        if (i, bs) not in inputs:
-            n, alpha = specs[i]
-            inputs[(i, bs)] = (S.spamm_generate(data, synth.lattice_3d(n, alpha=alpha, seed=2 * i + 1), bs, min(taus)),
-                               S.spamm_generate(data, synth.lattice_3d(n, alpha=alpha, seed=2 * i + 2), bs, min(taus)))
-        return inputs[(i, bs)]
+        n, alpha = specs[i]
+        A = B = None
+        try:
+            A = S.spamm_generate(data, synth.lattice_3d(n, alpha=alpha, seed=2 * i + 1), bs, min(taus))
+            B = S.spamm_generate(data, synth.lattice_3d(n, alpha=alpha, seed=2 * i + 2), bs, min(taus))
+        except S.SpammError as e:
+            if e.status != S.E_OOM:
+                raise
+        pair = (A, B)
+        if B is None or held() + sum(m.info()["nleaves"] * 8 * bs * bs for m in pair) > input_budget:
+            for m in pair:
+                if m is not None:
+                    m.close()
+            return None
+        return pair
 
-    def stream(rate):
+    def choice(i, tau):
+        n, alpha = specs[i]
+        return tuner.choose(n, alpha, tau) if tuner else Choice(args.prec, 64)
+
+    # resident inputs: every leaf size the stream's requests on input i ask for
+    live = []
+    for i in range(len(specs)):
+        need = sorted({choice(i, t).bs for t in taus} | ({64} if args.serve_fp64_prefix else set()))
+        got = {}
+        for bs in need:
+            pair = make(i, bs)
+            if pair is None:
+                break
+            got[bs] = pair
+        if len(got) == len(need):
+            inputs.update({(i, bs): pr for bs, pr in got.items()})
+            live.append(i)
+        else:
+            for pr in got.values():
+                for m in pr:
+                    m.close()
+            dropped.append({"n": specs[i][0], "alpha": specs[i][1], "why": "inputs above the resident-input budget"})
+    if not live:
+        print(json.dumps({"metric": "requests/s (served stream)", "unavailable": "no input pair fits"}), flush=True)
+        return
+
+    def stream(rate, forced=None, count=None):
         reqs, t = [], 0.0
         r2 = random.Random(11)
-        for _ in range(args.serve_requests):
+        for _ in range(count or args.serve_requests):
             if rate:
                 t += r2.expovariate(rate)
-            i = r2.randrange(len(specs))
+            i = live[r2.randrange(len(live))]
             tau = r2.choice(taus)
-            n, alpha = specs[i]
-            ch = tuner.choose(n, alpha, tau) if tuner else Choice(args.prec, 64)
-            A, B = resident(i, ch.bs)
+            ch = Choice(forced, 64) if forced else choice(i, tau)
+            A, B = inputs[(i, ch.bs)]
             reqs.append(Request(A, B, tau=tau, mode="combined", prec=ch.prec, arrival=t))
         return reqs
 
     def serve(reqs):
-        srv = Server(max_batch=args.serve_batch, exec_sms=144, slice_ms=args.serve_slice_ms)
+        srv = Server(max_batch=args.serve_batch, exec_sms=144, slice_ms=args.serve_slice_ms, rate_guess=guess,
+                     keep_results=False)
         srv.start()
         ids = [srv.submit(r) for r in reqs]
         for i in ids:
-            srv.wait(i, timeout=3600)
+            srv.wait(i, timeout=7200)
         srv.stop()
-        return srv.summary()
+        out = srv.summary()
+        for r in reqs:
+            if r.result is not None:
+                r.result.close()
+                r.result = None
+        return out
 
     first = stream(0.0)
     torch.cuda.synchronize()
@@ -398,18 +457,26 @@ def run_served(args):
     for r in first:
         k = f"{r.prec}/{r.A.info()['bs']}"
         forms[k] = forms.get(k, 0) + 1
-    serve(first[: min(8, args.serve_requests)])  # warm-up
+    del first
+    serve(stream(0.0, count=min(8, args.serve_requests)))  # warm-up
     sat = serve(stream(0.0))
     cap = sat["requests_per_s"]
     load = serve(stream(0.9 * cap))
+    prefix = None
+    if args.serve_fp64_prefix:
+        k = min(args.serve_fp64_prefix, args.serve_requests)
+        prefix = {"requests": k, "arrivals": "all at t = 0 (the stream's first requests)",
+                  "chosen_forms": serve(stream(0.0, count=k)), "fp64": serve(stream(0.0, forced="fp64", count=k))}
     line = {"metric": "requests/s (served stream)", "value": load["requests_per_s"], "unit": "req/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": args.prec, "data": "synthetic",
             "config": {"workload": "served_stream", "requests": args.serve_requests, "inputs": args.serve_inputs,
-                       "n_range": [4096, args.serve_nmax], "alpha": list(args.serve_alpha), "tau": taus,
-                       "method": "combined", "forms": forms, "arrivals": "Poisson at 0.9 x saturated capacity",
-                       "slice_ms": args.serve_slice_ms},
+                       "resident_inputs": [{"n": specs[i][0], "alpha": specs[i][1]} for i in live],
+                       "dropped_inputs": dropped, "n_range": [4096, args.serve_nmax],
+                       "alpha": list(args.serve_alpha), "tau": taus, "method": "combined", "forms": forms,
+                       "arrivals": "Poisson at 0.9 x saturated capacity", "slice_ms": args.serve_slice_ms,
+                       "rate_guess": guess},
             "saturated": sat, "loaded": load, "p50_s": load["p50_s"], "p99_s": load["p99_s"],
-            "kept_gflops": load["kept_gflops"]}
+            "kept_gflops": load["kept_gflops"], "prefix_vs_fp64": prefix}
     print(json.dumps(line), flush=True)
 
 

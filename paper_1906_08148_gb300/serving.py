@@ -126,13 +126,15 @@ class SpammBackend:
 
 class Server:
     def __init__(self, backend=None, hbm_budget: Optional[int] = None, max_batch: int = 64, device: int = 0,
-                 exec_sms: Optional[int] = None, slice_ms: float = 25.0, rate_guess: Optional[dict] = None):
+                 exec_sms: Optional[int] = None, slice_ms: float = 25.0, rate_guess: Optional[dict] = None,
+                 keep_results: bool = True):
         self.backend = backend if backend is not None else SpammBackend(device, exec_sms)
         if hbm_budget is None:
             hbm_budget = int(0.8 * getattr(self.backend, "free_bytes", 1 << 40))
         self.budget = int(hbm_budget)
         self.max_batch = max_batch
         self.slice_ms = float(slice_ms)
+        self.keep_results = keep_results  # False: a product is released once its statistics are taken
         self.in_use = 0            # bytes charged: requests being planned, planned and running
         self.peak_in_use = 0
         self.requests = {}
@@ -282,6 +284,9 @@ class Server:
         return base * (64.0 / bs) ** 3 if prec == "fp64" else base
 
     def _complete(self, r: Request, C, st: dict, err: Optional[str]):
+        if C is not None and not self.keep_results:
+            C.close()
+            C = None
         with self._lock:
             self._charge(-r.footprint)
             r.result, r.t_done = C, self.now()

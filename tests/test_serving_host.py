@@ -150,3 +150,24 @@ def test_requests_wait_for_their_arrival_time():
     srv, _, ids = _serve(reqs, budget=100)
     r = srv.requests[ids[0]]
     assert r.t_planned >= 0.15 and r.latency > 0
+
+
+def test_results_released_on_completion_when_not_kept():
+    closed = []
+
+    class Result:
+        def __init__(self, rid):
+            self.rid = rid
+
+        def close(self):
+            closed.append(self.rid)
+
+    class Releasing(FakeBackend):
+        def finish(self, job):
+            return Result(job["rid"]), {"kept_flops": 1e9}
+
+    reqs = [Request(A=100, B=20, tau=1e-6, prec="fp64", arrival=0.0) for _ in range(6)]
+    srv, fb, ids = _serve(reqs, 10_000, backend=Releasing(), keep_results=False)
+    assert sorted(closed) == sorted(ids)
+    assert all(srv.requests[i].state == "done" and srv.requests[i].result is None for i in ids)
+    assert srv.summary()["done"] == 6
