@@ -113,8 +113,8 @@ def parse_args():
     ap.add_argument("--sp2-tau", type=float, default=1e-6)
     ap.add_argument("--sp2-iters", type=int, default=20)
     ap.add_argument("--sp2-tol", type=float, default=0.0)
-    ap.add_argument("--sp2-fp64-iters", type=int, default=2,
-                    help="FP64 products of the chain timed (the rest of the FP64 chain is not run)")
+    ap.add_argument("--sp2-fp64-iters", type=int, default=None,
+                    help="iterations of the FP64 chain (default: as many as the tensor forms run)")
     ap.add_argument("--sp2-probe-every", type=int, default=5)
     ap.add_argument("--sp2-probe-rows", type=int, default=4)
     ap.add_argument("--sp2-budget", type=float, default=0.9, help="fraction of free device memory admitted")
@@ -664,18 +664,18 @@ def run_chain(args):
     print(json.dumps(out), flush=True)
 
 
-SP2_GROWTH = 2.0   # state leaves of the converged projector / leaves of X0
-SP2_PEAK = 6.0     # peak device bytes / (state leaves x 8 bs^2)
+SP2_GROWTH = 1.75  # state leaves of the converged projector / leaves of X0 (1.71 measured at n = 262144)
+SP2_PEAK = 3.7     # peak device bytes / (state leaves x 8 bs^2) (3.6 measured at n = 262144, FP16 form)
 
 
-def sp2_estimate(p, bs, delta, tau, rows=16):
+def sp2_estimate(p, bs, delta, tau, rows=16, held=0):
     """Leaves of X0 = (bI - F) / (2b) before any allocation: the generator's
     leaves of block rows sampled evenly over the matrix whose norm / (2b)
     reaches tau, plus the diagonal leaf, scaled to all block rows; and the
     chain's estimated peak device footprint (the state grows by SP2_GROWTH
     towards the projector; a product holds the previous state, its
     untruncated square and, on the 2X - X^2 branch, the sum: SP2_PEAK times
-    the state)."""
+    the state; `held` more states kept meanwhile)."""
     import numpy as np
 
     import synth
@@ -691,7 +691,7 @@ def sp2_estimate(p, bs, delta, tau, rows=16):
         nrm = np.sqrt(np.sum(d * d, axis=(1, 2)))
         counts.append(int(np.count_nonzero((nrm >= thr) | (cand == r))))
     leaves = float(np.mean(counts)) * nb
-    peak = leaves * SP2_GROWTH * SP2_PEAK * 8 * bs * bs
+    peak = leaves * SP2_GROWTH * (SP2_PEAK + held) * 8 * bs * bs
     return {"x0_leaves_est": int(leaves), "peak_bytes_est": int(peak), "bound": b, "v_threshold": thr}
 
 
@@ -746,14 +746,18 @@ def run_sp2(args):
     out = {"metric": "SP2 purification chain", "unit": "s", "data": "synthetic",
            "config": {"workload": "sp2_insulator", "alpha": args.sp2_alpha, "delta": args.sp2_delta, "bs": bs,
                       "tau": args.sp2_tau, "method": "combined", "iterations": args.sp2_iters,
-                      "fp64_iterations": args.sp2_fp64_iters, "sizes_tried": sorted(args.sp2_n, reverse=True)},
+                      "sizes_tried": sorted(args.sp2_n, reverse=True)},
            "admission": [], "forms": {}}
     free0, total = torch.cuda.mem_get_info()
     budget = args.sp2_budget * free0
     forms = sorted(args.chain_precs, key=lambda q: q != "fp64")  # FP64 first: the forms compare with it
+    fp64_iters = args.sp2_iters if args.sp2_fp64_iters is None else args.sp2_fp64_iters
+    out["config"]["fp64_iterations"] = fp64_iters
     for n in sorted(args.sp2_n, reverse=True):
         p = synth.lattice_3d(n, alpha=args.sp2_alpha, seed=1)
-        est = sp2_estimate(p, bs, args.sp2_delta, args.sp2_tau)
+        # the FP64 chain's final state is kept while the tensor forms run, to compare with
+        est = sp2_estimate(p, bs, args.sp2_delta, args.sp2_tau,
+                           held=int("fp64" in forms and len(forms) > 1))
         rec = {"n": n, **est, "budget_bytes": int(budget)}
         if est["peak_bytes_est"] > budget and not args.sp2_force:
             rec["admission"] = "refused (estimated footprint above the free device memory)"
@@ -778,10 +782,10 @@ def run_sp2(args):
             I.close()
             return X0
 
-        res, fp64_prod = {}, None
+        res, fp64_prod, fp64_final, fp64_hist = {}, None, None, None
         try:
             for prec in forms:
-                iters = args.sp2_fp64_iters if prec == "fp64" else args.sp2_iters
+                iters = fp64_iters if prec == "fp64" else args.sp2_iters
                 X0 = start()
                 x0_leaves = X0.info()["nleaves"]
                 used, keep, probe_s = [], {}, [0.0]
@@ -793,10 +797,10 @@ def run_sp2(args):
                     used.append(total - f)
                     d = {"device_bytes_in_use": int(total - f), "x_leaves": X.info()["nleaves"],
                          "product_leaves": X2.info()["nleaves"]}
-                    if prec != "fp64" and fp64_prod is not None and it == args.sp2_fp64_iters - 1:
+                    if prec != "fp64" and fp64_prod is not None and it == fp64_iters - 1 < args.sp2_iters - 1:
                         ref = S.spamm_frob_norm(ctx, fp64_prod)
-                        d["diff_vs_fp64_chain"] = S.spamm_error(ctx, fp64_prod, X2) / ref
-                    if prec == "fp64" and it == iters - 1:
+                        d["product_diff_vs_fp64_chain"] = S.spamm_error(ctx, fp64_prod, X2) / ref
+                    if prec == "fp64" and it == iters - 1 and iters < args.sp2_iters:
                         keep["prod"] = S.spamm_add(ctx, 1.0, X2, 0.0, X2)
                     if args.sp2_probe_every and (it % args.sp2_probe_every == 0 or it == iters - 1):
                         ea, ef, ex = sp2_probe_rows(S, ctx, X, X2, rows, args.sp2_tau, n, bs)
@@ -824,14 +828,22 @@ def run_sp2(args):
                              "history": hist}
                 if "prod" in keep:
                     fp64_prod = keep["prod"]
-                X.close()
+                if prec == "fp64":
+                    fp64_final, fp64_hist = X, hist
+                else:
+                    if fp64_final is not None and len(fp64_hist) == len(hist):
+                        res[prec]["final_diff_vs_fp64_chain"] = (S.spamm_error(ctx, fp64_final, X) /
+                                                                 S.spamm_frob_norm(ctx, fp64_final))
+                        res[prec]["same_branches_as_fp64"] = sum(
+                            a["branch"] == b["branch"] for a, b in zip(hist, fp64_hist))
+                    X.close()
         except S.SpammError as e:
             if e.status != S.E_OOM:
                 raise
             rec["admission"] = "admitted; ran out of device memory (%s)" % str(e)[:160]
             rec["partial"] = {k: {kk: v[kk] for kk in ("seconds", "iterations")} for k, v in res.items()}
             out["admission"].append(rec)
-            res, fp64_prod = None, None
+            res = fp64_prod = fp64_final = fp64_hist = None
             gc.collect()
             S.spamm_trim(ctx)
             continue
@@ -841,8 +853,9 @@ def run_sp2(args):
         out["config"]["n_occ"] = n_occ
         out["config"]["bound"] = est["bound"]
         out["forms"] = res
-        if fp64_prod is not None:
-            fp64_prod.close()
+        for m in (fp64_prod, fp64_final):
+            if m is not None:
+                m.close()
         break
     print(json.dumps(out), flush=True)
 

@@ -120,3 +120,15 @@ def test_defaults_are_one_gpu_the_bench_workload_and_three_warmups(monkeypatch):
     b = bench.parse_args()
     bench.resolve_defaults(b)
     assert not b.headline and b.prec == "fp64" and b.tau == 1e-6
+
+
+def test_sp2_footprint_estimate_admits_the_64_cubed_lattice_and_refuses_two_to_the_20():
+    import synth
+    est = {n: bench.sp2_estimate(synth.lattice_3d(n, alpha=1.0, seed=1), 64, 6.0, 1e-6, held=1)
+           for n in (262144, 1048576)}
+    gb300 = 284_208 * 2 ** 20
+    assert est[262144]["peak_bytes_est"] < 0.9 * 0.95 * gb300
+    assert est[1048576]["peak_bytes_est"] > gb300
+    # leaves per block row are about the same for both lattices (the decay sets them)
+    per_row = {n: e["x0_leaves_est"] / (n // 64) for n, e in est.items()}
+    assert 0.8 < per_row[262144] / per_row[1048576] < 1.25

@@ -128,7 +128,7 @@ def _insulator(S, ctx, n, delta, tau, bs=64):
 @pytest.mark.parametrize("prec", ["fp64", "fp16_scaled", "bf16_split4"])
 def test_sp2_insulator_matches_oracle(S, ctx, prec):
     from paper_1906_08148_gb300 import chain
-    n, delta, tau, iters = 2048, 6.0, 1e-7, 12
+    n, delta, tau, iters = 2048, 6.0, 1e-7, 22
     GF, OF, n_occ, bound = _insulator(S, ctx, n, delta, tau)
     GX, gh = chain.sp2(ctx, GF, n_occ, bound, tau, "combined", prec, iters)
     OX, oh = ochain.sp2(OF, n_occ, bound, tau, oracle.COMBINED, iters)
@@ -139,6 +139,8 @@ def test_sp2_insulator_matches_oracle(S, ctx, prec):
     D, R = S.spamm_to_dense(ctx, GX), oracle.to_dense(OX)
     tol = 1e-12 if prec == "fp64" else (1e-9 if prec == "bf16_split4" else 1e-4)
     assert np.linalg.norm(D - R) <= tol * np.linalg.norm(R), np.linalg.norm(D - R) / np.linalg.norm(R)
+    # converged: the trace counts the occupied states
+    assert ochain.trace(OX) == pytest.approx(n_occ, rel=1e-6)
     assert S.spamm_trace(ctx, GX) == pytest.approx(n_occ, rel=1e-6)
 
 
