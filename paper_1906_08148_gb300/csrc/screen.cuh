@@ -1,0 +1,82 @@
+// screen.cuh -- the norm test ||A_ik|| ||B_kj|| >= tau of Algorithm 1 (the
+// product rounded to FP64, as the oracle computes it), screened without FP64
+// arithmetic.  This part issues two FP64 operations per clock per SM, so the
+// task-list builder first decides with integer exponents and an FP32 product
+// of leading mantissa bits; only pairs the screen cannot decide take the FP64
+// product.  With |A| = fa 2^ea, |B| = fb 2^eb, tau = ft 2^et (f in [1, 2),
+// e unbiased) and E = ea + eb - et:
+//   E >= 2:  p >= 2^(et+2) > tau, kept;
+//   E <= -2: the exact product is at most (1 - 2^-53)^2 2^et, whose FP64
+//            rounding stays below 2^et <= tau, skipped;
+//   |E| <= 1: m = fl32(fa' fb') of the 23-bit truncated mantissas lies within
+//            (1 - 2^-24, 1 + 2^-21.4) times fa fb, so m above hi[E+1] =
+//            ft (1 + 2^-18) 2^-E (rounded up to FP32) keeps and m below
+//            lo[E+1] = ft (1 - 2^-18) 2^-E (rounded down) skips; the FP64
+//            rounding of p is far inside these margins;
+//   a zero or subnormal norm, or tau zero or subnormal: undecided.
+// Host-compilable so that the screen can be checked against FP64 products.
+#pragma once
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <cmath>
+
+#if defined(__CUDACC__)
+#define SCREEN_HD __host__ __device__ __forceinline__
+#else
+#define SCREEN_HD static inline
+#endif
+
+struct TauScreen {
+  int K;            // biased field of tau + 1023: E = eA + eB - K from biased fields
+  float hi[3], lo[3];
+  int exact_only;   // tau zero or subnormal
+};
+
+// Biased exponent field and the leading 23 mantissa bits as a float in [1, 2).
+SCREEN_HD void split_norm(double x, float* m, int* e) {
+  uint64_t b;
+  memcpy(&b, &x, sizeof b);
+  *e = (int)((b >> 52) & 0x7ff);
+  const uint32_t fb = 0x3f800000u | (uint32_t)((b >> 29) & 0x7fffff);
+  memcpy(m, &fb, sizeof fb);
+}
+
+// 1: kept, 0: skipped, -1: undecided (take the FP64 product).
+SCREEN_HD int screen_decide(float ma, int ea, float mb, int eb, const TauScreen& sc) {
+  if (sc.exact_only || ea == 0 || eb == 0) return -1;
+  const int E = ea + eb - sc.K;
+  if (E >= 2) return 1;
+  if (E <= -2) return 0;
+  const float mp = ma * mb;  // one FP32 rounding (no contraction: a plain product)
+  const float hi = E == -1 ? sc.hi[0] : (E == 0 ? sc.hi[1] : sc.hi[2]);
+  const float lo = E == -1 ? sc.lo[0] : (E == 0 ? sc.lo[1] : sc.lo[2]);
+  if (mp > hi) return 1;
+  if (mp < lo) return 0;
+  return -1;
+}
+
+// Thresholds for tau (host side), rounded outwards to FP32.
+static inline TauScreen make_screen(double tau) {
+  TauScreen sc;
+  memset(&sc, 0, sizeof sc);
+  uint64_t b;
+  memcpy(&b, &tau, sizeof b);
+  const int et = (int)((b >> 52) & 0x7ff);
+  sc.K = et + 1023;
+  sc.exact_only = (et == 0);
+  int e2 = 0;
+  const double ft = et ? 2.0 * std::frexp(tau, &e2) : 1.0;
+  for (int i = 0; i < 3; ++i) {
+    const int E = i - 1;
+    const double h = std::ldexp(ft * (1.0 + std::ldexp(1.0, -18)), -E);
+    const double l = std::ldexp(ft * (1.0 - std::ldexp(1.0, -18)), -E);
+    float hf = (float)h, lf = (float)l;
+    if ((double)hf < h) hf = std::nextafter(hf, INFINITY);
+    if ((double)lf > l) lf = std::nextafter(lf, -INFINITY);
+    sc.hi[i] = hf;
+    sc.lo[i] = lf;
+  }
+  return sc;
+}

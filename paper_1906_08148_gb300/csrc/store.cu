@@ -34,23 +34,28 @@ static unsigned grid_for(spamm_ctx ctx, int64_t items, int per_block, int max_pe
 // the 16-byte pairs l, l+32, ... (coalesced 512-byte rows), squares are
 // accumulated with explicit FMAs in that fixed order and the 32 partial sums
 // are combined by a butterfly, so every build path gives identical bits.
+// The FMA is the only FP64 instruction per element: this part issues two FP64
+// operations per clock per SM, so the non-zero and finiteness checks work on
+// the bit patterns in the integer pipe (any bit besides the sign set: non-zero;
+// exponent field all ones: Inf or NaN).
 template <class Get>
 __device__ __forceinline__ void warp_leaf_sumsq(Get get, int bs, int lane, double* s_out, bool* nz_out, bool* bad_out) {
   const int pairs = bs * bs / 2;
   double s = 0.0;
-  bool nz = false, bad = false;
+  uint32_t bits = 0, emax = 0;
   for (int i = lane; i < pairs; i += 32) {
     double2 v = get(i);
     s = __fma_rn(v.x, v.x, s);
     s = __fma_rn(v.y, v.y, s);
-    nz |= (v.x != 0.0) || (v.y != 0.0);
-    bad |= !isfinite(v.x) || !isfinite(v.y);
+    const uint32_t hx = (uint32_t)__double2hiint(v.x), hy = (uint32_t)__double2hiint(v.y);
+    bits |= (uint32_t)__double2loint(v.x) | (uint32_t)__double2loint(v.y) | ((hx | hy) & 0x7fffffffu);
+    emax = max(emax, max(hx & 0x7ff00000u, hy & 0x7ff00000u));
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   *s_out = s;
-  *nz_out = __any_sync(0xffffffffu, nz);
-  *bad_out = __any_sync(0xffffffffu, bad);
+  *nz_out = __any_sync(0xffffffffu, bits != 0);
+  *bad_out = __any_sync(0xffffffffu, emax == 0x7ff00000u);
 }
 
 // Block b takes leaves [64 b, 64 b + 64), each of its 8 warps every 8th of
