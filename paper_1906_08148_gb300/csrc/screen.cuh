@@ -8,12 +8,14 @@
 //   E >= 2:  p >= 2^(et+2) > tau, kept;
 //   E <= -2: the exact product is at most (1 - 2^-53)^2 2^et, whose FP64
 //            rounding stays below 2^et <= tau, skipped;
-//   |E| <= 1: m = fl32(fa' fb') of the 23-bit truncated mantissas lies within
-//            (1 - 2^-24, 1 + 2^-21.4) times fa fb, so m above hi[E+1] =
+//   |E| <= 1: m = fl32(fa' fb') of the mantissas truncated to 21 bits lies
+//            within (1 - 2^-24, 1 + 2^-19.9) times fa fb, so m above hi[E+1] =
 //            ft (1 + 2^-18) 2^-E (rounded up to FP32) keeps and m below
 //            lo[E+1] = ft (1 - 2^-18) 2^-E (rounded down) skips; the FP64
 //            rounding of p is far inside these margins;
 //   a zero or subnormal norm, or tau zero or subnormal: undecided.
+// A norm is packed into one 32-bit key: its biased exponent field in the top
+// 11 bits, the leading 21 mantissa bits below.
 // Host-compilable so that the screen can be checked against FP64 products.
 #pragma once
 #include <math.h>
@@ -34,21 +36,24 @@ struct TauScreen {
   int exact_only;   // tau zero or subnormal
 };
 
-// Biased exponent field and the leading 23 mantissa bits as a float in [1, 2).
-SCREEN_HD void split_norm(double x, float* m, int* e) {
+// The 32-bit key of a norm (non-negative double).
+SCREEN_HD uint32_t pack_norm(double x) {
   uint64_t b;
   memcpy(&b, &x, sizeof b);
-  *e = (int)((b >> 52) & 0x7ff);
-  const uint32_t fb = 0x3f800000u | (uint32_t)((b >> 29) & 0x7fffff);
-  memcpy(m, &fb, sizeof fb);
+  return (uint32_t)((b >> 52) & 0x7ff) << 21 | (uint32_t)((b >> 31) & 0x1fffff);
 }
 
 // 1: kept, 0: skipped, -1: undecided (take the FP64 product).
-SCREEN_HD int screen_decide(float ma, int ea, float mb, int eb, const TauScreen& sc) {
+SCREEN_HD int screen_decide(uint32_t ka, uint32_t kb, const TauScreen& sc) {
+  const int ea = (int)(ka >> 21), eb = (int)(kb >> 21);
   if (sc.exact_only || ea == 0 || eb == 0) return -1;
   const int E = ea + eb - sc.K;
   if (E >= 2) return 1;
   if (E <= -2) return 0;
+  const uint32_t fa = 0x3f800000u | ((ka & 0x1fffffu) << 2), fb = 0x3f800000u | ((kb & 0x1fffffu) << 2);
+  float ma, mb;
+  memcpy(&ma, &fa, sizeof ma);
+  memcpy(&mb, &fb, sizeof mb);
   const float mp = ma * mb;  // one FP32 rounding (no contraction: a plain product)
   const float hi = E == -1 ? sc.hi[0] : (E == 0 ? sc.hi[1] : sc.hi[2]);
   const float lo = E == -1 ? sc.lo[0] : (E == 0 ? sc.lo[1] : sc.lo[2]);

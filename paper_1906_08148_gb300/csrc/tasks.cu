@@ -40,40 +40,37 @@ __device__ __forceinline__ double comp4d(const double4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
-// Per node of a level: the Frobenius norms sqrt(s) of its four children
-// (-1 where a child is null), so the descent reads one 32-byte record per
-// node of a pair instead of four scattered squared norms; and the same norms
-// split for the screen of screen.cuh: the biased exponent field and the
-// leading 23 mantissa bits as a float in [1, 2).
-struct NormKey {
-  float4 m;
-  int4 e;
+// Per node of a level, one 32-byte record: its four children (node indices
+// on the next level, -1 where null) and their Frobenius norms sqrt(s) as the
+// 32-bit keys of screen.cuh, so the descent reads one sector per node of a
+// pair; the norms themselves (-1 where null) go to a second array that only
+// the pairs the screen leaves undecided read.  One launch covers both
+// operands' levels (A's nodes first).
+struct __align__(32) NodeRec {
+  int4 child;
+  uint4 key;
 };
 
-__global__ void child_norms_kernel(int64_t n, const int4* __restrict__ child, const double* __restrict__ sq_next,
-                                   double4* __restrict__ out, NormKey* __restrict__ key) {
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-    const int4 c = child[q];
-    const double4 v = make_double4(c.x >= 0 ? sqrt(sq_next[c.x]) : -1.0, c.y >= 0 ? sqrt(sq_next[c.y]) : -1.0,
-                                   c.z >= 0 ? sqrt(sq_next[c.z]) : -1.0, c.w >= 0 ? sqrt(sq_next[c.w]) : -1.0);
-    out[q] = v;
-    NormKey k;
-    split_norm(v.x, &k.m.x, &k.e.x);
-    split_norm(v.y, &k.m.y, &k.e.y);
-    split_norm(v.z, &k.m.z, &k.e.z);
-    split_norm(v.w, &k.m.w, &k.e.w);
-    key[q] = k;
+__global__ void node_rec_kernel(int64_t nA, const int4* __restrict__ childA, const double* __restrict__ sqA,
+                                NodeRec* __restrict__ recA, double4* __restrict__ normA, int64_t nB,
+                                const int4* __restrict__ childB, const double* __restrict__ sqB,
+                                NodeRec* __restrict__ recB, double4* __restrict__ normB) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nA + nB; q += (int64_t)gridDim.x * blockDim.x) {
+    const bool a = q < nA;
+    const int64_t r = a ? q : q - nA;
+    const int4 c = (a ? childA : childB)[r];
+    const double* sq = a ? sqA : sqB;
+    const double4 v = make_double4(c.x >= 0 ? sqrt(sq[c.x]) : -1.0, c.y >= 0 ? sqrt(sq[c.y]) : -1.0,
+                                   c.z >= 0 ? sqrt(sq[c.z]) : -1.0, c.w >= 0 ? sqrt(sq[c.w]) : -1.0);
+    NodeRec rec;
+    rec.child = c;
+    rec.key = make_uint4(pack_norm(v.x), pack_norm(v.y), pack_norm(v.z), pack_norm(v.w));
+    (a ? recA : recB)[r] = rec;
+    (a ? normA : normB)[r] = v;
   }
 }
 
-// mask bit (2*c + ck) for child group c = 2*ci + cj and child k-index ck;
-// na / nb: the children's norms of the pair's A and B nodes.  The product is
-// the FP64 round-to-nearest product of the two norms; the comparisons use its
-// bits (non-negative doubles order like their bit patterns), because this part
-// issues FP64 instructions at two per clock per SM.  The borderline test
-// |prod - tau| <= 1e-12 tau is evaluated in FP64 only for products within
-// 2^14 units in the last place of tau (1e-12 relative is about 4500 of them).
-__device__ __forceinline__ float compf(const float4& v, int i) {
+__device__ __forceinline__ uint32_t compu(const uint4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
@@ -86,9 +83,16 @@ __device__ __forceinline__ bool exact_keep(double na, double nb, double tau, boo
   return pb >= tb;  // prod >= tau for prod, tau >= 0
 }
 
-__device__ __forceinline__ unsigned child_mask(const int4& ca, const int4& cb, const NormKey& ka, const NormKey& kb,
-                                               const double4* na, const double4* nb, const TauScreen& sc,
-                                               double tau, int test, bool leaf, long long* cand, long long* border) {
+// mask bit (2*c + ck) for child group c = 2*ci + cj and child k-index ck;
+// na / nb: the children's norms of the pair's A and B nodes.  The product is
+// the FP64 round-to-nearest product of the two norms; the comparisons use its
+// bits (non-negative doubles order like their bit patterns), because this part
+// issues FP64 instructions at two per clock per SM.  The borderline test
+// |prod - tau| <= 1e-12 tau is evaluated in FP64 only for products within
+// 2^14 units in the last place of tau (1e-12 relative is about 4500 of them).
+__device__ __forceinline__ unsigned child_mask(const NodeRec& ra, const NodeRec& rb, const double4* na,
+                                               const double4* nb, const TauScreen& sc, double tau, int test,
+                                               bool leaf, long long* cand, long long* border) {
   unsigned m = 0;
 #pragma unroll
   for (int ci = 0; ci < 2; ++ci)
@@ -97,12 +101,11 @@ __device__ __forceinline__ unsigned child_mask(const int4& ca, const int4& cb, c
 #pragma unroll
       for (int ck = 0; ck < 2; ++ck) {
         const int ia = 2 * ci + ck, ib = 2 * ck + cj;
-        const int a = comp4(ca, ia), b = comp4(cb, ib);
-        if (a < 0 || b < 0) continue;
+        if (comp4(ra.child, ia) < 0 || comp4(rb.child, ib) < 0) continue;
         ++*cand;
         bool keep = true;
         if (test) {
-          const int d = screen_decide(compf(ka.m, ia), comp4(ka.e, ia), compf(kb.m, ib), comp4(kb.e, ib), sc);
+          const int d = screen_decide(compu(ra.key, ia), compu(rb.key, ib), sc);
           keep = d >= 0 ? d == 1 : exact_keep(comp4d(*na, ia), comp4d(*nb, ib), tau, leaf, border);
         }
         if (keep) m |= 1u << (2 * (2 * ci + cj) + ck);
@@ -113,11 +116,10 @@ __device__ __forceinline__ unsigned child_mask(const int4& ca, const int4& cb, c
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     task_count_kernel(int64_t Gcap, const int64_t* __restrict__ dG, const int64_t* __restrict__ gstart,
                       const int32_t* __restrict__ ta,
-                      const int32_t* __restrict__ tb, const int4* __restrict__ childA, const int4* __restrict__ childB,
-                      const double4* __restrict__ normA, const double4* __restrict__ normB,
-                      const NormKey* __restrict__ keyA, const NormKey* __restrict__ keyB, TauScreen sc, double tau,
-                      int test, int leaf, uint8_t* __restrict__ mask, uint64_t* __restrict__ packed,
-                      unsigned long long* stats) {
+                      const int32_t* __restrict__ tb, const NodeRec* __restrict__ recA,
+                      const NodeRec* __restrict__ recB, const double4* __restrict__ normA,
+                      const double4* __restrict__ normB, TauScreen sc, double tau, int test, int leaf,
+                      uint8_t* __restrict__ mask, uint64_t* __restrict__ packed, unsigned long long* stats) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t G = *dG;
@@ -131,11 +133,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     unsigned cnt[4] = {0, 0, 0, 0};
     for (int64_t q = q0 + lane; q < q1; q += 32) {
       const int32_t ia = ta[q], ib = tb[q];
-      const int4 ca = childA[ia], cb = childB[ib];
-      const unsigned m = test ? child_mask(ca, cb, keyA[ia], keyB[ib], normA + ia, normB + ib, sc, tau, test, leaf,
-                                           &cand, &border)
-                              : child_mask(ca, cb, NormKey{}, NormKey{}, normA + ia, normB + ib, sc, tau, 0, leaf,
-                                           &cand, &border);
+      const unsigned m = child_mask(recA[ia], recB[ib], normA + ia, normB + ib, sc, tau, test, leaf, &cand, &border);
       mask[q] = (uint8_t)m;
 #pragma unroll
       for (int c = 0; c < 4; ++c) cnt[c] += __popc((m >> (2 * c)) & 3u);
@@ -320,21 +318,20 @@ TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm
     CK(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned long long), ctx->stream));
     BufP mask = alloc_n<uint8_t>(ctx, Q);
     BufP packed = alloc_n<uint64_t>(ctx, 4 * G), off = alloc_n<uint64_t>(ctx, 4 * G), tot = alloc_n<uint64_t>(ctx, 1);
-    BufP normA = alloc_n<double4>(ctx, A->lv[t].count), normB = alloc_n<double4>(ctx, B->lv[t].count);
-    BufP keyA = alloc_n<NormKey>(ctx, A->lv[t].count), keyB = alloc_n<NormKey>(ctx, B->lv[t].count);
-    for (int side = 0; side < 2; ++side) {
-      const Level& lv = (side ? B : A)->lv[t];
-      if (lv.count == 0) continue;
-      const int64_t g = (lv.count + 255) / 256, cap = (int64_t)ctx->num_sms * 16;
-      child_norms_kernel<<<(unsigned)(g < cap ? g : cap), 256, 0, ctx->stream>>>(
-          lv.count, P<int4>(lv.child), P<double>((side ? B : A)->lv[t + 1].sq), P<double4>(side ? normB : normA),
-          P<NormKey>(side ? keyB : keyA));
-      CK_LAUNCH("child_norms_kernel");
+    const int64_t nA = A->lv[t].count, nB = B->lv[t].count;
+    BufP normA = alloc_n<double4>(ctx, nA), normB = alloc_n<double4>(ctx, nB);
+    BufP recA = alloc_n<NodeRec>(ctx, nA), recB = alloc_n<NodeRec>(ctx, nB);
+    {
+      const int64_t g = (nA + nB + 255) / 256, cap = (int64_t)ctx->num_sms * 16;
+      node_rec_kernel<<<(unsigned)(g < cap ? g : cap), 256, 0, ctx->stream>>>(
+          nA, P<int4>(A->lv[t].child), P<double>(A->lv[t + 1].sq), P<NodeRec>(recA), P<double4>(normA), nB,
+          P<int4>(B->lv[t].child), P<double>(B->lv[t + 1].sq), P<NodeRec>(recB), P<double4>(normB));
+      CK_LAUNCH("node_rec_kernel");
     }
     task_count_kernel<<<warps_grid(ctx, G), kWarpsPerBlock * 32, 0, ctx->stream>>>(
-        G, dG, P<int64_t>(gstart), P<int32_t>(ta), P<int32_t>(tb), P<int4>(A->lv[t].child), P<int4>(B->lv[t].child),
-        P<double4>(normA), P<double4>(normB), P<NormKey>(keyA), P<NormKey>(keyB), screen, tau, test_norms, leaf,
-        P<uint8_t>(mask), P<uint64_t>(packed), stats);
+        G, dG, P<int64_t>(gstart), P<int32_t>(ta), P<int32_t>(tb), P<NodeRec>(recA), P<NodeRec>(recB),
+        P<double4>(normA), P<double4>(normB), screen, tau, test_norms, leaf, P<uint8_t>(mask), P<uint64_t>(packed),
+        stats);
     CK_LAUNCH("task_count_kernel");
     scan_exclusive_u64(ctx, P<uint64_t>(packed), P<uint64_t>(off), 4 * G, P<uint64_t>(tot));
     // capacities of the next level: exact after a wait, else the bounds 8 Q and 4 G

@@ -22,12 +22,7 @@ def scr(tmp_path_factory):
         f.write('#include "screen.cuh"\n'
                 'extern "C" void decide(double tau, const double* a, const double* b, long n, int* out) {\n'
                 "  const TauScreen sc = make_screen(tau);\n"
-                "  for (long i = 0; i < n; ++i) {\n"
-                "    float ma, mb; int ea, eb;\n"
-                "    split_norm(a[i], &ma, &ea);\n"
-                "    split_norm(b[i], &mb, &eb);\n"
-                "    out[i] = screen_decide(ma, ea, mb, eb, sc);\n"
-                "  }\n"
+                "  for (long i = 0; i < n; ++i) out[i] = screen_decide(pack_norm(a[i]), pack_norm(b[i]), sc);\n"
                 "}\n")
     so = os.path.join(d, "libshim.so")
     subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I", CSRC,

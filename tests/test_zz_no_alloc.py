@@ -65,8 +65,13 @@ def test_noalloc_second_call_with_fewer_leaves_and_limits(S):
         assert abs(float(total.item()) - want) <= 1e-13 * max(want, 1.0)
         if nl:
             assert np.allclose(sq.cpu().numpy()[:nl], ref[:nl], rtol=1e-13)
-    assert S.spamm_leaf_sqnorms_noalloc(payload, S.NOALLOC_MAX_LEAVES + 1, 32, sq, total, None) == S.E_CAPACITY
-    assert S.spamm_leaf_sqnorms_noalloc(payload, 10, 48, sq, total, None) == S.E_INVALID_ARG
+    # the library's own limits, reached with raw pointers (the binding checks
+    # tensor sizes first; the library refuses these before anything is enqueued)
+    p, q, t = payload.data_ptr(), sq.data_ptr(), total.data_ptr()
+    assert S.spamm_leaf_sqnorms_noalloc(p, S.NOALLOC_MAX_LEAVES + 1, 32, q, t, None) == S.E_CAPACITY
+    assert S.spamm_leaf_sqnorms_noalloc(p, 10, 48, q, t, None) == S.E_INVALID_ARG
+    with pytest.raises(ValueError):
+        S.spamm_leaf_sqnorms_noalloc(payload, S.NOALLOC_MAX_LEAVES + 1, 32, sq, total, None)
 
 
 def test_noalloc_refuses_misaligned_or_wrong_buffers_on_the_host(S):
