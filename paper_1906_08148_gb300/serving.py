@@ -89,6 +89,7 @@ class SpammBackend:
             S.spamm_set_gemm_sms(self.exec_ctx, exec_sms)
         free, _ = torch.cuda.mem_get_info(device)
         self.free_bytes = free
+        self.sms = exec_sms or torch.cuda.get_device_properties(device).multi_processor_count
 
     def estimate(self, req: Request) -> int:
         """Bytes to charge before planning: the operand terms and an output as
@@ -109,6 +110,15 @@ class SpammBackend:
     def work(self, job):
         i = job.info()
         return i["work"], i["work_done"]
+
+    def units(self, job):
+        i = job.info()
+        return i["units"], i["units_done"]
+
+    def slots(self, prec: str, bs) -> int:
+        """Work units one launch runs side by side: the FP64 kernel holds three
+        CTAs per SM, the tensor-core kernel one."""
+        return (3 if prec == "fp64" else 1) * self.sms
 
     def run(self, jobs, budgets) -> float:
         _, ms = self.S.spamm_run(self.exec_ctx, jobs, budgets)
@@ -283,6 +293,26 @@ class Server:
         base = self._rate_guess.get(prec, 2400.0)
         return base * (64.0 / bs) ** 3 if prec == "fp64" else base
 
+    def _budgets(self, key, group, rate: float):
+        """Work each job of the launch may run: its share of the slice at the
+        measured rate, but at least enough units that the launch fills every
+        CTA slot (a unit is one output leaf or quad and runs on one CTA: FP64
+        units of long rows take tens of milliseconds, so a slice of a few of
+        them would leave most of the device idle)."""
+        share = max(1.0, rate * self.slice_ms / len(group))
+        slots = getattr(self.backend, "slots", None)
+        units = getattr(self.backend, "units", None)
+        if slots is None or units is None:
+            return [share] * len(group)
+        per_job = -(-slots(*key) // len(group))
+        out = []
+        for r in group:
+            total, done = self.backend.work(r.job)
+            nu, nd = units(r.job)
+            left = max(1, nu - nd)
+            out.append(max(share, per_job * (total - done) / left))
+        return out
+
     def _complete(self, r: Request, C, st: dict, err: Optional[str]):
         if C is not None and not self.keep_results:
             C.close()
@@ -325,11 +355,11 @@ class Server:
             turn += 1
             group = [r for r in active if self._key(r) == key][:self.max_batch]
             rate = self._rate.get(key, self._first_rate(*key))
-            budget = max(1.0, rate * self.slice_ms / len(group))
+            budgets = self._budgets(key, group, rate)
             before = [self.backend.work(r.job)[1] for r in group]
             t_launch = self.now()
             try:
-                ms = self.backend.run([r.job for r in group], [budget] * len(group))
+                ms = self.backend.run([r.job for r in group], budgets)
                 err = None
             except Exception as e:
                 ms, err = 0.0, str(e)

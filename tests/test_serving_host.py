@@ -171,3 +171,36 @@ def test_results_released_on_completion_when_not_kept():
     assert sorted(closed) == sorted(ids)
     assert all(srv.requests[i].state == "done" and srv.requests[i].result is None for i in ids)
     assert srv.summary()["done"] == 6
+
+
+def test_launch_budgets_fill_every_slot():
+    """With long units (fake FP64 rows of 100 work each) and a small rate, a
+    launch still covers enough units to occupy every CTA slot."""
+    class Slotted(FakeBackend):
+        def __init__(self):
+            super().__init__()
+            self.budgets = []
+
+        def plan(self, req):
+            return ("plan", req.rid, 2000), int(req.A), {"n_kept": 10, "bs": 64}
+
+        def begin(self, plan):
+            return {"rid": plan[1], "work": plan[2], "done": 0, "units": 20}
+
+        def units(self, job):
+            return job["units"], job["done"] * job["units"] // job["work"]
+
+        def slots(self, prec, bs):
+            return 8
+
+        def run(self, jobs, budgets):
+            self.budgets.append(list(budgets))
+            return super().run(jobs, budgets)
+
+    fb = Slotted()
+    reqs = [Request(A=100, B=None, tau=1e-6, prec="fp64", arrival=0.0) for _ in range(2)]
+    srv, fb, ids = _serve(reqs, 10_000, backend=fb)
+    assert all(srv.requests[i].state == "done" for i in ids)
+    # 8 slots over the launch's jobs: each job's budget covers >= 4 of its 100-work units
+    first = fb.budgets[0]
+    assert all(b >= 4 * 100 for b in first)
