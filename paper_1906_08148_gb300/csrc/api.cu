@@ -552,6 +552,9 @@ std::vector<spamm_mat> execute_plans(spamm_ctx ctx, const std::vector<spamm_plan
     CK(cudaEventRecordWithFlags(ev.e[0], ctx->stream, evflags));
     launch_gemm(ctx, prec, bs, batch);
     CK(cudaEventRecordWithFlags(ev.e[1], ctx->stream, evflags));
+    if (prec != SPAMM_PREC_FP64)
+      for (int64_t r = 0; r < np; ++r)
+        tc_finish(ctx, prec, P<double>(outp[r]->pool), outp[r]->nleaves, bs, P<double>(outp[r]->lv[outp[r]->L].sq));
     for (int64_t r = 0; r < np; ++r) fill_iota_i64(ctx, P<int64_t>(outp[r]->slot), outp[r]->nleaves);
     propagate_norms_batch(ctx, nlv);
     CK(cudaEventRecordWithFlags(ev.e[2], ctx->stream, evflags));
@@ -785,6 +788,8 @@ spamm_status spamm_job_finish(spamm_ctx ctx, spamm_job job, spamm_mat* C, spamm_
     spamm_mat Cm = job->out.C.get();
     Events ev;
     CK(cudaEventRecord(ev.e[0], ctx->stream));
+    if (job->plan->prec != SPAMM_PREC_FP64)
+      tc_finish(ctx, job->plan->prec, P<double>(Cm->pool), Cm->nleaves, job->plan->bs, P<double>(Cm->lv[Cm->L].sq));
     fill_iota_i64(ctx, P<int64_t>(Cm->slot), Cm->nleaves);
     std::vector<NormBatchLevel> nlv;
     BufP ntab = norm_batch_tables(ctx, {Cm}, &nlv);

@@ -1,6 +1,7 @@
 // gemm_tc.cu -- kernel (c), tensor-core forms (bs = 64 and 128): BF16 error-free
-// slice splits (3 or 4 slices) and FP16 with per-leaf power-of-two scaling,
-// with the C-leaf norms of kernel (d) in the epilogue.
+// slice splits (3 or 4 slices) and FP16 with per-leaf power-of-two scaling;
+// and their kernel (d), the pass that finishes the output leaves in FP64 and
+// takes their norms.
 //
 // Each leaf product of Algorithm 1 ("C = AB" at the lowest level) is a real
 // 64 x 64 x 64 contraction on tcgen05.  Operands are split at plan time
@@ -19,7 +20,10 @@
 // (exact) and drained into registers: the FP16 form adds them to one FP32
 // accumulator per output element; the BF16 forms keep a two-float (hi + lo)
 // accumulator, adding each exact accumulator with an error-free TwoSum and
-// the rest into lo, and write hi + lo in FP64.
+// the rest into lo.  The epilogue stores the pairs as they are; the finishing
+// pass writes hi + lo in FP64 and the leaf norms, away from the GEMM, because
+// this part issues FP64 instructions at two per clock per SM and an epilogue
+// busy with them stops draining the accumulators the next MMAs need.
 //
 // 128 x 128 leaves.  A unit is one output leaf; its four 64 x 64 quadrants
 // are the children, and every kept product runs as two K-half steps over the
@@ -51,10 +55,11 @@
 //   warp 1     allocates 512 TMEM columns and issues the MMAs of each step.
 //   warps 2-3  idle (they fill the first warpgroup, see the register split)
 //   warps 4-11 epilogue: warps 4-7 column 0, warps 8-11 column 1; TMEM lane =
-//              output row (warp w reads lanes 32 (w mod 4) ..); writes the FP64
-//              output leaves and their squared norms.
+//              output row (warp w reads lanes 32 (w mod 4) ..); writes the
+//              output rows as two-float pairs.
 // No atomics on C: one CTA owns each output quad; k runs in ascending order.
 // Every wait is bounded; on timeout the CTA sets the error word and leaves.
+#include "convert.cuh"
 #include "internal.cuh"
 #include "ptx.cuh"
 #include "tcforms.cuh"
@@ -123,15 +128,6 @@ __device__ __forceinline__ void issue_acc(uint32_t d, uint32_t a_s, uint32_t b_s
   }
 }
 
-// Empty asm statements that read and write their registers: placed before a
-// group of FP64 conversions they keep the compiler from hoisting the
-// conversions of later groups (asm statements stay in order), which bounds
-// the registers live beside the two-float accumulators.
-__device__ __forceinline__ void pin2(uint64_t* x) { asm volatile("" : "+l"(x[0]), "+l"(x[1])); }
-__device__ __forceinline__ void pin4d(double* x) {
-  asm volatile("" : "+d"(x[0]), "+d"(x[1]), "+d"(x[2]), "+d"(x[3]));
-}
-
 // (hi, lo) += x sc for two adjacent output elements at once, with an
 // error-free TwoSum of hi and x sc (x sc is exact: sc is a power of two) in
 // the packed FP32x2 instructions, each lane rounding like the scalar
@@ -161,9 +157,6 @@ __device__ __forceinline__ void fma_x2(uint64_t& lo2, uint32_t v0, uint32_t v1, 
       : "+l"(lo2)
       : "r"(v0), "r"(v1), "l"(sc2));
 }
-__device__ __forceinline__ float2 unpack2(uint64_t x) {
-  return make_float2(__uint_as_float((uint32_t)x), __uint_as_float((uint32_t)(x >> 32)));
-}
 
 template <int PREC>
 __global__ void __launch_bounds__(kQuadThreads, 1)
@@ -179,7 +172,6 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
   __shared__ int64_t qid[kQuadQ], epi_un;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, epi_stop;
-  __shared__ double red[2][4];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -426,53 +418,27 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
           mbar_arrive(&tempty[b]);
         }
       }
-      // output row `row` of leaf g[child]: FP64, and its squared norm
+      // output row `row` of leaf g[child], unconverted: each element's 8-byte
+      // slot receives its two-float pair (hi, lo) (FP16: (hi, 0)); the finishing
+      // pass (tc_finish_kernel) turns the slots into FP64 and takes the leaf
+      // norms, so no FP64 instruction runs here, where it would hold up the
+      // draining of the accumulators the next quad's MMAs wait for
       const int gl = g[child];
-      double s2 = 0.0;
       if (gl >= 0) {
-        double2* out = reinterpret_cast<double2*>(big ? pl.cpool + (int64_t)gl * 16384 + (64 * half + row) * 128 + 64 * col
-                                                      : pl.cpool + (int64_t)gl * 4096 + row * 64);
+        uint4* out = reinterpret_cast<uint4*>(big ? pl.cpool + (int64_t)gl * 16384 + (64 * half + row) * 128 + 64 * col
+                                                  : pl.cpool + (int64_t)gl * 4096 + row * 64);
 #pragma unroll
-        for (int q = 0; q < 64; q += 4) {
-          double x[4];
+        for (int q = 0; q < 64; q += 2) {
           if constexpr (NACC == 1) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) x[i] = (double)hi[q + i];
+            out[q >> 1] = make_uint4(__float_as_uint(hi[q]), 0u, __float_as_uint(hi[q + 1]), 0u);
           } else {
-            // one group of four at a time: the FP64 conversions are not hoisted
-            pin2(hi2 + q / 2);
-            pin2(lo2 + q / 2);
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-              const float2 h = unpack2(hi2[q / 2 + i]), l = unpack2(lo2[q / 2 + i]);
-              x[2 * i] = (double)h.x + (double)l.x;
-              x[2 * i + 1] = (double)h.y + (double)l.y;
-            }
+            const uint64_t h = hi2[q / 2], l = lo2[q / 2];
+            out[q >> 1] = make_uint4((uint32_t)h, (uint32_t)l, (uint32_t)(h >> 32), (uint32_t)(l >> 32));
           }
-          out[q >> 1] = make_double2(x[0], x[1]);
-          out[(q >> 1) + 1] = make_double2(x[2], x[3]);
-#pragma unroll
-          for (int i = 0; i < 4; ++i) s2 = __fma_rn(x[i], x[i], s2);
-          if constexpr (NACC > 1) pin4d(x);
         }
       }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-      if (lane == 0) red[col][quarter] = s2;
       if (te == 0) epi_stop = *abortp;
       named_barrier(1, 256);
-      if (big) {
-        // one output leaf: its quadrants' squared norms added in quadrant order
-        if (te == 0 && g[0] >= 0) {
-          double t = 0.0;
-          for (int hh = 0; hh < 2; ++hh)
-            for (int cc = 0; cc < 2; ++cc) t += red[cc][2 * hh] + red[cc][2 * hh + 1];
-          pl.csq[g[0]] = t;
-        }
-      } else if (te < 4) {
-        const int cc = te & 1, hh = te >> 1;  // child 2 hh + cc: its rows are quarters 2 hh, 2 hh + 1
-        if (g[2 * hh + cc] >= 0) pl.csq[g[2 * hh + cc]] = red[cc][2 * hh] + red[cc][2 * hh + 1];
-      }
       const bool stop = epi_stop != 0;
       named_barrier(1, 256);
       if (stop) break;
@@ -508,6 +474,59 @@ static void launch_quads(spamm_ctx ctx, const BatchDev& b) {
   CK(cudaMemsetAsync(work, 0, sizeof(unsigned long long), ctx->stream));
   gemm_quad_kernel<PREC><<<gemm_grid(ctx, b.nunits), kQuadThreads, smem, ctx->stream>>>(b, work, ctx->d_err);
   CK_LAUNCH("gemm_quad_kernel");
+}
+
+// ------------------------------------------------------------------ finish
+// Kernel (d) for the tensor-core forms: every 8-byte slot of an output leaf
+// holds the two-float pair (hi, lo) the GEMM's epilogue left there (FP16: lo =
+// 0); the slot becomes the FP64 value hi + lo (the two conversions are exact
+// and done on bit patterns, one FP64 addition rounds the sum; FP16: the exact
+// conversion of hi alone), and the leaf's squared Frobenius norm is
+// accumulated with one FMA per element in the order of kernel (a) -- lane l
+// takes the 16-byte pairs l, l + 32, ..., a butterfly combines the lanes -- so
+// the stored norm equals kernel (a) applied to the finished leaf, bit for bit.
+// One warp per leaf, 64 leaves per block.  Bound by the FP64 pipe: two FP64
+// instructions per element (one for FP16) at two per clock per SM.
+constexpr int64_t kFinishLeavesPerBlock = 64;
+
+template <bool TWO>
+__global__ void __launch_bounds__(256) tc_finish_kernel(double* __restrict__ pool, int64_t m, int bs,
+                                                        double* __restrict__ sq) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t e = (int64_t)bs * bs;
+  const int pairs = bs * bs / 2;
+  for (int64_t q0 = (int64_t)blockIdx.x * kFinishLeavesPerBlock; q0 < m;
+       q0 += (int64_t)gridDim.x * kFinishLeavesPerBlock)
+    for (int64_t q = q0 + warp; q < q0 + kFinishLeavesPerBlock && q < m; q += 8) {
+      uint4* leaf = reinterpret_cast<uint4*>(pool + q * e);
+      double s = 0.0;
+      for (int i = lane; i < pairs; i += 32) {
+        const uint4 v = leaf[i];  // (hi, lo) of elements 2i and 2i + 1
+        double x0 = __longlong_as_double((long long)f32_to_f64_bits(v.x));
+        double x1 = __longlong_as_double((long long)f32_to_f64_bits(v.z));
+        if (TWO) {
+          x0 = __dadd_rn(x0, __longlong_as_double((long long)f32_to_f64_bits(v.y)));
+          x1 = __dadd_rn(x1, __longlong_as_double((long long)f32_to_f64_bits(v.w)));
+        }
+        s = __fma_rn(x0, x0, s);
+        s = __fma_rn(x1, x1, s);
+        reinterpret_cast<double2*>(leaf)[i] = make_double2(x0, x1);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if (lane == 0) sq[q] = s;
+    }
+}
+
+void tc_finish(spamm_ctx ctx, spamm_prec prec, double* pool, int64_t nleaves, int bs, double* sq) {
+  if (nleaves <= 0) return;
+  const int64_t nblk = (nleaves + kFinishLeavesPerBlock - 1) / kFinishLeavesPerBlock;
+  const unsigned grid = (unsigned)(nblk < (1ll << 30) ? nblk : (1ll << 30));
+  if (prec == SPAMM_PREC_FP16_SCALED)
+    tc_finish_kernel<false><<<grid, 256, 0, ctx->stream>>>(pool, nleaves, bs, sq);
+  else
+    tc_finish_kernel<true><<<grid, 256, 0, ctx->stream>>>(pool, nleaves, bs, sq);
+  CK_LAUNCH("tc_finish_kernel");
 }
 
 void gemm_tc_batch(spamm_ctx ctx, spamm_prec prec, const BatchDev& b) {

@@ -244,6 +244,9 @@ int fp64_units_per_leaf(int bs);
 BufP fp64_unit_order(spamm_ctx ctx, const TaskList& T, int bs);
 // The tensor-core forms' persistent quad kernel (gemm_tc.cu).
 void gemm_tc_batch(spamm_ctx ctx, spamm_prec prec, const BatchDev& b);
+// Kernel (d) of the tensor-core forms: the GEMM's two-float output slots to
+// FP64 in place, and each leaf's squared norm (kernel (a)'s order).
+void tc_finish(spamm_ctx ctx, spamm_prec prec, double* pool, int64_t nleaves, int bs, double* sq);
 // 64 x 64 operand tiles per leaf of the tensor forms (bs 64: 1, bs 128: 4).
 inline int tc_tiles_per_leaf(int bs) { return (bs / 64) * (bs / 64); }
 // Operand terms of a leaf set for a tensor form (role 0: used as A, 1: as B),

@@ -233,3 +233,22 @@ def test_symmetric_square_shares_terms(S, ctx, prec, bs):
     ref, ikj = oracle.multiply(M, M, 0.0, oracle.SPAMM)
     bnd = oracle.to_dense(oracle.LeafMatrix(4 * bs, bs, ref.bi, ref.bj, tcbound.bound(prec, M, M, ikj, ref)))
     assert np.all(np.abs(S.spamm_to_dense(ctx, C) - D @ D) <= bnd)
+
+
+@pytest.mark.parametrize("prec", TC)
+@pytest.mark.parametrize("bs", [64, 128])
+def test_output_norms_are_kernel_a_of_the_finished_leaves(S, ctx, prec, bs):
+    """The finishing pass (kernel (d) of the tensor forms) stores each output
+    leaf's squared norm in kernel (a)'s order: rebuilding the matrix from its
+    own FP64 leaves gives the same norms bit for bit, and they agree with
+    NumPy's sums of squares."""
+    p = synth.lattice_3d(4096, alpha=0.9, seed=4)
+    G = S.spamm_generate(ctx, p, bs)
+    C = S.spamm_multiply(ctx, G, G, 1e-7, "combined", prec)
+    bi, bj, pay, sq = S.spamm_to_blocks(ctx, C)
+    R = S.spamm_from_blocks(ctx, 4096, bs, bi, bj, pay)
+    _, _, pay2, sq2 = S.spamm_to_blocks(ctx, R)
+    assert np.array_equal(pay, pay2)
+    assert np.array_equal(sq, sq2)
+    assert np.allclose(sq, np.sum(pay * pay, axis=(1, 2)), rtol=1e-13, atol=0)
+    assert S.spamm_frob_norm(ctx, C) == pytest.approx(np.sqrt(np.sum(pay * pay)), rel=1e-13)
