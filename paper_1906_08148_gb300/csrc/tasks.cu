@@ -242,7 +242,7 @@ static unsigned warps_grid(spamm_ctx ctx, int64_t items) {
 // Sizes of the next level from the scan total, on the device: its pair and
 // group counts, the closing entry of its group offsets, and this level's
 // statistics (lv[4 t ..]: candidates, borderline pairs, pairs, groups).
-__global__ void level_finish_kernel(const uint64_t* __restrict__ tot, const unsigned long long* __restrict__ stats,
+__global__ void level_finish_kernel(const uint64_t* __restrict__ tot, unsigned long long* __restrict__ stats,
                                     int64_t* __restrict__ dQ2, int64_t* __restrict__ dG2, int64_t* __restrict__ gstart2,
                                     int64_t* __restrict__ lv) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -252,14 +252,18 @@ __global__ void level_finish_kernel(const uint64_t* __restrict__ tot, const unsi
   gstart2[G2] = Q2;
   lv[0] = (int64_t)stats[0];
   lv[1] = (int64_t)stats[1];
+  stats[0] = stats[1] = 0;  // for the next level's count
   lv[2] = Q2;
   lv[3] = G2;
 }
 
 // Upper bounds on the next level's sizes below which the host does not wait
-// for the exact counts (buffers are allocated at the bound instead).
-constexpr int64_t kPairsNoSync = 1ll << 22;
-constexpr int64_t kGroupsNoSync = 1ll << 20;
+// for the exact counts: buffers are allocated at the bound instead (8 Q pairs
+// of 8 bytes and 4 G groups: at most 512 MB and 16 M groups), so the descent
+// of a problem of tens of millions of leaf products waits once, near the
+// bottom, and reads every size back at the end.
+constexpr int64_t kPairsNoSync = 1ll << 26;
+constexpr int64_t kGroupsNoSync = 1ll << 24;
 
 TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm_ctx on) {
   spamm_ctx ctx = on ? on : A->ctx;
@@ -312,10 +316,10 @@ TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm
   }
   const TauScreen screen = make_screen(tau);
   int last = 0;  // level whose sizes describe the current arrays
+  CK(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned long long), ctx->stream));  // level_finish re-zeroes them
   for (int t = 0; t < A->L; ++t) {
     const bool leaf = (t + 1 == A->L);
     const int64_t* dG = dsz + 2 * t + 1;
-    CK(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned long long), ctx->stream));
     BufP mask = alloc_n<uint8_t>(ctx, Q);
     BufP packed = alloc_n<uint64_t>(ctx, 4 * G), off = alloc_n<uint64_t>(ctx, 4 * G), tot = alloc_n<uint64_t>(ctx, 1);
     const int64_t nA = A->lv[t].count, nB = B->lv[t].count;
@@ -336,15 +340,13 @@ TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm
     scan_exclusive_u64(ctx, P<uint64_t>(packed), P<uint64_t>(off), 4 * G, P<uint64_t>(tot));
     // capacities of the next level: exact after a wait, else the bounds 8 Q and 4 G
     int64_t Q2 = 8 * Q, G2 = 4 * G;
-    const bool wait = Q2 > kPairsNoSync || G2 > kGroupsNoSync || leaf;
+    const bool wait = Q2 > kPairsNoSync || G2 > kGroupsNoSync;
     BufP gstart2;
     if (wait) {
       CK(cudaMemcpyAsync(hp, P<uint64_t>(tot), sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
-      CK(cudaMemcpyAsync(hp + 1, dG, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaStreamSynchronize(ctx->stream));
       Q2 = (int64_t)(hp[0] & kCountMask);
       G2 = (int64_t)(hp[0] >> 36);
-      if (leaf) T.nquads = (int64_t)hp[1];  // this level's groups are the parents of the C leaves
     }
     gstart2 = alloc_n<int64_t>(ctx, G2 + 1);
     level_finish_kernel<<<1, 32, 0, ctx->stream>>>(P<uint64_t>(tot), stats, dsz + 2 * (t + 1), dsz + 2 * (t + 1) + 1,
@@ -370,20 +372,23 @@ TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm
     last = t + 1;
     if (exact && G == 0) break;
   }
-  // exact sizes and per-level statistics, one read-back
-  const int nread = 4 * nlev;
-  std::vector<int64_t> h(2 + nread);
-  CK(cudaMemcpyAsync(h.data(), dsz + 2 * last, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(h.data() + 2, dlv, nread * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  // exact sizes of every level and per-level statistics, one read-back (the
+  // two arrays are adjacent)
+  std::vector<int64_t> h(6 * nlev);
+  CK(cudaMemcpyAsync(h.data(), dsz, 6 * nlev * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  const int64_t* hl = h.data() + 2 * nlev;
   if (A->L > 0) {
-    Q = h[0];
-    G = h[1];
+    Q = h[2 * last];
+    G = h[2 * last + 1];
     for (int t = 1; t <= last; ++t) {
-      T.n_candidates[t] = h[2 + 4 * t + 0];
-      T.n_kept_level[t] = h[2 + 4 * t + 2];
+      T.n_candidates[t] = hl[4 * t + 0];
+      T.n_kept_level[t] = hl[4 * t + 2];
     }
-    if (last == A->L) T.n_borderline = h[2 + 4 * A->L + 1];
+    if (last == A->L) {
+      T.n_borderline = hl[4 * A->L + 1];
+      T.nquads = h[2 * (A->L - 1) + 1];  // the groups one level up are the parents of the C leaves
+    }
   }
   T.ngroups = G;
   T.ntasks = Q;
