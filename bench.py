@@ -433,7 +433,7 @@ def run_served(args):
             tau = r2.choice(taus)
             ch = Choice(forced, 64) if forced else choice(i, tau)
             A, B = inputs[(i, ch.bs)]
-            reqs.append(Request(A, B, tau=tau, mode="combined", prec=ch.prec, arrival=t))
+            reqs.append(Request(A, B, tau=tau, mode="combined", prec=ch.prec, order=ch.order, arrival=t))
         return reqs
 
     def serve(reqs):

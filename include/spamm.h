@@ -338,6 +338,27 @@ SPAMM_API spamm_status spamm_job_release(spamm_job job);
  * the next requests while a batch executes. */
 SPAMM_API spamm_status spamm_set_gemm_sms(spamm_ctx ctx, int nsms);
 
+/* Order in which the persistent leaf-product kernels claim their work units
+ * (an output leaf, a 64 x 64 sub-tile of one, or a quad of four output leaves),
+ * for plans created afterwards on `ctx` -- the tile schedule.  Section 4.4's
+ * batched multiply fixes the output structure before any leaf product runs,
+ * so the order is free:
+ *   SPAMM_ORDER_MORTON: output Morton order; the units in flight on all SMs
+ *     share A rows and B columns in L2;
+ *   SPAMM_ORDER_LONGEST_FIRST: units with the most kept products (steps)
+ *     first, ties in Morton order; shortens the tail of launches that hold
+ *     few units per SM;
+ *   SPAMM_ORDER_AUTO (default): longest first for FP64 leaves of 128 and 256,
+ *     Morton otherwise.
+ * Results are identical in every order (each output leaf sums its products
+ * in k order on one CTA). */
+typedef enum {
+  SPAMM_ORDER_AUTO = 0,
+  SPAMM_ORDER_MORTON = 1,
+  SPAMM_ORDER_LONGEST_FIRST = 2
+} spamm_claim_order;
+SPAMM_API spamm_status spamm_set_claim_order(spamm_ctx ctx, int order);
+
 /* enable != 0: spamm_execute / spamm_multiply run their execute phase (the
  * persistent leaf-product launch of every plan in the batch, then the output
  * quadtrees' parent norms, one launch per level for the whole batch) as one

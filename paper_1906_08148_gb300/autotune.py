@@ -24,6 +24,11 @@ candidate wins.  Each candidate's measured work rate (kept products per ms
 for FP64, quad steps per ms for the tensor forms) is kept too: the server
 sizes its launches from it (the slice schedule).
 
+The tile schedule is calibrated too: for the winner at each point the leaf
+products run once with the work units claimed in Morton order and once
+longest first (spamm_set_claim_order), and the faster order (GEMM time) is
+part of the choice.
+
 `choose` maps a request to the winner of the nearest calibrated point
 (distance in log2 n, alpha, log10 tau).  It depends only on the request and
 the table, so a request gets the same form and leaf size alone or in a mix.
@@ -47,6 +52,7 @@ TABLE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.jso
 class Choice:
     prec: str
     bs: int
+    order: str = "auto"   # claiming order of the leaf-product units (spamm_set_claim_order)
 
 
 @dataclass
@@ -60,6 +66,7 @@ class Point:
     trunc_err: float  # ||AB - C||_F estimate, or a dict per leaf size
     rate: dict = None       # candidate -> work per ms (kept products or quad steps)
     estimated: tuple = ()   # candidates whose ms is estimated from a rate
+    order_ms: dict = None   # claiming order -> GEMM ms of the winner (empty: not measured)
 
     def trunc(self, bs: int) -> float:
         return self.trunc_err.get(str(bs), math.inf) if isinstance(self.trunc_err, dict) else self.trunc_err
@@ -114,7 +121,10 @@ class Autotuner:
         if bs is None:
             return p.choice
         ms = {k: v for k, v in p.ms.items() if int(k.split("/")[1]) == bs}
-        return decide(ms, p.arith_err, p.trunc_err) if ms else default
+        if not ms:
+            return default
+        c = decide(ms, p.arith_err, p.trunc_err)
+        return p.choice if (c.prec, c.bs) == (p.choice.prec, p.choice.bs) else c
 
     def rate(self, prec: str, bs: int) -> Optional[float]:
         """Median measured work rate (per ms) of a candidate over the table, or None."""
@@ -124,16 +134,18 @@ class Autotuner:
 
 def load(path: str = TABLE_PATH) -> List[Point]:
     d = json.load(open(path))
-    return [Point(p["n"], p["alpha"], p["tau"], Choice(p["choice"]["prec"], p["choice"]["bs"]), p["ms"],
-                  p["arith_err"], p["trunc_err"], p.get("rate"), tuple(p.get("estimated", ())))
+    return [Point(p["n"], p["alpha"], p["tau"],
+                  Choice(p["choice"]["prec"], p["choice"]["bs"], p["choice"].get("order", "auto")), p["ms"],
+                  p["arith_err"], p["trunc_err"], p.get("rate"), tuple(p.get("estimated", ())), p.get("order_ms"))
             for p in d["points"]]
 
 
 def save(points: Iterable[Point], path: str = TABLE_PATH, meta: Optional[dict] = None):
     out = {"meta": meta or {}, "points": [
-        {"n": p.n, "alpha": p.alpha, "tau": p.tau, "choice": {"prec": p.choice.prec, "bs": p.choice.bs},
+        {"n": p.n, "alpha": p.alpha, "tau": p.tau,
+         "choice": {"prec": p.choice.prec, "bs": p.choice.bs, "order": p.choice.order},
          "ms": p.ms, "arith_err": p.arith_err, "trunc_err": p.trunc_err, "rate": p.rate,
-         "estimated": list(p.estimated)} for p in points]}
+         "estimated": list(p.estimated), "order_ms": p.order_ms} for p in points]}
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
 
@@ -162,7 +174,17 @@ def calibrate(S, ctx, grid: Iterable[tuple], repeats: int = 2, mode: str = "comb
             k = _name("bf16_split4", bs)
             if k + ":vs_fp64" in arith:
                 arith[k] = arith[k + ":vs_fp64"]
-        pt = Point(n, alpha, tau, decide(ms, arith, trunc), ms, arith, trunc, rate, tuple(est))
+        ch = decide(ms, arith, trunc)
+        order_ms = {}
+        if _name(ch.prec, ch.bs) not in est:
+            try:
+                order_ms = _measure_order(S, ctx, pa, pb, tau, mode, ch, repeats)
+            except S.SpammError as e:
+                if e.status != S.E_OOM:
+                    raise
+        if order_ms:
+            ch = Choice(ch.prec, ch.bs, min(order_ms, key=order_ms.get))
+        pt = Point(n, alpha, tau, ch, ms, arith, trunc, rate, tuple(est), order_ms)
         pts.append(pt)
         if log:
             log(pt)
@@ -236,6 +258,29 @@ def _measure_point(S, ctx, pa, pb, tau, mode, repeats, fp64_rate, ms, arith, tru
             h.close()
 
 
+def _measure_order(S, ctx, pa, pb, tau, mode, ch: Choice, repeats) -> dict:
+    """GEMM milliseconds of the chosen form with its units claimed in Morton
+    order and longest first (median of `repeats` after one untimed run)."""
+    out = {}
+    GA = S.spamm_generate(ctx, pa, ch.bs, tau / 100.0)
+    GB = S.spamm_generate(ctx, pb, ch.bs, tau / 100.0)
+    try:
+        for order in ("morton", "longest"):
+            S.spamm_set_claim_order(ctx, order)
+            t = []
+            for _ in range(repeats + 1):
+                C, st = S.spamm_multiply(ctx, GA, GB, tau, mode, ch.prec, stats=True)
+                C.close()
+                t.append(st["ms_gemm"])
+            v = sorted(t[1:])
+            out[order] = v[len(v) // 2]
+    finally:
+        S.spamm_set_claim_order(ctx, "auto")
+        GA.close()
+        GB.close()
+    return out
+
+
 if __name__ == "__main__":
     # Calibration run on a GPU: writes tuned.json beside this file.
     import argparse
@@ -258,7 +303,7 @@ if __name__ == "__main__":
             print(p, flush=True)
             return
         print(p.n, p.alpha, p.tau, p.choice, {k: round(v, 2) for k, v in p.ms.items()},
-              {k: "%.2e" % v for k, v in p.arith_err.items()}, p.trunc_err, flush=True)
+              {k: "%.2e" % v for k, v in p.arith_err.items()}, p.trunc_err, p.order_ms, flush=True)
 
     pts = calibrate(S, c, grid, repeats=a.repeats, log=log)
     save(pts, a.out, meta={"workload": "3-D lattice decay, seeds 1 and 2, combined method",

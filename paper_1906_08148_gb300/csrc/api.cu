@@ -381,7 +381,9 @@ spamm_plan make_plan(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_
     p->slotA = At->slot;
     p->poolB = Bt->pool;
     p->slotB = Bt->slot;
-    p->uorder = fp64_unit_order(ctx, p->T, p->bs);
+    const bool longest = ctx->claim_order == SPAMM_ORDER_LONGEST_FIRST ||
+                         (ctx->claim_order == SPAMM_ORDER_AUTO && p->bs >= 128);
+    if (longest) p->uorder = unit_order_longest(ctx, P<int64_t>(p->T.gstart), p->T.ngroups);
   } else {
     prep_terms(At, prec, 0, &p->termsA, &p->expA, ctx);
     // X times X with X symmetric: the B operand of leaf (k, j) is the transpose
@@ -401,6 +403,8 @@ spamm_plan make_plan(spamm_ctx ctx, spamm_mat A, spamm_mat B, double tau, spamm_
     else
       p->nsteps = build_quad_steps(ctx, p->T, P<uint32_t>(At->lv[At->L].code), P<int32_t>(p->expA),
                                    P<int32_t>(p->expB), P<int32_t>(p->bmap), &p->qstart, &p->qsteps);
+    if (ctx->claim_order == SPAMM_ORDER_LONGEST_FIRST)
+      p->uorder = unit_order_longest(ctx, P<int64_t>(p->qstart), p->bs == 128 ? p->T.ngroups : p->T.nquads);
   }
   CK(cudaEventRecord(ev.e[3], ctx->stream));
   sync_and_check(ctx);
@@ -502,6 +506,8 @@ PlanDev slice_view(const spamm_plan_s& p, const PlanDev& d, int64_t first) {
       v.csq += leaf0;
       if (v.csq_part) v.csq_part += leaf0 * fp64_units_per_leaf(p.bs);
     }
+  } else if (v.uorder) {
+    v.uorder += first;  // units in claiming order; steps and outputs indexed by the unit itself
   } else {
     v.qstart += first;  // quads; their output leaves are named in quads[] itself
     v.quads += 4 * first;
@@ -689,11 +695,18 @@ void job_work_prefix(spamm_job j) {
       j->wpre[x + 1] = j->wpre[x] + (double)(gs[g + 1] - gs[g]) / j->nq;
     }
   } else {
-    std::vector<int64_t> qs(u + 1);
+    std::vector<int64_t> qs(u + 1), ord;
     CK(cudaMemcpyAsync(qs.data(), P<int64_t>(p.qstart), (u + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost,
                        ctx->stream));
+    if (p.uorder) {
+      ord.resize(u);
+      CK(cudaMemcpyAsync(ord.data(), P<int64_t>(p.uorder), u * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    }
     sync_and_check(ctx);
-    for (int64_t x = 0; x < u; ++x) j->wpre[x + 1] = j->wpre[x] + (double)(qs[x + 1] - qs[x]);
+    for (int64_t x = 0; x < u; ++x) {
+      const int64_t q = ord.empty() ? x : ord[x];
+      j->wpre[x + 1] = j->wpre[x] + (double)(qs[q + 1] - qs[q]);
+    }
   }
 }
 
@@ -822,6 +835,14 @@ spamm_status spamm_set_gemm_sms(spamm_ctx ctx, int nsms) {
     need(nsms >= 0 && nsms <= ctx->num_sms, "nsms must be in [0, number of SMs]");
     ctx->gemm_sm_limit = nsms;
   });
+}
+
+spamm_status spamm_set_claim_order(spamm_ctx ctx, int order) {
+  if (!ctx) return SPAMM_E_INVALID_ARG;
+  if (order != SPAMM_ORDER_AUTO && order != SPAMM_ORDER_MORTON && order != SPAMM_ORDER_LONGEST_FIRST)
+    return SPAMM_E_INVALID_ARG;
+  ctx->claim_order = order;
+  return SPAMM_OK;
 }
 
 spamm_status spamm_set_exec_graph(spamm_ctx ctx, int enable) {

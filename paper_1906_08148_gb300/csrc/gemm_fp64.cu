@@ -223,15 +223,14 @@ __global__ void unit_order_keys_kernel(const int64_t* __restrict__ gstart, int64
   }
 }
 
-BufP fp64_unit_order(spamm_ctx ctx, const TaskList& T, int bs) {
-  if (bs < 128 || T.ngroups <= 1) return BufP();
-  BufP keys = alloc_n<uint64_t>(ctx, T.ngroups), vals = alloc_n<int64_t>(ctx, T.ngroups);
-  int64_t grid = (T.ngroups + 255) / 256;
+BufP unit_order_longest(spamm_ctx ctx, const int64_t* start, int64_t n) {
+  if (n <= 1) return BufP();
+  BufP keys = alloc_n<uint64_t>(ctx, n), vals = alloc_n<int64_t>(ctx, n);
+  int64_t grid = (n + 255) / 256;
   if (grid > 4 * (int64_t)ctx->num_sms) grid = 4 * (int64_t)ctx->num_sms;
-  unit_order_keys_kernel<<<(unsigned)grid, 256, 0, ctx->stream>>>(P<int64_t>(T.gstart), T.ngroups, P<uint64_t>(keys),
-                                                                 P<int64_t>(vals));
+  unit_order_keys_kernel<<<(unsigned)grid, 256, 0, ctx->stream>>>(start, n, P<uint64_t>(keys), P<int64_t>(vals));
   CK_LAUNCH("unit_order_keys_kernel");
-  radix_sort_pairs(ctx, P<uint64_t>(keys), P<int64_t>(vals), T.ngroups, kUnitKeyBits);
+  radix_sort_pairs(ctx, P<uint64_t>(keys), P<int64_t>(vals), n, kUnitKeyBits);
   return vals;
 }
 

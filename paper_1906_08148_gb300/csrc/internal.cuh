@@ -113,6 +113,7 @@ struct spamm_ctx_s {
   int num_sms = 0;
   int gemm_sm_limit = 0;                     // 0: leaf GEMM may use every SM
   int exec_graph = 0;                        // run the execute phase as a captured CUDA graph
+  int claim_order = 0;                       // spamm_claim_order of the plans created on this context
   cudaStream_t capture_stream = nullptr;     // created on first graph capture
   cudaGraphExec_t graph_exec = nullptr;      // the last execute graph, updated in place for the next batch
   int64_t graph_instantiations = 0, graph_updates = 0;
@@ -213,7 +214,7 @@ struct PlanDev {
   const QuadStep* qsteps;
   double* cpool;
   double* csq;
-  const int64_t* uorder;  // FP64 form: output leaf at each claiming position (longest first), or null for identity
+  const int64_t* uorder;  // unit (FP64: output leaf; tensor forms: quad or 128-leaf) at each claiming position, or null for identity
   double* csq_part;       // FP64 form, leaves split into sub-tile units: partial squared norms [leaf][sub-tile]
   int32_t tc_bs;          // tensor forms: 64 (units are quads of output leaves) or 128 (units are output leaves)
 };
@@ -241,7 +242,9 @@ int fp64_units_per_leaf(int bs);
 // Output leaves ordered by their number of kept products, largest first
 // (stable), for the FP64 kernel's unit claiming; an empty buffer when the
 // leaves are small enough that the claiming tail does not matter.
-BufP fp64_unit_order(spamm_ctx ctx, const TaskList& T, int bs);
+// Units 0..n-1 sorted by their work start[u+1] - start[u], largest first,
+// ties in index order (stable); empty for n <= 1.
+BufP unit_order_longest(spamm_ctx ctx, const int64_t* start, int64_t n);
 // The tensor-core forms' persistent quad kernel (gemm_tc.cu).
 void gemm_tc_batch(spamm_ctx ctx, spamm_prec prec, const BatchDev& b);
 // Kernel (d) of the tensor-core forms: the GEMM's two-float output slots to

@@ -52,6 +52,7 @@ class Request:
     tau: float
     mode: str = "combined"
     prec: str = "bf16_split4"
+    order: str = "auto"      # claiming order of its leaf-product units (spamm_set_claim_order)
     rid: int = -1
     arrival: float = 0.0     # seconds since the server started (when it may be served)
     # filled in by the server
@@ -99,6 +100,7 @@ class SpammBackend:
         return int(leaves * (TERM_BYTES.get(req.prec, 0) + 8 * ia["bs"] ** 2))
 
     def plan(self, req: Request):
+        self.S.spamm_set_claim_order(self.plan_ctx, req.order)  # the planner thread is the context's only user
         p = self.S.spamm_plan_create(self.plan_ctx, req.A, req.B, req.tau, req.mode, req.prec)
         info = p.info()
         info["bs"] = req.A.info()["bs"]

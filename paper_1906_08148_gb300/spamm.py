@@ -36,7 +36,7 @@ ENTRY_POINTS = (
     "spamm_multiply", "spamm_kept_tasks", "spamm_frob_norm", "spamm_error", "spamm_mat_info", "spamm_to_dense",
     "spamm_to_blocks", "spamm_gather_leaves", "spamm_level_norms", "spamm_leaf_sqnorms_noalloc",
     "spamm_plan_create", "spamm_plan_info", "spamm_execute", "spamm_plan_release", "spamm_set_gemm_sms",
-    "spamm_set_exec_graph", "spamm_add", "spamm_identity", "spamm_trace", "spamm_check_timeout_path", "spamm_trim",
+    "spamm_set_exec_graph", "spamm_set_claim_order", "spamm_add", "spamm_identity", "spamm_trace", "spamm_check_timeout_path", "spamm_trim",
     "spamm_set_symmetric", "spamm_job_begin", "spamm_job_info", "spamm_run", "spamm_job_finish",
     "spamm_job_release", "spamm_exec_graph_info",
 )
@@ -130,6 +130,7 @@ def load(path: str = LIB_PATH):
         "spamm_plan_release": [vp],
         "spamm_set_gemm_sms": [vp, ctypes.c_int],
         "spamm_set_exec_graph": [vp, ctypes.c_int],
+        "spamm_set_claim_order": [vp, ctypes.c_int],
         "spamm_add": [vp, f64, vp, f64, vp, ctypes.POINTER(vp)],
         "spamm_identity": [vp, i64, ctypes.c_int, ctypes.POINTER(vp)],
         "spamm_trace": [vp, vp, pf64],
@@ -560,6 +561,15 @@ def spamm_trace(ctx: Context, X: Matrix) -> float:
 def spamm_check_timeout_path(ctx: Context, wait_ns: int = 50_000_000) -> int:
     """Run the device-timeout diagnostic; returns the raw status (E_TIMEOUT expected)."""
     return int(load().spamm_check_timeout_path(ctx.handle, int(wait_ns)))
+
+
+ORDERS = {"auto": 0, "morton": 1, "longest": 2}
+
+
+def spamm_set_claim_order(ctx: Context, order: str):
+    """spamm_set_claim_order: the work units' claiming order of the plans
+    created afterwards on ctx ("auto", "morton" or "longest")."""
+    _check(ctx.handle, load().spamm_set_claim_order(ctx.handle, ORDERS[order]))
 
 
 def spamm_set_exec_graph(ctx: Context, enable: bool):

@@ -70,3 +70,19 @@ def test_truncation_error_per_leaf_size_and_rates(tmp_path):
     assert t.choose(4096, 1.0, 1e-6) == Choice("bf16_split4", 128)
     assert t.rate("bf16_split4", 64) == 51000.0 and t.rate("fp16_scaled", 64) is None
     assert autotune.load(path)[0].estimated == ("fp64/128",)
+
+
+def test_claim_order_is_part_of_the_choice_and_round_trips(tmp_path):
+    from paper_1906_08148_gb300.autotune import Autotuner, Choice, Point, load, save
+    pts = [Point(16384, 1.0, 1e-6, Choice("fp16_scaled", 64, "longest"), {"fp16_scaled/64": 5.0, "fp64/64": 900.0},
+                 {"fp16_scaled/64": 1e-6}, {"64": 1e-4}, {"fp16_scaled/64": 1.5e5}, (), {"morton": 5.2, "longest": 4.9}),
+           Point(4096, 1.0, 1e-8, Choice("fp64", 64), {"fp64/64": 90.0}, {}, {"64": 0.0})]
+    path = str(tmp_path / "t.json")
+    save(pts, path)
+    back = load(path)
+    assert back[0].choice == Choice("fp16_scaled", 64, "longest") and back[0].order_ms["longest"] == 4.9
+    assert back[1].choice.order == "auto"
+    tuner = Autotuner(back)
+    assert tuner.choose(16384, 1.0, 1e-6).order == "longest"
+    # a given leaf size keeps the point's order when its winner has that size
+    assert tuner.choose(16384, 1.0, 1e-6, bs=64) == Choice("fp16_scaled", 64, "longest")

@@ -236,3 +236,32 @@ def test_sliced_jobs_equal_one_execute_bitwise(S, ctx, prec, bs):
         S.spamm_job_finish(ctx, j)
     assert err.value.status == S.E_BUSY
     j.close()
+
+
+@pytest.mark.parametrize("prec,bs", [("fp64", 64), ("fp64", 128), ("fp16_scaled", 64), ("bf16_split4", 64),
+                                     ("bf16_split4", 128)])
+def test_claim_order_keeps_results_bitwise(S, ctx, prec, bs):
+    """The tile schedule (spamm_set_claim_order) changes only the order in which
+    CTAs claim work units: every order gives the same bits, in one launch and
+    in sliced execution."""
+    GA, GB = _inputs(S, ctx, 4096, 0.8, bs)
+    outs = {}
+    try:
+        for order in ("morton", "longest", "auto"):
+            S.spamm_set_claim_order(ctx, order)
+            p = S.spamm_plan_create(ctx, GA, GB, 1e-7, "combined", prec)
+            C = S.spamm_execute(ctx, [p])[0]
+            outs[order] = S.spamm_to_blocks(ctx, C)
+            j = S.spamm_job_begin(ctx, p)
+            while j.info()["units_done"] < j.info()["units"]:
+                S.spamm_run(ctx, [j], [j.info()["work"] / 5.0 + 1.0])
+            Cj = S.spamm_job_finish(ctx, j)
+            for x, y in zip(outs[order], S.spamm_to_blocks(ctx, Cj)):
+                assert np.array_equal(x, y)
+            j.close()
+    finally:
+        S.spamm_set_claim_order(ctx, "auto")
+    for order in ("longest", "auto"):
+        for x, y in zip(outs["morton"], outs[order]):
+            assert np.array_equal(x, y)
+    assert S.load().spamm_set_claim_order(ctx.handle, 7) == S.E_INVALID_ARG
