@@ -1274,8 +1274,9 @@ def roofline(prec, bs, kept, ms_gemm, executed_flops):
         return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                 "frac": achieved / FP64_PEAK_GFLOPS, "traffic": load_traffic(kernel, kept),
                 "peak_source": "FP64 DFMA units x clock (derived; no FP64 entry in MEASURED_PEAKS.json)"}
-    peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops_sustained": 1700.0}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = _json.load(open(path)) if os.path.exists(path) else {}
+    measured = "bf16_tflops_sustained" in peaks
     peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
     achieved = algo / secs / 1e12
     executed = executed_flops / secs / 1e12
@@ -1283,7 +1284,9 @@ def roofline(prec, bs, kept, ms_gemm, executed_flops):
     return {"kernel": kernel, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "executed": executed, "executed_frac": executed / peak,
             "traffic": load_traffic(kernel, kept),
-            "peak_source": "bf16 dense sustained, measured (fp16 dense has the same nominal rate)"}
+            "peak_source": ("bf16 dense sustained, of measured (MEASURED_PEAKS.json)" if measured else
+                            "bf16 dense sustained, of fallback (1.7 PFLOP/s; MEASURED_PEAKS.json absent)")
+                           + "; fp16 dense has the same nominal rate"}
 
 
 def load_traffic(kernel, kept):

@@ -593,6 +593,11 @@ std::vector<spamm_mat> execute_plans(spamm_ctx ctx, const std::vector<spamm_plan
       updated = cudaGraphExecUpdate(ctx->graph_exec, g, &info) == cudaSuccess;
       if (!updated) {
         cudaGetLastError();
+        // not an error: the graph is re-instantiated; the reason is kept for diagnosis
+        cudaGraphNodeType nt = cudaGraphNodeTypeEmpty;
+        if (info.errorNode) cudaGraphNodeGetType(info.errorNode, &nt);
+        ctx->last_error = "execute graph re-instantiated: update result " + std::to_string((int)info.result) +
+                          ", node type " + std::to_string((int)nt);
         cudaGraphExecDestroy(ctx->graph_exec);
         ctx->graph_exec = nullptr;
       }

@@ -118,7 +118,7 @@ def test_graph_execute_equals_eager(S, ctx, prec):
         single = S.spamm_multiply(ctx, keep[0][0], keep[0][1], REQUESTS[0][2], REQUESTS[0][3], prec)
     finally:
         S.spamm_set_exec_graph(ctx, False)
-    assert g1["updates"] >= g0["updates"] + 1
+    assert g1["updates"] >= g0["updates"] + 1, S.load().spamm_last_error(ctx.handle)
     for G, A in zip(graph, again):
         assert np.array_equal(S.spamm_to_blocks(ctx, G)[2], S.spamm_to_blocks(ctx, A)[2])
     for r, (E, G) in enumerate(zip(eager, graph)):
