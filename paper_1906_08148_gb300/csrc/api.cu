@@ -509,8 +509,7 @@ PlanDev slice_view(const spamm_plan_s& p, const PlanDev& d, int64_t first) {
   } else if (v.uorder) {
     v.uorder += first;  // units in claiming order; steps and outputs indexed by the unit itself
   } else {
-    v.qstart += first;  // quads; their output leaves are named in quads[] itself
-    v.quads += 4 * first;
+    v.ufirst = first;  // steps and outputs indexed by the unit itself (a 128-leaf unit is its output leaf)
   }
   return v;
 }

@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
         if (un < 0) break;
         const int r = plan_of(batch.ubegin, batch.nplans, un);
         const PlanDev& pl = batch.plans[r];
-        const int64_t Qc = un - batch.ubegin[r], Q = pl.uorder ? pl.uorder[Qc] : Qc;
+        const int64_t Qc = un - batch.ubegin[r], Q = pl.uorder ? pl.uorder[Qc] : pl.ufirst + Qc;
         const int64_t j1 = pl.qstart[Q + 1];
         int64_t j = pl.qstart[Q];
         const int4* rec = reinterpret_cast<const int4*>(pl.qsteps);  // word 2j: a0, a1, b0, b1 of step j
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
         if (un < 0) break;
         const int r = plan_of(batch.ubegin, batch.nplans, un);
         const PlanDev& pl = batch.plans[r];
-        const int64_t Qc = un - batch.ubegin[r], Q = pl.uorder ? pl.uorder[Qc] : Qc;
+        const int64_t Qc = un - batch.ubegin[r], Q = pl.uorder ? pl.uorder[Qc] : pl.ufirst + Qc;
         const int64_t nstep = pl.qstart[Q + 1] - pl.qstart[Q];
         for (int64_t j = 0; j < nstep && !stop; ++j) {
 #pragma unroll
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
       }
       const int r = plan_of(batch.ubegin, batch.nplans, un);
       const PlanDev& pl = batch.plans[r];
-      const int64_t Qc = un - batch.ubegin[r], Q = pl.uorder ? pl.uorder[Qc] : Qc;
+      const int64_t Qc = un - batch.ubegin[r], Q = pl.uorder ? pl.uorder[Qc] : pl.ufirst + Qc;
       // children: four output leaves (64-leaves), or the four quadrants of output leaf Q (128-leaves)
       const bool big = pl.tc_bs == 128;
       const int32_t g[4] = {big ? (int32_t)Q : pl.quads[4 * Q], big ? (int32_t)Q : pl.quads[4 * Q + 1],

@@ -217,6 +217,7 @@ struct PlanDev {
   const int64_t* uorder;  // unit (FP64: output leaf; tensor forms: quad or 128-leaf) at each claiming position, or null for identity
   double* csq_part;       // FP64 form, leaves split into sub-tile units: partial squared norms [leaf][sub-tile]
   int32_t tc_bs;          // tensor forms: 64 (units are quads of output leaves) or 128 (units are output leaves)
+  int64_t ufirst;         // tensor forms without uorder: unit number of this view's unit 0 (sliced execution)
 };
 struct BatchDev {
   const PlanDev* plans;

@@ -198,7 +198,8 @@ def test_graph_and_batch_with_subtile_units(S, ctx, bs):
 
 
 @pytest.mark.parametrize("prec,bs", [("fp64", 64), ("fp64", 32), ("fp64", 128), ("fp64", 256), ("bf16_split", 64),
-                                     ("bf16_split4", 64), ("fp16_scaled", 64)])
+                                     ("bf16_split4", 64), ("fp16_scaled", 64), ("bf16_split4", 128),
+                                     ("fp16_scaled", 128)])
 def test_sliced_jobs_equal_one_execute_bitwise(S, ctx, prec, bs):
     """Sliced execution (spamm_job_begin / spamm_run / spamm_job_finish):
     several jobs run their units in many small launches, a job joining
