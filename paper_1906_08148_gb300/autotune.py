@@ -193,8 +193,26 @@ def calibrate(S, ctx, grid: Iterable[tuple], repeats: int = 2, mode: str = "comb
 
 def _measure_point(S, ctx, pa, pb, tau, mode, repeats, fp64_rate, ms, arith, trunc, rate, est):
     """Every candidate at one grid point (inputs truncated while generated at
-    tau / 100, exact for the combined method at tau and at tau / 100).  Every
-    handle is released on the way out, also when a candidate does not fit."""
+    tau / 100, exact for the combined method at tau and at tau / 100).  A leaf
+    size whose inputs or products do not fit leaves its candidates out (the
+    others are still measured); every handle is released on the way out."""
+    for bs in sorted({b for _, b in CANDIDATES}):
+        try:
+            _measure_bs(S, ctx, pa, pb, tau, mode, repeats, fp64_rate, ms, arith, trunc, rate, est, bs)
+        except S.SpammError as e:
+            if e.status != S.E_OOM:
+                raise
+            for prec, b in CANDIDATES:
+                if b == bs:
+                    ms.pop(_name(prec, bs), None)
+                    arith.pop(_name(prec, bs), None)
+            trunc.pop(str(bs), None)
+            S.spamm_trim(ctx)
+    if not ms:
+        raise S.SpammError(S.E_OOM, "no candidate fits")
+
+
+def _measure_bs(S, ctx, pa, pb, tau, mode, repeats, fp64_rate, ms, arith, trunc, rate, est, bs):
     held = []
 
     def keep(h):
@@ -206,53 +224,48 @@ def _measure_point(S, ctx, pa, pb, tau, mode, repeats, fp64_rate, ms, arith, tru
         h.close()
 
     try:
-        for bs in sorted({b for _, b in CANDIDATES}):
-            GA = keep(S.spamm_generate(ctx, pa, bs, tau / 100.0))
-            GB = keep(S.spamm_generate(ctx, pb, bs, tau / 100.0))
-            tensor = [p for p, b in CANDIDATES if b == bs and p != "fp64"]
-            ref = None
-            if tensor:
-                ref, _ = S.spamm_multiply(ctx, GA, GB, tau, mode, "bf16_split4", stats=True)
-                keep(ref)
-                fine = keep(S.spamm_multiply(ctx, GA, GB, tau / 100.0, mode, "bf16_split4"))
-                trunc[str(bs)] = S.spamm_error(ctx, fine, ref)
-                drop(fine)
-            for prec, cbs in CANDIDATES:
-                if cbs != bs:
+        GA = keep(S.spamm_generate(ctx, pa, bs, tau / 100.0))
+        GB = keep(S.spamm_generate(ctx, pb, bs, tau / 100.0))
+        tensor = [p for p, b in CANDIDATES if b == bs and p != "fp64"]
+        ref = None
+        if tensor:
+            ref, _ = S.spamm_multiply(ctx, GA, GB, tau, mode, "bf16_split4", stats=True)
+            keep(ref)
+            fine = keep(S.spamm_multiply(ctx, GA, GB, tau / 100.0, mode, "bf16_split4"))
+            trunc[str(bs)] = S.spamm_error(ctx, fine, ref)
+            drop(fine)
+        for prec, cbs in CANDIDATES:
+            if cbs != bs:
+                continue
+            k = _name(prec, bs)
+            if prec == "fp64" and bs in fp64_rate:
+                plan = keep(S.spamm_plan_create(ctx, GA, GB, tau, mode, "fp64"))
+                nk = plan.info()["n_kept"]
+                drop(plan)
+                if nk / fp64_rate[bs] > FP64_TIMED_MAX_S:
+                    ms[k] = 1e3 * nk / fp64_rate[bs]  # too long to time here: estimated from its rate
+                    est.append(k)
                     continue
-                k = _name(prec, bs)
-                if prec == "fp64" and bs in fp64_rate:
-                    plan = keep(S.spamm_plan_create(ctx, GA, GB, tau, mode, "fp64"))
-                    nk = plan.info()["n_kept"]
-                    drop(plan)
-                    if nk / fp64_rate[bs] > FP64_TIMED_MAX_S:
-                        ms[k] = 1e3 * nk / fp64_rate[bs]  # too long to time here: estimated from its rate
-                        est.append(k)
-                        continue
-                times, st, C = [], None, None
-                for _ in range(repeats + 1):  # the first run warms up
-                    if C is not None:
-                        drop(C)
-                    t0 = time.perf_counter()
-                    C, st = S.spamm_multiply(ctx, GA, GB, tau, mode, prec, stats=True)
-                    times.append(time.perf_counter() - t0)
-                    keep(C)
-                    if prec == "fp64" and times[-1] > FP64_TIMED_MAX_S:
-                        break
-                tm = sorted(times[1:])[len(times[1:]) // 2] if len(times) > 1 else times[0]
-                ms[k] = 1e3 * tm
-                rate[k] = st["n_steps"] / st["ms_gemm"] if st["ms_gemm"] > 0 else None
-                if prec == "fp64":
-                    fp64_rate[bs] = st["n_kept"] / max(tm, 1e-9)
-                if ref is not None:
-                    arith[k] = S.spamm_error(ctx, ref, C) if prec != "fp64" else 0.0
-                    if prec == "fp64":  # the reference's own error, where FP64 ran
-                        arith[_name("bf16_split4", bs) + ":vs_fp64"] = S.spamm_error(ctx, C, ref)
-                drop(C)
+            times, st, C = [], None, None
+            for _ in range(repeats + 1):  # the first run warms up
+                if C is not None:
+                    drop(C)
+                t0 = time.perf_counter()
+                C, st = S.spamm_multiply(ctx, GA, GB, tau, mode, prec, stats=True)
+                times.append(time.perf_counter() - t0)
+                keep(C)
+                if prec == "fp64" and times[-1] > FP64_TIMED_MAX_S:
+                    break
+            tm = sorted(times[1:])[len(times[1:]) // 2] if len(times) > 1 else times[0]
+            ms[k] = 1e3 * tm
+            rate[k] = st["n_steps"] / st["ms_gemm"] if st["ms_gemm"] > 0 else None
+            if prec == "fp64":
+                fp64_rate[bs] = st["n_kept"] / max(tm, 1e-9)
             if ref is not None:
-                drop(ref)
-            drop(GA)
-            drop(GB)
+                arith[k] = S.spamm_error(ctx, ref, C) if prec != "fp64" else 0.0
+                if prec == "fp64":  # the reference's own error, where FP64 ran
+                    arith[_name("bf16_split4", bs) + ":vs_fp64"] = S.spamm_error(ctx, C, ref)
+            drop(C)
     finally:
         for h in reversed(held):
             h.close()
