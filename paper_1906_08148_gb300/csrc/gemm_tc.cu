@@ -88,14 +88,16 @@ constexpr int kQuadQ = 4;     // ring of claimed quads shared by the three roles
 template <int PREC>
 struct QuadLayout {
   using Cfg = FormCfg<PREC>;
-  static constexpr uint32_t TILE = Cfg::KHALF ? kHalfTerm : kTerm;
-  static constexpr int SPS = Cfg::KHALF ? 2 : 1;  // stages per step
-  static constexpr int KS = Cfg::KHALF ? 2 : 4;   // K = 16 MMAs per stage
+  static constexpr uint32_t TILE = kTerm / Cfg::KPARTS;
+  static constexpr int SPS = Cfg::KPARTS;      // stages per step
+  static constexpr int KS = 4 / Cfg::KPARTS;   // K = 16 MMAs per stage
   static constexpr uint32_t BREG = (uint32_t)Cfg::TERMS * 2 * TILE;
   static constexpr uint32_t STAGE = 2 * BREG;
   static constexpr size_t SMEM = 1024 + (size_t)Cfg::NS * STAGE;
   __device__ static uint64_t desc(uint32_t saddr) {
-    return Cfg::KHALF ? sw64_kmajor_desc(saddr) : sw128_kmajor_desc(saddr);
+    if constexpr (Cfg::KPARTS == 1) return sw128_kmajor_desc(saddr);
+    if constexpr (Cfg::KPARTS == 2) return sw64_kmajor_desc(saddr);
+    return sw32_kmajor_desc(saddr);
   }
 };
 
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
             for (int term = 0; term < TERMS; ++term) {
               uint8_t* sa = st + term * 2 * TILE;
               uint8_t* sb = st + BREG + term * 2 * TILE;
-              const int64_t off = Cfg::KHALF ? (int64_t)(h * TERMS + term) * kHalfTerm : (int64_t)term * kTerm;
+              const int64_t off = (int64_t)(h * TERMS + term) * TILE;
               if (ab.x >= 0) bulk_g2s(sa, pl.termsA + (int64_t)ab.x * LEAF + off, TILE, &full[s]);
               if (ab.y >= 0) bulk_g2s(sa + TILE, pl.termsA + (int64_t)ab.y * LEAF + off, TILE, &full[s]);
               if (ab.z >= 0) bulk_g2s(sb, pl.termsB + (int64_t)ab.z * LEAF + off, TILE, &full[s]);

@@ -55,7 +55,7 @@ __device__ __forceinline__ const double* tile_src(const double* leaf, int bs, in
 // of the leaf, the leaf's scale exponent f (stored in expo[m]), then every
 // element's S digits (slices.cuh) as BF16 values d_s 2^(e - 8 - 9 s).  The
 // slices are assembled in shared memory and leave as one contiguous block.
-template <int S, bool KHALF>
+template <int S, int KPARTS>
 __global__ void __launch_bounds__(256) prep_slices_kernel(const double* __restrict__ pool,
                                                           const int64_t* __restrict__ slot, int64_t nleaves, int bs,
                                                           int role, uint8_t* __restrict__ out,
@@ -119,11 +119,7 @@ __global__ void __launch_bounds__(256) prep_slices_kernel(const double* __restri
       }
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        uint32_t off;
-        if constexpr (KHALF)
-          off = ((uint32_t)(cm.c8[j] >> 2) * S + s) * kHalfTerm + sw64_offset(cm.row[j], 8 * (cm.c8[j] & 3));
-        else
-          off = (uint32_t)s * kTerm + sw128_offset(cm.row[j], 8 * cm.c8[j]);
+        const uint32_t off = term_offset<KPARTS>(S, s, cm.row[j], 8 * cm.c8[j]);
         stile[off >> 4] = *reinterpret_cast<const uint4*>(term[s]);
       }
     }
@@ -196,7 +192,8 @@ __global__ void __launch_bounds__(256) prep_fp16_kernel(const double* __restrict
       }
 #pragma unroll
       for (int s = 0; s < TERMS; ++s)
-        *reinterpret_cast<uint4*>(dst + s * kTerm + sw128_offset(cm.row[j], 8 * cm.c8[j])) =
+        *reinterpret_cast<uint4*>(dst + term_offset<FormCfg<SPAMM_PREC_FP16_SCALED>::KPARTS>(TERMS, s, cm.row[j],
+                                                                                          8 * cm.c8[j])) =
             *reinterpret_cast<const uint4*>(term[s]);
     }
     __syncthreads();  // smax and s_shift are reused by the next leaf
@@ -223,11 +220,11 @@ void prep_terms(spamm_mat M, spamm_prec prec, int role, BufP* terms, BufP* expo,
   const double* pool = P<double>(M->pool);
   const int64_t* slot = P<int64_t>(M->slot);
   if (prec == SPAMM_PREC_BF16_SPLIT) {
-    prep_slices_kernel<3, false><<<grid, 256, 0, ctx->stream>>>(pool, slot, M->nleaves, bs, role,
+    prep_slices_kernel<3, FormCfg<SPAMM_PREC_BF16_SPLIT>::KPARTS><<<grid, 256, 0, ctx->stream>>>(pool, slot, M->nleaves, bs, role,
                                                                 P<uint8_t>(*terms), P<int32_t>(*expo));
     CK_LAUNCH("prep_slices_kernel<3>");
   } else if (prec == SPAMM_PREC_BF16_SPLIT4) {
-    prep_slices_kernel<4, true><<<grid, 256, 0, ctx->stream>>>(pool, slot, M->nleaves, bs, role,
+    prep_slices_kernel<4, FormCfg<SPAMM_PREC_BF16_SPLIT4>::KPARTS><<<grid, 256, 0, ctx->stream>>>(pool, slot, M->nleaves, bs, role,
                                                                P<uint8_t>(*terms), P<int32_t>(*expo));
     CK_LAUNCH("prep_slices_kernel<4>");
   } else {

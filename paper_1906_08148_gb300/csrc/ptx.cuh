@@ -200,6 +200,13 @@ __device__ __forceinline__ uint64_t sw64_kmajor_desc(uint32_t saddr) {
          ((uint64_t)1u << 46) | ((uint64_t)4u << 61);
 }
 
+// The same for the 32-byte swizzle: rows of 32 bytes, 8-row atoms of 256
+// bytes (stride byte offset), base 256-byte aligned; layout type 6 (SWIZZLE_32B).
+__device__ __forceinline__ uint64_t sw32_kmajor_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(256u >> 4) << 32) |
+         ((uint64_t)1u << 46) | ((uint64_t)6u << 61);
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulator, A and B of format
 // `ab` (0 = f16, 1 = bf16), both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t umma_idesc_f16(uint32_t ab, uint32_t M, uint32_t N) {
