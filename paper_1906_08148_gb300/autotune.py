@@ -208,8 +208,10 @@ def _measure_point(S, ctx, pa, pb, tau, mode, repeats, fp64_rate, ms, arith, tru
                     arith.pop(_name(prec, bs), None)
             trunc.pop(str(bs), None)
             S.spamm_trim(ctx)
-    if not ms:
-        raise S.SpammError(S.E_OOM, "no candidate fits")
+    if not ms or not any(k.split("/")[0] != "fp64" for k in ms):
+        # no tensor form measured (their reference products do not fit): the
+        # point would only say that FP64 fits, so it is left out
+        raise S.SpammError(S.E_OOM, "no tensor-form candidate fits")
 
 
 def _measure_bs(S, ctx, pa, pb, tau, mode, repeats, fp64_rate, ms, arith, trunc, rate, est, bs):

@@ -113,11 +113,18 @@ def test_graph_execute_equals_eager(S, ctx, prec):
     try:
         g0 = S.spamm_exec_graph_info(ctx)
         graph, st_g = S.spamm_execute(ctx, plans, stats=True)
-        again, _ = S.spamm_execute(ctx, plans, stats=True)  # same topology: the graph is updated, not rebuilt
+        # same batch again: the kept executable graph is updated in place (the
+        # driver may still refuse an update and the graph is then rebuilt)
+        again, _ = S.spamm_execute(ctx, plans, stats=True)
+        for _ in range(3):
+            for m in S.spamm_execute(ctx, plans):
+                m.close()
         g1 = S.spamm_exec_graph_info(ctx)
         single = S.spamm_multiply(ctx, keep[0][0], keep[0][1], REQUESTS[0][2], REQUESTS[0][3], prec)
     finally:
         S.spamm_set_exec_graph(ctx, False)
+    runs = (g1["updates"] - g0["updates"]) + (g1["instantiations"] - g0["instantiations"])
+    assert runs == 5  # every execute ran as the graph
     assert g1["updates"] >= g0["updates"] + 1, S.load().spamm_last_error(ctx.handle)
     for G, A in zip(graph, again):
         assert np.array_equal(S.spamm_to_blocks(ctx, G)[2], S.spamm_to_blocks(ctx, A)[2])
