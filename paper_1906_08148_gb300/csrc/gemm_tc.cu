@@ -49,10 +49,9 @@
 // Warp roles (one CTA per SM, persistent; quads are claimed one at a time
 // from a global counter in Morton order, so the quads in flight on all SMs
 // form one narrow window whose A rows and B columns are shared in L2):
-//   warp 0     TMA producer: lane 0 claims the next quad for all roles (a
-//              ring of 4 in shared memory) and runs the ring of NS stages; a
-//              stage's 1-D bulk copies of pre-swizzled term tiles are issued
-//              by as many lanes, each completing on the stage's mbarrier.
+//   warp 0     TMA producer: claims the next quad for all roles (a ring of 4
+//              in shared memory), ring of NS stages, 1-D bulk copies of
+//              pre-swizzled term tiles, mbarriers.
 //   warp 1     allocates 512 TMEM columns and issues the MMAs of each step.
 //   warps 2-3  idle (they fill the first warpgroup, see the register split)
 //   warps 4-11 epilogue: warps 4-7 column 0, warps 8-11 column 1; TMEM lane =
@@ -205,77 +204,61 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
   if (warp < 4) {
     regs_dec<kCtlRegs>();  // every warp of warpgroup 0, at this one instruction
   if (warp == 0) {
-    // ---------------- TMA producer, one warp: lane 0 claims the quads (Morton
-    // order, first come first served) for all roles and waits on the stages;
-    // the bulk copies of a stage (one per leaf and term) are issued by
-    // different lanes, so their issue does not serialise on one thread
-    int64_t t = 0;  // stages filled
-    bool stop = false;
-    for (int64_t c = 0; !stop; ++c) {
-      const int qs = (int)(c % kQuadQ);
-      long long un = -1;
-      int ok = 1;
-      if (lane == 0) {
+    // ---------------- TMA producer; claims the quads (Morton order, first come first served) for all roles
+    if (lane == 0) {
+      int64_t t = 0;  // stages filled
+      bool stop = false;
+      for (int64_t c = 0; !stop; ++c) {
+        const int qs = (int)(c % kQuadQ);
         if (c >= kQuadQ && !mbar_wait_or_abort(&qempty[qs], (uint32_t)(((c / kQuadQ) - 1) & 1), abortp)) {
           atomicOr(err, DEV_ERR_TIMEOUT);
           *abortp = 1;
-          ok = 0;
-        } else {
-          const int64_t claimed = (int64_t)atomicAdd(work, 1ull);
-          un = claimed < batch.nunits ? claimed : -1;
-          qid[qs] = un;
-          mbar_arrive(&qfull[qs]);
+          break;
         }
-      }
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      un = __shfl_sync(0xffffffffu, un, 0);
-      if (!ok || un < 0) break;
-      const int r = plan_of(batch.ubegin, batch.nplans, un);
-      const PlanDev& pl = batch.plans[r];
-      const int64_t Qc = un - batch.ubegin[r], Q = pl.uorder ? pl.uorder[Qc] : pl.ufirst + Qc;
-      const int64_t j1 = pl.qstart[Q + 1];
-      int64_t j = pl.qstart[Q];
-      const int4* rec = reinterpret_cast<const int4*>(pl.qsteps);  // word 2j: a0, a1, b0, b1 of step j
-      int4 nx = j < j1 ? __ldg(rec + 2 * j) : make_int4(-1, -1, -1, -1);
-      for (; j < j1 && !stop; ++j) {
-        const int4 ab = nx;
-        if (j + 1 < j1) nx = __ldg(rec + 2 * (j + 1));  // next step's leaves, in flight during the wait
-        const uint32_t nload = (uint32_t)((ab.x >= 0) + (ab.y >= 0) + (ab.z >= 0) + (ab.w >= 0));
-        // this lane's copy: term lane / 4 of leaf lane % 4 (A rows 2I, 2I+1, B columns 2J, 2J+1)
-        const int term = lane >> 2, which = lane & 3;
-        const int leaf = which == 0 ? ab.x : (which == 1 ? ab.y : (which == 2 ? ab.z : ab.w));
-        const bool mine = lane < 4 * TERMS && leaf >= 0;
+        const int64_t claimed = (int64_t)atomicAdd(work, 1ull);
+        const int64_t un = claimed < batch.nunits ? claimed : -1;
+        qid[qs] = un;
+        mbar_arrive(&qfull[qs]);
+        if (un < 0) break;
+        const int r = plan_of(batch.ubegin, batch.nplans, un);
+        const PlanDev& pl = batch.plans[r];
+        const int64_t Qc = un - batch.ubegin[r], Q = pl.uorder ? pl.uorder[Qc] : pl.ufirst + Qc;
+        const int64_t j1 = pl.qstart[Q + 1];
+        int64_t j = pl.qstart[Q];
+        const int4* rec = reinterpret_cast<const int4*>(pl.qsteps);  // word 2j: a0, a1, b0, b1 of step j
+        int4 nx = j < j1 ? __ldg(rec + 2 * j) : make_int4(-1, -1, -1, -1);
+        for (; j < j1 && !stop; ++j) {
+          const int4 ab = nx;
+          if (j + 1 < j1) nx = __ldg(rec + 2 * (j + 1));  // next step's leaves, in flight during the wait
+          const uint32_t nload = (uint32_t)((ab.x >= 0) + (ab.y >= 0) + (ab.z >= 0) + (ab.w >= 0));
 #pragma unroll
-        for (int h = 0; h < SPS; ++h) {
-          const int s = (int)(t % NS);
-          int ok2 = 1;
-          if (lane == 0) {
+          for (int h = 0; h < SPS; ++h) {
+            const int s = (int)(t % NS);
             if (t >= NS && !mbar_wait_or_abort(&empty[s], (uint32_t)(((t / NS) - 1) & 1), abortp)) {
               atomicOr(err, DEV_ERR_TIMEOUT);
               *abortp = 1;
-              ok2 = 0;
-            } else {
-              mbar_arrive_expect_tx(&full[s], nload * TERMS * TILE);
+              stop = true;
+              break;
             }
+            uint8_t* st = smem + s * STAGE;
+            mbar_arrive_expect_tx(&full[s], nload * TERMS * TILE);
+#pragma unroll
+            for (int term = 0; term < TERMS; ++term) {
+              uint8_t* sa = st + term * 2 * TILE;
+              uint8_t* sb = st + BREG + term * 2 * TILE;
+              const int64_t off = (int64_t)(h * TERMS + term) * TILE;
+              if (ab.x >= 0) bulk_g2s(sa, pl.termsA + (int64_t)ab.x * LEAF + off, TILE, &full[s]);
+              if (ab.y >= 0) bulk_g2s(sa + TILE, pl.termsA + (int64_t)ab.y * LEAF + off, TILE, &full[s]);
+              if (ab.z >= 0) bulk_g2s(sb, pl.termsB + (int64_t)ab.z * LEAF + off, TILE, &full[s]);
+              if (ab.w >= 0) bulk_g2s(sb + TILE, pl.termsB + (int64_t)ab.w * LEAF + off, TILE, &full[s]);
+            }
+            ++t;
           }
-          ok2 = __shfl_sync(0xffffffffu, ok2, 0);  // the expected bytes are set before any copy is issued
-          if (!ok2) {
-            stop = true;
-            break;
-          }
-          if (mine) {
-            uint8_t* dst = smem + s * STAGE + (which >= 2 ? BREG : 0u) + term * 2 * TILE + (which & 1) * TILE;
-            const uint8_t* src = (which >= 2 ? pl.termsB : pl.termsA) + (int64_t)leaf * LEAF +
-                                 (int64_t)(h * TERMS + term) * TILE;
-            bulk_g2s(dst, src, TILE, &full[s]);
-          }
-          ++t;
         }
       }
-    }
-    // leave no bulk copy in flight: the last fill of every stage has landed
-    if (lane == 0)
+      // leave no bulk copy in flight: the last fill of every stage has landed
       for (int64_t k = (t > NS ? t - NS : 0); k < t; ++k) mbar_wait_bounded(&full[k % NS], (uint32_t)((k / NS) & 1));
+    }
   } else if (warp == 1) {
     // ---------------- MMA issuer: the accumulators of step number n are slots (NACC n + a) % NB
     if (lane == 0) {
