@@ -258,12 +258,12 @@ __global__ void level_finish_kernel(const uint64_t* __restrict__ tot, unsigned l
 }
 
 // Upper bounds on the next level's sizes below which the host does not wait
-// for the exact counts: buffers are allocated at the bound instead (8 Q pairs
-// of 8 bytes and 4 G groups: at most 512 MB and 16 M groups), so the descent
-// of a problem of tens of millions of leaf products waits once, near the
-// bottom, and reads every size back at the end.
-constexpr int64_t kPairsNoSync = 1ll << 26;
-constexpr int64_t kGroupsNoSync = 1ll << 24;
+// for the exact counts (buffers are allocated at the bound instead).  The
+// leaf level always waits: its arrays are the plan's task list, kept for the
+// leaf products.  (Waiting less often measured slower: the kernels of a level
+// allocated at the bound run over the bound, 4 G groups, and the scan too.)
+constexpr int64_t kPairsNoSync = 1ll << 22;
+constexpr int64_t kGroupsNoSync = 1ll << 20;
 
 TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm_ctx on) {
   spamm_ctx ctx = on ? on : A->ctx;
@@ -340,7 +340,7 @@ TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm
     scan_exclusive_u64(ctx, P<uint64_t>(packed), P<uint64_t>(off), 4 * G, P<uint64_t>(tot));
     // capacities of the next level: exact after a wait, else the bounds 8 Q and 4 G
     int64_t Q2 = 8 * Q, G2 = 4 * G;
-    const bool wait = Q2 > kPairsNoSync || G2 > kGroupsNoSync;
+    const bool wait = Q2 > kPairsNoSync || G2 > kGroupsNoSync || leaf;
     BufP gstart2;
     if (wait) {
       CK(cudaMemcpyAsync(hp, P<uint64_t>(tot), sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
