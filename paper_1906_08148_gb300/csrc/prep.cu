@@ -29,11 +29,24 @@ struct ChunkMap {
   }
   // src: the tile's first element; ld: the leaf's row length
   __device__ void load(const unsigned long long* src, int ld, int role, unsigned long long (&v)[2][8]) const {
+    if (role == 0) {
+      // 8 consecutive doubles of one row: four 16-byte loads
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
+      for (int j = 0; j < 2; ++j) {
+        const ulonglong2* p = reinterpret_cast<const ulonglong2*>(src + row[j] * ld + 8 * c8[j]);
 #pragma unroll
-      for (int e = 0; e < 8; ++e)
-        v[j][e] = role == 0 ? __ldg(src + row[j] * ld + 8 * c8[j] + e) : __ldg(src + (8 * c8[j] + e) * ld + row[j]);
+        for (int e = 0; e < 4; ++e) {
+          const ulonglong2 w = __ldg(p + e);
+          v[j][2 * e] = w.x;
+          v[j][2 * e + 1] = w.y;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[j][e] = __ldg(src + (8 * c8[j] + e) * ld + row[j]);
+    }
   }
 };
 

@@ -66,7 +66,7 @@ SLICE_HD void slice_digits(uint64_t b, int emax_line, int32_t* d) {
     int32_t t = (int32_t)(M & 511);
     if (t >= 256) t -= 512;
     d[s] = t;
-    M = (M - t) / 512;  // exact: M - t is a multiple of 512
+    M = (M - t) >> 9;  // exact: M - t is a multiple of 512 (arithmetic shift of a two's-complement multiple)
   }
   d[0] = (int32_t)M;
 }
@@ -94,8 +94,12 @@ SLICE_HD float slice_f32_from_bits(uint32_t u) {
 // BF16 bits of d 2^p (|d| <= 256, so at most 8 significant bits: exact).
 // A digit whose unit 2^p lies below the FP32 normal range (p < -126) is
 // dropped: with the leaf scaled to max|x| in [1, 2) it is below 2^-118.
+// The integer d becomes a float without a conversion instruction: 1.5 2^23 + d
+// is a float whose low mantissa bits are d (|d| < 2^22), and subtracting
+// 1.5 2^23 leaves d exactly; scaling by 2^p is exact too.
 SLICE_HD uint16_t slice_bf16_bits(int32_t d, int p) {
-  if (d == 0 || p < -126) return 0;
-  const float v = (float)d * slice_f32_from_bits((uint32_t)(p + 127) << 23);
+  if (p < -126) return 0;
+  const float f = slice_f32_from_bits(0x4B400000u + (uint32_t)d) - 12582912.0f;
+  const float v = f * slice_f32_from_bits((uint32_t)(p + 127) << 23);
   return (uint16_t)(slice_f32_bits(v) >> 16);
 }
