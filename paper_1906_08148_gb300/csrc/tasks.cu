@@ -148,14 +148,27 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       for (int c = 0; c < 4; ++c) packed[4 * g + c] = (uint64_t)cnt[c] | ((uint64_t)(cnt[c] > 0) << 36);
     }
   }
+  // the level's counters: warp sums, then one atomic per block (atomics on one
+  // address from every warp of the grid would queue at a single L2 slice)
+  __shared__ long long s_cnt[kWarpsPerBlock][2];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     cand += __shfl_xor_sync(0xffffffffu, cand, off);
     border += __shfl_xor_sync(0xffffffffu, border, off);
   }
-  if (lane == 0 && (cand || border)) {
-    atomicAdd(stats + 0, (unsigned long long)cand);
-    atomicAdd(stats + 1, (unsigned long long)border);
+  if (lane == 0) {
+    s_cnt[threadIdx.x >> 5][0] = cand;
+    s_cnt[threadIdx.x >> 5][1] = border;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long c = 0, b = 0;
+    for (int w = 0; w < kWarpsPerBlock; ++w) {
+      c += s_cnt[w][0];
+      b += s_cnt[w][1];
+    }
+    if (c) atomicAdd(stats + 0, (unsigned long long)c);
+    if (b) atomicAdd(stats + 1, (unsigned long long)b);
   }
 }
 
