@@ -12,9 +12,10 @@
 // at least one entered pair, in Morton order, each owning a contiguous run of
 // pairs (a = node index in A, b = node index in B) ordered by K ascending.
 // One level step:
-//   count  (warp per group): evaluate the 8 children of every pair, store an
-//          8-bit kept mask per pair and, per child output node c = 2ci + cj,
-//          the number of kept pairs; pack (count | nonempty << 36).
+//   count  (thread per pair) evaluate the 8 children of every pair and store
+//          an 8-bit kept mask per pair; then (warp per group) per child output
+//          node c = 2ci + cj the number of kept pairs, packed as
+//          (count | nonempty << 36).
 //   scan   exclusive prefix over the 4 * groups packed values: output offset
 //          of every child group and its index among the non-empty ones.
 //   write  (warp per group): every lane takes one pair, per child group a
@@ -113,28 +114,65 @@ __device__ __forceinline__ unsigned child_mask(const NodeRec& ra, const NodeRec&
   return m;
 }
 
+// count, part 1: the norm test of every entered pair, one thread per pair
+// (the pairs of a level, flat: no group loop, so every thread has one chain
+// of gathers in flight and the level's pairs all run at once); the 8-bit
+// child mask of each pair, and the level's candidate and borderline counts.
+__global__ void __launch_bounds__(256)
+    task_mask_kernel(const int64_t* __restrict__ dQ, const int32_t* __restrict__ ta,
+                     const int32_t* __restrict__ tb, const NodeRec* __restrict__ recA,
+                     const NodeRec* __restrict__ recB, const double4* __restrict__ normA,
+                     const double4* __restrict__ normB, TauScreen sc, double tau, int test, int leaf,
+                     uint8_t* __restrict__ mask, unsigned long long* stats) {
+  const int64_t Q = *dQ;
+  long long cand = 0, border = 0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t ia = ta[q], ib = tb[q];
+    mask[q] = (uint8_t)child_mask(recA[ia], recB[ib], normA + ia, normB + ib, sc, tau, test, leaf, &cand, &border);
+  }
+  // warp sums, then one atomic per block (atomics on one address from every
+  // warp of the grid would queue at a single L2 slice)
+  __shared__ long long s_cnt[8][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    cand += __shfl_xor_sync(0xffffffffu, cand, off);
+    border += __shfl_xor_sync(0xffffffffu, border, off);
+  }
+  if (lane == 0) {
+    s_cnt[warp][0] = cand;
+    s_cnt[warp][1] = border;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long c = 0, b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      c += s_cnt[w][0];
+      b += s_cnt[w][1];
+    }
+    if (c) atomicAdd(stats + 0, (unsigned long long)c);
+    if (b) atomicAdd(stats + 1, (unsigned long long)b);
+  }
+}
+
+// count, part 2 (warp per group): per child group c = 2 ci + cj the number of
+// kept pairs, from the masks; packed as (count | nonempty << 36).  Groups past
+// this level's count (up to the capacity the scan runs over) get zeros.
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    task_count_kernel(int64_t Gcap, const int64_t* __restrict__ dG, const int64_t* __restrict__ gstart,
-                      const int32_t* __restrict__ ta,
-                      const int32_t* __restrict__ tb, const NodeRec* __restrict__ recA,
-                      const NodeRec* __restrict__ recB, const double4* __restrict__ normA,
-                      const double4* __restrict__ normB, TauScreen sc, double tau, int test, int leaf,
-                      uint8_t* __restrict__ mask, uint64_t* __restrict__ packed, unsigned long long* stats) {
+    task_group_count_kernel(int64_t Gcap, const int64_t* __restrict__ dG, const int64_t* __restrict__ gstart,
+                            const uint8_t* __restrict__ mask, uint64_t* __restrict__ packed) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t G = *dG;
-  long long cand = 0, border = 0;
   for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < Gcap; g += nw) {
-    if (g >= G) {  // beyond this level's groups: no children (the scan runs over the capacity)
+    if (g >= G) {
       if (lane < 4) packed[4 * g + lane] = 0;
       continue;
     }
     const int64_t q0 = gstart[g], q1 = gstart[g + 1];
     unsigned cnt[4] = {0, 0, 0, 0};
     for (int64_t q = q0 + lane; q < q1; q += 32) {
-      const int32_t ia = ta[q], ib = tb[q];
-      const unsigned m = child_mask(recA[ia], recB[ib], normA + ia, normB + ib, sc, tau, test, leaf, &cand, &border);
-      mask[q] = (uint8_t)m;
+      const unsigned m = mask[q];
 #pragma unroll
       for (int c = 0; c < 4; ++c) cnt[c] += __popc((m >> (2 * c)) & 3u);
     }
@@ -147,28 +185,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 #pragma unroll
       for (int c = 0; c < 4; ++c) packed[4 * g + c] = (uint64_t)cnt[c] | ((uint64_t)(cnt[c] > 0) << 36);
     }
-  }
-  // the level's counters: warp sums, then one atomic per block (atomics on one
-  // address from every warp of the grid would queue at a single L2 slice)
-  __shared__ long long s_cnt[kWarpsPerBlock][2];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    cand += __shfl_xor_sync(0xffffffffu, cand, off);
-    border += __shfl_xor_sync(0xffffffffu, border, off);
-  }
-  if (lane == 0) {
-    s_cnt[threadIdx.x >> 5][0] = cand;
-    s_cnt[threadIdx.x >> 5][1] = border;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    long long c = 0, b = 0;
-    for (int w = 0; w < kWarpsPerBlock; ++w) {
-      c += s_cnt[w][0];
-      b += s_cnt[w][1];
-    }
-    if (c) atomicAdd(stats + 0, (unsigned long long)c);
-    if (b) atomicAdd(stats + 1, (unsigned long long)b);
   }
 }
 
@@ -345,11 +361,16 @@ TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm
           P<int4>(B->lv[t].child), P<double>(B->lv[t + 1].sq), P<NodeRec>(recB), P<double4>(normB));
       CK_LAUNCH("node_rec_kernel");
     }
-    task_count_kernel<<<warps_grid(ctx, G), kWarpsPerBlock * 32, 0, ctx->stream>>>(
-        G, dG, P<int64_t>(gstart), P<int32_t>(ta), P<int32_t>(tb), P<NodeRec>(recA), P<NodeRec>(recB),
-        P<double4>(normA), P<double4>(normB), screen, tau, test_norms, leaf, P<uint8_t>(mask), P<uint64_t>(packed),
-        stats);
-    CK_LAUNCH("task_count_kernel");
+    {
+      const int64_t g = (Q + 255) / 256, cap = (int64_t)ctx->num_sms * 16;
+      task_mask_kernel<<<(unsigned)(g < cap ? (g > 0 ? g : 1) : cap), 256, 0, ctx->stream>>>(
+          dsz + 2 * t, P<int32_t>(ta), P<int32_t>(tb), P<NodeRec>(recA), P<NodeRec>(recB), P<double4>(normA),
+          P<double4>(normB), screen, tau, test_norms, leaf, P<uint8_t>(mask), stats);
+      CK_LAUNCH("task_mask_kernel");
+    }
+    task_group_count_kernel<<<warps_grid(ctx, G), kWarpsPerBlock * 32, 0, ctx->stream>>>(
+        G, dG, P<int64_t>(gstart), P<uint8_t>(mask), P<uint64_t>(packed));
+    CK_LAUNCH("task_group_count_kernel");
     scan_exclusive_u64(ctx, P<uint64_t>(packed), P<uint64_t>(off), 4 * G, P<uint64_t>(tot));
     // capacities of the next level: exact after a wait, else the bounds 8 Q and 4 G
     int64_t Q2 = 8 * Q, G2 = 4 * G;
