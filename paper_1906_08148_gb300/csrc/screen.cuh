@@ -8,15 +8,17 @@
 //   E >= 2:  p >= 2^(et+2) > tau, kept;
 //   E <= -2: the exact product is at most (1 - 2^-53)^2 2^et, whose FP64
 //            rounding stays below 2^et <= tau, skipped;
-//   |E| <= 1: m = fl32(fa' fb') of the mantissas truncated to 21 bits lies
-//            within (1 - 2^-24, 1 + 2^-19.9) times fa fb, so m above hi[E+1] =
-//            ft (1 + 2^-18) 2^-E (rounded up to FP32) keeps and m below
-//            lo[E+1] = ft (1 - 2^-18) 2^-E (rounded down) skips; the FP64
+//   |E| <= 1: m = fl32(fa' fb') of the mantissas truncated to 13 bits lies
+//            within (1 - 2^-24, 1 + 2^-11.9) times fa fb, so m above hi[E+1] =
+//            ft (1 + 2^-10) 2^-E (rounded up to FP32) keeps and m below
+//            lo[E+1] = ft (1 - 2^-10) 2^-E (rounded down) skips; the FP64
 //            rounding of p is far inside these margins;
 //   a zero or subnormal norm, or tau zero or subnormal: undecided.
-// A norm is packed into one 32-bit key: its biased exponent field in the top
-// 11 bits, the leading 21 mantissa bits below.
+// A norm is packed into a 24-bit key: its biased exponent field in the top
+// 11 bits, the leading 13 mantissa bits below; 0xFFFFFF (an exponent field no
+// finite norm has) marks a null child.
 // Host-compilable so that the screen can be checked against FP64 products.
+// (Short keys keep a node's four children and their keys in one 16-byte record.)
 #pragma once
 #include <math.h>
 #include <stdint.h>
@@ -36,21 +38,23 @@ struct TauScreen {
   int exact_only;   // tau zero or subnormal
 };
 
-// The 32-bit key of a norm (non-negative double).
+constexpr uint32_t kNullKey = 0xFFFFFFu;
+
+// The 24-bit key of a norm (non-negative finite double).
 SCREEN_HD uint32_t pack_norm(double x) {
   uint64_t b;
   memcpy(&b, &x, sizeof b);
-  return (uint32_t)((b >> 52) & 0x7ff) << 21 | (uint32_t)((b >> 31) & 0x1fffff);
+  return (uint32_t)((b >> 52) & 0x7ff) << 13 | (uint32_t)((b >> 39) & 0x1fff);
 }
 
 // 1: kept, 0: skipped, -1: undecided (take the FP64 product).
 SCREEN_HD int screen_decide(uint32_t ka, uint32_t kb, const TauScreen& sc) {
-  const int ea = (int)(ka >> 21), eb = (int)(kb >> 21);
+  const int ea = (int)(ka >> 13), eb = (int)(kb >> 13);
   if (sc.exact_only || ea == 0 || eb == 0) return -1;
   const int E = ea + eb - sc.K;
   if (E >= 2) return 1;
   if (E <= -2) return 0;
-  const uint32_t fa = 0x3f800000u | ((ka & 0x1fffffu) << 2), fb = 0x3f800000u | ((kb & 0x1fffffu) << 2);
+  const uint32_t fa = 0x3f800000u | ((ka & 0x1fffu) << 10), fb = 0x3f800000u | ((kb & 0x1fffu) << 10);
   float ma, mb;
   memcpy(&ma, &fa, sizeof ma);
   memcpy(&mb, &fb, sizeof mb);
@@ -75,8 +79,8 @@ static inline TauScreen make_screen(double tau) {
   const double ft = et ? 2.0 * std::frexp(tau, &e2) : 1.0;
   for (int i = 0; i < 3; ++i) {
     const int E = i - 1;
-    const double h = std::ldexp(ft * (1.0 + std::ldexp(1.0, -18)), -E);
-    const double l = std::ldexp(ft * (1.0 - std::ldexp(1.0, -18)), -E);
+    const double h = std::ldexp(ft * (1.0 + std::ldexp(1.0, -10)), -E);
+    const double l = std::ldexp(ft * (1.0 - std::ldexp(1.0, -10)), -E);
     float hf = (float)h, lf = (float)l;
     if ((double)hf < h) hf = std::nextafter(hf, INFINITY);
     if ((double)lf > l) lf = std::nextafter(lf, -INFINITY);

@@ -41,21 +41,40 @@ __device__ __forceinline__ double comp4d(const double4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
-// Per node of a level, one 32-byte record: its four children (node indices
-// on the next level, -1 where null) and their Frobenius norms sqrt(s) as the
-// 32-bit keys of screen.cuh, so the descent reads one sector per node of a
-// pair; the norms themselves (-1 where null) go to a second array that only
-// the pairs the screen leaves undecided read.  One launch covers both
-// operands' levels (A's nodes first).
-struct __align__(32) NodeRec {
-  int4 child;
-  uint4 key;
+// Per node of a level, one 16-byte record: the index of its first child on
+// the next level (the children of a node are consecutive there: every level
+// is in Morton order) and the four children's 24-bit norm keys (screen.cuh;
+// kNullKey where a child is null), so the descent reads one 16-byte load per
+// node of a pair.  The norms themselves (-1 where null) go to a second array
+// that only the pairs the screen leaves undecided read.  One launch covers
+// both operands' levels (A's nodes first); a node whose children are not
+// consecutive sets the range error (a broken quadtree).
+struct __align__(16) NodeRec {
+  uint32_t base;
+  uint32_t w[3];  // keys k0..k3, 24 bits each, k0 in the low bits of w[0]
 };
+
+__device__ __forceinline__ uint32_t rec_key(const NodeRec& r, int c) {
+  switch (c) {
+    case 0: return r.w[0] & 0xFFFFFFu;
+    case 1: return (r.w[0] >> 24) | ((r.w[1] & 0xFFFFu) << 8);
+    case 2: return (r.w[1] >> 16) | ((r.w[2] & 0xFFu) << 16);
+    default: return r.w[2] >> 8;
+  }
+}
+
+// Next-level index of child c (-1 when null).
+__device__ __forceinline__ int rec_child(const NodeRec& r, int c) {
+  if (rec_key(r, c) == kNullKey) return -1;
+  int rank = 0;
+  for (int i = 0; i < c; ++i) rank += rec_key(r, i) != kNullKey;
+  return (int)r.base + rank;
+}
 
 __global__ void node_rec_kernel(int64_t nA, const int4* __restrict__ childA, const double* __restrict__ sqA,
                                 NodeRec* __restrict__ recA, double4* __restrict__ normA, int64_t nB,
                                 const int4* __restrict__ childB, const double* __restrict__ sqB,
-                                NodeRec* __restrict__ recB, double4* __restrict__ normB) {
+                                NodeRec* __restrict__ recB, double4* __restrict__ normB, int* err) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nA + nB; q += (int64_t)gridDim.x * blockDim.x) {
     const bool a = q < nA;
     const int64_t r = a ? q : q - nA;
@@ -63,16 +82,30 @@ __global__ void node_rec_kernel(int64_t nA, const int4* __restrict__ childA, con
     const double* sq = a ? sqA : sqB;
     const double4 v = make_double4(c.x >= 0 ? sqrt(sq[c.x]) : -1.0, c.y >= 0 ? sqrt(sq[c.y]) : -1.0,
                                    c.z >= 0 ? sqrt(sq[c.z]) : -1.0, c.w >= 0 ? sqrt(sq[c.w]) : -1.0);
+    const int ch[4] = {c.x, c.y, c.z, c.w};
+    uint32_t k[4];
+    int base = -1, rank = 0;
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (ch[i] < 0) {
+        k[i] = kNullKey;
+        continue;
+      }
+      if (base < 0) base = ch[i];
+      ok &= ch[i] == base + rank;
+      ++rank;
+      k[i] = pack_norm(comp4d(v, i));
+    }
+    if (!ok) atomicOr(err, DEV_ERR_RANGE);
     NodeRec rec;
-    rec.child = c;
-    rec.key = make_uint4(pack_norm(v.x), pack_norm(v.y), pack_norm(v.z), pack_norm(v.w));
+    rec.base = (uint32_t)(base < 0 ? 0 : base);
+    rec.w[0] = k[0] | (k[1] << 24);
+    rec.w[1] = (k[1] >> 8) | (k[2] << 16);
+    rec.w[2] = (k[2] >> 16) | (k[3] << 8);
     (a ? recA : recB)[r] = rec;
     (a ? normA : normB)[r] = v;
   }
-}
-
-__device__ __forceinline__ uint32_t compu(const uint4& v, int i) {
-  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
 // The FP64 decision p >= tau (and the borderline count at the leaf level).
@@ -94,6 +127,12 @@ __device__ __forceinline__ bool exact_keep(double na, double nb, double tau, boo
 __device__ __forceinline__ unsigned child_mask(const NodeRec& ra, const NodeRec& rb, const double4* na,
                                                const double4* nb, const TauScreen& sc, double tau, int test,
                                                bool leaf, long long* cand, long long* border) {
+  uint32_t ka[4], kb[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    ka[i] = rec_key(ra, i);
+    kb[i] = rec_key(rb, i);
+  }
   unsigned m = 0;
 #pragma unroll
   for (int ci = 0; ci < 2; ++ci)
@@ -102,11 +141,11 @@ __device__ __forceinline__ unsigned child_mask(const NodeRec& ra, const NodeRec&
 #pragma unroll
       for (int ck = 0; ck < 2; ++ck) {
         const int ia = 2 * ci + ck, ib = 2 * ck + cj;
-        if (comp4(ra.child, ia) < 0 || comp4(rb.child, ib) < 0) continue;
+        if (ka[ia] == kNullKey || kb[ib] == kNullKey) continue;
         ++*cand;
         bool keep = true;
         if (test) {
-          const int d = screen_decide(compu(ra.key, ia), compu(rb.key, ib), sc);
+          const int d = screen_decide(ka[ia], kb[ib], sc);
           keep = d >= 0 ? d == 1 : exact_keep(comp4d(*na, ia), comp4d(*nb, ib), tau, leaf, border);
         }
         if (keep) m |= 1u << (2 * (2 * ci + cj) + ck);
@@ -191,8 +230,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     task_write_kernel(const int64_t* __restrict__ dG, const int64_t* __restrict__ gstart,
                       const uint32_t* __restrict__ gcode,
-                      const int32_t* __restrict__ ta, const int32_t* __restrict__ tb, const int4* __restrict__ childA,
-                      const int4* __restrict__ childB, const uint8_t* __restrict__ mask,
+                      const int32_t* __restrict__ ta, const int32_t* __restrict__ tb, const NodeRec* __restrict__ recA,
+                      const NodeRec* __restrict__ recB, const uint8_t* __restrict__ mask,
                       const uint64_t* __restrict__ packed, const uint64_t* __restrict__ off,
                       int32_t* __restrict__ ta2, int32_t* __restrict__ tb2, uint32_t* __restrict__ gcode2,
                       int64_t* __restrict__ gstart2, int32_t* __restrict__ quad) {
@@ -220,8 +259,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       const unsigned m = active ? mask[q] : 0u;
       int4 ca = make_int4(-1, -1, -1, -1), cb = ca;
       if (m) {
-        ca = childA[ta[q]];
-        cb = childB[tb[q]];
+        const NodeRec ra = recA[ta[q]], rb = recB[tb[q]];
+        ca = make_int4(rec_child(ra, 0), rec_child(ra, 1), rec_child(ra, 2), rec_child(ra, 3));
+        cb = make_int4(rec_child(rb, 0), rec_child(rb, 1), rec_child(rb, 2), rec_child(rb, 3));
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -358,7 +398,7 @@ TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm
       const int64_t g = (nA + nB + 255) / 256, cap = (int64_t)ctx->num_sms * 16;
       node_rec_kernel<<<(unsigned)(g < cap ? g : cap), 256, 0, ctx->stream>>>(
           nA, P<int4>(A->lv[t].child), P<double>(A->lv[t + 1].sq), P<NodeRec>(recA), P<double4>(normA), nB,
-          P<int4>(B->lv[t].child), P<double>(B->lv[t + 1].sq), P<NodeRec>(recB), P<double4>(normB));
+          P<int4>(B->lv[t].child), P<double>(B->lv[t + 1].sq), P<NodeRec>(recB), P<double4>(normB), ctx->d_err);
       CK_LAUNCH("node_rec_kernel");
     }
     {
@@ -391,8 +431,8 @@ TaskList build_tasks(spamm_mat A, spamm_mat B, double tau, int test_norms, spamm
     BufP ta2 = alloc_n<int32_t>(ctx, Q2), tb2 = alloc_n<int32_t>(ctx, Q2);
     if (G2 > 0) {
       task_write_kernel<<<warps_grid(ctx, G), kWarpsPerBlock * 32, 0, ctx->stream>>>(
-          dG, P<int64_t>(gstart), P<uint32_t>(gcode), P<int32_t>(ta), P<int32_t>(tb), P<int4>(A->lv[t].child),
-          P<int4>(B->lv[t].child), P<uint8_t>(mask), P<uint64_t>(packed), P<uint64_t>(off), P<int32_t>(ta2),
+          dG, P<int64_t>(gstart), P<uint32_t>(gcode), P<int32_t>(ta), P<int32_t>(tb), P<NodeRec>(recA),
+          P<NodeRec>(recB), P<uint8_t>(mask), P<uint64_t>(packed), P<uint64_t>(off), P<int32_t>(ta2),
           P<int32_t>(tb2), P<uint32_t>(gcode2), P<int64_t>(gstart2), leaf ? P<int32_t>(T.quads) : nullptr);
       CK_LAUNCH("task_write_kernel");
     }

@@ -1,7 +1,7 @@
 """The norm-test screen of the task-list builder (csrc/screen.cuh), compiled
 for the host: wherever it decides, its decision equals the FP64 rule
 fl(||A|| ||B||) >= tau that the oracle applies (Algorithm 1's test), and it
-leaves undecided only pairs whose product lies within about 2^-18 of tau or
+leaves undecided only pairs whose product lies within about 2^-10 of tau or
 that involve zero or subnormal norms."""
 import ctypes
 import os
@@ -59,7 +59,7 @@ def test_screen_agrees_with_fp64_products_over_the_range(scr, tau):
     b = tau / a * 10.0 ** rng.uniform(-3, 3, n)  # products spread over six decades around tau
     d = _check(scr, tau, a, b)
     # almost everything is decided without the FP64 product
-    assert np.mean(d < 0) < 1e-4
+    assert np.mean(d < 0) < 1e-3
 
 
 @pytest.mark.parametrize("tau", TAUS)
@@ -70,10 +70,10 @@ def test_screen_near_tau(scr, tau):
     rel = rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-17, -3, n)
     b = tau * (1.0 + rel) / a
     d = _check(scr, tau, a, b)
-    # undecided only inside the margin (2^-18 plus the mantissa truncation)
-    close = np.abs(a * b / tau - 1.0) < 2.0 ** -17
+    # undecided only inside the margin (2^-10 plus the mantissa truncation)
+    close = np.abs(a * b / tau - 1.0) < 2.0 ** -9
     assert np.all(close[d < 0])
-    assert np.all(d[np.abs(a * b / tau - 1.0) > 2.0 ** -16] >= 0)
+    assert np.all(d[np.abs(a * b / tau - 1.0) > 2.0 ** -8] >= 0)
 
 
 def test_screen_exponent_boundaries_and_special_values(scr):
