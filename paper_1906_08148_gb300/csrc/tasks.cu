@@ -18,8 +18,8 @@
 //          (count | nonempty << 36).
 //   scan   exclusive prefix over the 4 * groups packed values: output offset
 //          of every child group and its index among the non-empty ones.
-//   write  (warp per group): every lane takes one pair, per child group a
-//          warp prefix sum of the kept counts places the pairs; within a
+//   write  (warp per group): every lane takes one pair, per child group two
+//          warp ballots (k-child 0 and 1) place the kept pairs; within a
 //          child group pairs stay in parent order with k = 2K, 2K+1, so the
 //          children are again sorted by k.  Lane 0 writes the child groups.
 // Because a parent's squared norm is a floating-point sum of non-negative
@@ -63,12 +63,14 @@ __device__ __forceinline__ uint32_t rec_key(const NodeRec& r, int c) {
   }
 }
 
-// Next-level index of child c (-1 when null).
-__device__ __forceinline__ int rec_child(const NodeRec& r, int c) {
-  if (rec_key(r, c) == kNullKey) return -1;
-  int rank = 0;
-  for (int i = 0; i < c; ++i) rank += rec_key(r, i) != kNullKey;
-  return (int)r.base + rank;
+// Next-level indices of the four children (-1 where null).
+__device__ __forceinline__ int4 rec_children(const NodeRec& r) {
+  unsigned pres = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) pres |= (unsigned)(rec_key(r, i) != kNullKey) << i;
+  const int b = (int)r.base;
+  return make_int4(pres & 1u ? b : -1, pres & 2u ? b + __popc(pres & 1u) : -1, pres & 4u ? b + __popc(pres & 3u) : -1,
+                   pres & 8u ? b + __popc(pres & 7u) : -1);
 }
 
 __global__ void node_rec_kernel(int64_t nA, const int4* __restrict__ childA, const double* __restrict__ sqA,
@@ -259,22 +261,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       const unsigned m = active ? mask[q] : 0u;
       int4 ca = make_int4(-1, -1, -1, -1), cb = ca;
       if (m) {
-        const NodeRec ra = recA[ta[q]], rb = recB[tb[q]];
-        ca = make_int4(rec_child(ra, 0), rec_child(ra, 1), rec_child(ra, 2), rec_child(ra, 3));
-        cb = make_int4(rec_child(rb, 0), rec_child(rb, 1), rec_child(rb, 2), rec_child(rb, 3));
+        ca = rec_children(recA[ta[q]]);
+        cb = rec_children(recB[tb[q]]);
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const unsigned bits = (m >> (2 * c)) & 3u;
-        const int cntc = __popc(bits);
-        int incl = cntc;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          int y = __shfl_up_sync(0xffffffffu, incl, d);
-          if (lane >= d) incl += y;
-        }
-        const int tot = __shfl_sync(0xffffffffu, incl, 31);
-        int64_t pos = base[c] + (incl - cntc);
+        // warp ballots compact the kept children: a lane's entries follow
+        // every kept child of the lanes before it (k-child 0, then 1)
+        const unsigned b0 = __ballot_sync(0xffffffffu, bits & 1u), b1 = __ballot_sync(0xffffffffu, bits & 2u);
+        const unsigned lt = (1u << lane) - 1u;
+        const int tot = __popc(b0) + __popc(b1);
+        int64_t pos = base[c] + __popc(b0 & lt) + __popc(b1 & lt);
         const int ci = c >> 1, cj = c & 1;
         if (bits & 1u) {
           ta2[pos] = comp4(ca, 2 * ci + 0);
