@@ -50,8 +50,9 @@
 // from a global counter in Morton order, so the quads in flight on all SMs
 // form one narrow window whose A rows and B columns are shared in L2):
 //   warp 0     TMA producer: claims the next quad for all roles (a ring of 4
-//              in shared memory), ring of NS stages, 1-D bulk copies of
-//              pre-swizzled term tiles, mbarriers.
+//              in shared memory), ring of NS stages, one 1-D bulk copy per
+//              leaf and stage (the leaf's K-part with all its pre-swizzled,
+//              atom-interleaved terms), mbarriers.
 //   warp 1     allocates 512 TMEM columns and issues the MMAs of each step.
 //   warps 2-3  idle (they fill the first warpgroup, see the register split)
 //   warps 4-11 epilogue: warps 4-7 column 0, warps 8-11 column 1; TMEM lane =
@@ -81,23 +82,26 @@ constexpr int kQuadBufs = 4;  // rotating TMEM accumulator slots of 128 FP32 col
 constexpr int kQuadQ = 4;     // ring of claimed quads shared by the three roles
 
 // One stage: two A and two B leaves, every term of a step (whole-K forms) or
-// of one K-half of it (the 4-slice form).  A region: term s at s * 2 * TILE =
-// [A(2I,k)_s; A(2I+1,k)_s] (128 rows); B region at TERMS * 2 * TILE, term t at
-// t * 2 * TILE = [B(k,2J)_t; B(k,2J+1)_t] (128 rows n).  Both are 128-row
-// K-major operands in the form's swizzle.
+// of one K-part of it.  A region: leaf 2I's part (all terms, atom-interleaved,
+// tcforms.cuh) then leaf 2I+1's; B region at BREG: leaves 2J, 2J+1 likewise.
+// Term s of the 128-row A operand [A(2I,k)_s; A(2I+1,k)_s] starts at s x atom
+// with TERMS x atom between 8-row groups, and the same for B.
 template <int PREC>
 struct QuadLayout {
   using Cfg = FormCfg<PREC>;
-  static constexpr uint32_t TILE = kTerm / Cfg::KPARTS;
+  static constexpr uint32_t TILE = kTerm / Cfg::KPARTS;            // one term's part of one leaf
+  static constexpr uint32_t LPART = (uint32_t)Cfg::TERMS * TILE;   // one leaf's part, all terms
+  static constexpr uint32_t ATOM = term_atom<Cfg::KPARTS>();
+  static constexpr uint32_t SBO = (uint32_t)Cfg::TERMS * ATOM;
   static constexpr int SPS = Cfg::KPARTS;      // stages per step
   static constexpr int KS = 4 / Cfg::KPARTS;   // K = 16 MMAs per stage
-  static constexpr uint32_t BREG = (uint32_t)Cfg::TERMS * 2 * TILE;
+  static constexpr uint32_t BREG = 2 * LPART;
   static constexpr uint32_t STAGE = 2 * BREG;
   static constexpr size_t SMEM = 1024 + (size_t)Cfg::NS * STAGE;
   __device__ static uint64_t desc(uint32_t saddr) {
-    if constexpr (Cfg::KPARTS == 1) return sw128_kmajor_desc(saddr);
-    if constexpr (Cfg::KPARTS == 2) return sw64_kmajor_desc(saddr);
-    return sw32_kmajor_desc(saddr);
+    if constexpr (Cfg::KPARTS == 1) return sw128_kmajor_desc(saddr, SBO);
+    if constexpr (Cfg::KPARTS == 2) return sw64_kmajor_desc(saddr, SBO);
+    return sw32_kmajor_desc(saddr, SBO);
   }
 };
 
@@ -122,8 +126,8 @@ __device__ __forceinline__ void issue_acc(uint32_t d, uint32_t a_s, uint32_t b_s
     for (int i = g; i >= 0; --i) {
 #pragma unroll
       for (int ks = 0; ks < Lay::KS; ++ks) {
-        umma_f16(d, Lay::desc(a_s + (uint32_t)i * 2 * Lay::TILE + 32 * ks),
-                 Lay::desc(b_s + (uint32_t)(g - i) * 2 * Lay::TILE + 32 * ks), idesc, accumulate);
+        umma_f16(d, Lay::desc(a_s + (uint32_t)i * Lay::ATOM + 32 * ks),
+                 Lay::desc(b_s + (uint32_t)(g - i) * Lay::ATOM + 32 * ks), idesc, accumulate);
         accumulate = 1u;
       }
     }
@@ -241,17 +245,14 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
               break;
             }
             uint8_t* st = smem + s * STAGE;
-            mbar_arrive_expect_tx(&full[s], nload * TERMS * TILE);
-#pragma unroll
-            for (int term = 0; term < TERMS; ++term) {
-              uint8_t* sa = st + term * 2 * TILE;
-              uint8_t* sb = st + BREG + term * 2 * TILE;
-              const int64_t off = (int64_t)(h * TERMS + term) * TILE;
-              if (ab.x >= 0) bulk_g2s(sa, pl.termsA + (int64_t)ab.x * LEAF + off, TILE, &full[s]);
-              if (ab.y >= 0) bulk_g2s(sa + TILE, pl.termsA + (int64_t)ab.y * LEAF + off, TILE, &full[s]);
-              if (ab.z >= 0) bulk_g2s(sb, pl.termsB + (int64_t)ab.z * LEAF + off, TILE, &full[s]);
-              if (ab.w >= 0) bulk_g2s(sb + TILE, pl.termsB + (int64_t)ab.w * LEAF + off, TILE, &full[s]);
-            }
+            constexpr uint32_t LP = Lay::LPART;
+            mbar_arrive_expect_tx(&full[s], nload * LP);
+            // one copy per leaf: its part h, every term
+            const int64_t off = (int64_t)h * LP;
+            if (ab.x >= 0) bulk_g2s(st, pl.termsA + (int64_t)ab.x * LEAF + off, LP, &full[s]);
+            if (ab.y >= 0) bulk_g2s(st + LP, pl.termsA + (int64_t)ab.y * LEAF + off, LP, &full[s]);
+            if (ab.z >= 0) bulk_g2s(st + BREG, pl.termsB + (int64_t)ab.z * LEAF + off, LP, &full[s]);
+            if (ab.w >= 0) bulk_g2s(st + BREG + LP, pl.termsB + (int64_t)ab.w * LEAF + off, LP, &full[s]);
             ++t;
           }
         }

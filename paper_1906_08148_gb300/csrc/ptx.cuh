@@ -186,24 +186,26 @@ __device__ __forceinline__ void tmem_wait16(uint32_t* r) {
 }
 
 // Shared-memory matrix descriptor of a K-major operand in the 128-byte swizzle
-// layout: rows of 128 bytes, 8-row atoms of 1024 bytes (stride byte offset),
+// layout: rows of 128 bytes, 8-row atoms of 1024 bytes, `sbo` bytes from one
+// 8-row group to the next (the stride byte offset; 1024 when the atoms follow
+// each other),
 // base 1024-byte aligned; descriptor version 1, layout type 2 (SWIZZLE_128B).
-__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(1024u >> 4) << 32) |
+__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr, uint32_t sbo = 1024u) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) |
          ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
 }
 
 // The same for the 64-byte swizzle: rows of 64 bytes, 8-row atoms of 512
 // bytes (stride byte offset), base 512-byte aligned; layout type 4 (SWIZZLE_64B).
-__device__ __forceinline__ uint64_t sw64_kmajor_desc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(512u >> 4) << 32) |
+__device__ __forceinline__ uint64_t sw64_kmajor_desc(uint32_t saddr, uint32_t sbo = 512u) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) |
          ((uint64_t)1u << 46) | ((uint64_t)4u << 61);
 }
 
 // The same for the 32-byte swizzle: rows of 32 bytes, 8-row atoms of 256
 // bytes (stride byte offset), base 256-byte aligned; layout type 6 (SWIZZLE_32B).
-__device__ __forceinline__ uint64_t sw32_kmajor_desc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(256u >> 4) << 32) |
+__device__ __forceinline__ uint64_t sw32_kmajor_desc(uint32_t saddr, uint32_t sbo = 256u) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) |
          ((uint64_t)1u << 46) | ((uint64_t)6u << 61);
 }
 

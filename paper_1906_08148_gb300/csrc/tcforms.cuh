@@ -1,14 +1,15 @@
 // tcforms.cuh -- the operand-term layout shared by the operand preparation
 // (prep.cu) and the tensor-core leaf GEMM (gemm_tc.cu).  Per leaf, TERMS
 // two-byte term (slice) tiles, every tile swizzled and K-major (tile row =
-// leaf row for an A operand, leaf column for a B operand; k along the row), so
-// one 1-D bulk copy lands a tile ready for tcgen05.  A form stages a step's K
-// in KPARTS parts; part h of term s sits at (h * TERMS + s) * (8 KB / KPARTS):
-//   KPARTS = 1: a 64 x 64 tile in the 128-byte swizzle (a row holds all 64 k);
-//   KPARTS = 2: a 64 x 32 tile (k = 32 h ..) in the 64-byte swizzle;
-//   KPARTS = 4: a 64 x 16 tile (k = 16 h ..) in the 32-byte swizzle.
-// Smaller parts give smaller pipeline stages, so more of them fit in shared
-// memory and more copies are in flight for the same bytes.
+// leaf row for an A operand, leaf column for a B operand; k along the row).
+// A form stages a step's K in KPARTS parts: a row of a part holds 64 / KPARTS
+// k (128, 64 or 32 bytes, in the 128-, 64- or 32-byte swizzle), and 8 rows of
+// it make one swizzle atom (1 KB, 512 B or 256 B).  Part h of a leaf is one
+// contiguous block of TERMS x 8 KB / KPARTS: atom g (rows 8 g ..) of term s at
+// (g TERMS + s) x atom -- the terms interleaved atom by atom.  So one 1-D bulk
+// copy lands a leaf's part with all its terms, and the 128-row operand of
+// term s over two leaves placed one after the other is a single matrix
+// descriptor: start at s x atom, stride between 8-row groups TERMS x atom.
 #pragma once
 #include <cstdint>
 
@@ -77,16 +78,22 @@ __host__ __device__ __forceinline__ uint32_t sw32_offset(int row, int k) {
   return (uint32_t)(row * 32 + ((((k >> 3) ^ (row >> 2)) & 1) << 4) + (k & 7) * 2);
 }
 
+// Bytes of one 8-row swizzle atom of a part.
+template <int KPARTS>
+__host__ __device__ constexpr uint32_t term_atom() {
+  return 8u * 2u * (64u / KPARTS);
+}
+
 // Offset of element (row, k), 0 <= k < 64, of term s in a leaf's terms.
 template <int KPARTS>
 __host__ __device__ __forceinline__ uint32_t term_offset(int terms, int s, int row, int k) {
-  constexpr uint32_t part = kTerm / KPARTS;
+  constexpr uint32_t part = kTerm / KPARTS, atom = term_atom<KPARTS>();
   constexpr int kw = 64 / KPARTS;  // k per part
-  const int h = k / kw, kk = k % kw;
-  const uint32_t base = (uint32_t)(h * terms + s) * part;
-  if constexpr (KPARTS == 1) return base + sw128_offset(row, kk);
-  if constexpr (KPARTS == 2) return base + sw64_offset(row, kk);
-  return base + sw32_offset(row, kk);
+  const int h = k / kw, kk = k % kw, g = row >> 3, r8 = row & 7;
+  const uint32_t base = (uint32_t)h * terms * part + (uint32_t)(g * terms + s) * atom;
+  if constexpr (KPARTS == 1) return base + sw128_offset(r8, kk);
+  if constexpr (KPARTS == 2) return base + sw64_offset(r8, kk);
+  return base + sw32_offset(r8, kk);
 }
 
 }  // namespace spamm

@@ -2,9 +2,11 @@
 compiled for the host: for every K split (1, 2 or 4 parts, in the 128-,
 64- and 32-byte swizzles) each element of a leaf's terms has its own
 two-byte slot inside the leaf's terms, eight consecutive k share one 16-byte
-chunk, every part of every term is one contiguous tile, and the chunk order
-inside a row follows the swizzle (chunk index XOR the row bits above the
-atom's row stride)."""
+chunk, every part of a leaf (all its terms) is one contiguous block, inside
+it the 8-row atom g of term s sits at (g TERMS + s) x atom (so the 128-row
+operand of term s over two such blocks is one strided matrix), and the chunk
+order inside a row follows the swizzle (chunk index XOR the row bits above
+the atom's row stride)."""
 import ctypes
 import os
 import subprocess
@@ -53,14 +55,19 @@ def test_term_layout_is_a_swizzled_bijection(lay, kp, terms):
     part = 8192 // kp
     kw = 64 // kp
     rowb = 2 * kw  # bytes per tile row
-    for s in range(terms):
-        for h in range(kp):
-            blk = off[s, :, h * kw:(h + 1) * kw]
-            base = (h * terms + s) * part
-            assert blk.min() == base and blk.max() == base + part - 2
-            rel = blk - base
-            assert np.array_equal(rel // rowb, np.repeat(np.arange(64)[:, None], kw, axis=1))
-            chunk = (rel % rowb) // 16
-            nchunk = rowb // 16
-            want = (np.arange(kw)[None, :] // 8) ^ ((np.arange(64)[:, None] * rowb >> 7) % nchunk)
-            assert np.array_equal(chunk, want)
+    atom = 8 * rowb
+    for h in range(kp):
+        blk = off[:, :, h * kw:(h + 1) * kw]
+        base = h * terms * part
+        assert blk.min() == base and blk.max() == base + terms * part - 2
+        for s in range(terms):
+            for g in range(8):
+                a = blk[s, 8 * g:8 * g + 8] - base
+                start = (g * terms + s) * atom
+                assert a.min() == start and a.max() == start + atom - 2
+                rel = a - start
+                assert np.array_equal(rel // rowb, np.repeat(np.arange(8)[:, None], kw, axis=1))
+                chunk = (rel % rowb) // 16
+                nchunk = rowb // 16
+                want = (np.arange(kw)[None, :] // 8) ^ ((np.arange(8)[:, None] * rowb >> 7) % nchunk)
+                assert np.array_equal(chunk, want)
