@@ -393,18 +393,25 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
             break;
           }
           tc_fence_after();
+          bool released = false;
           if (sc != 0.f) {  // this warp's child has a kept product at this k
             const bool exact = a < NACC - 1;  // an exact accumulator: TwoSum into (hi, lo)
             const uint64_t sc2 = ((uint64_t)__float_as_uint(sc) << 32) | __float_as_uint(sc);
-            // four 16-column chunks; chunk hh + 1 is in flight while chunk hh is added
+            // the slot's 64 columns of this thread's row: four loads in flight
+            // at once, one wait; the slot is handed back to the MMAs before
+            // the registers are added up
             const uint32_t ta = taddr0 + (uint32_t)b * 128u;
-            uint32_t buf[2][16];
-            tmem_ld16_async(ta, buf[0]);
+            uint32_t buf[4][16];
+#pragma unroll
+            for (int hh = 0; hh < 4; ++hh) tmem_ld16_async(ta + 16u * hh, buf[hh]);
+#pragma unroll
+            for (int hh = 0; hh < 4; ++hh) tmem_wait16(buf[hh]);  // the first waits for all four
+            tc_fence_before();
+            mbar_arrive(&tempty[b]);
+            released = true;
 #pragma unroll
             for (int hh = 0; hh < 4; ++hh) {
-              uint32_t* v = buf[hh & 1];
-              tmem_wait16(v);
-              if (hh + 1 < 4) tmem_ld16_async(ta + 16u * (hh + 1), buf[(hh + 1) & 1]);
+              const uint32_t* v = buf[hh];
               if constexpr (NACC == 1) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) hi[16 * hh + i] = fmaf(__uint_as_float(v[i]), sc, hi[16 * hh + i]);
@@ -417,8 +424,10 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
               }
             }
           }
-          tc_fence_before();
-          mbar_arrive(&tempty[b]);
+          if (!released) {
+            tc_fence_before();
+            mbar_arrive(&tempty[b]);
+          }
         }
       }
       // output row `row` of leaf g[child], unconverted: each element's 8-byte
