@@ -104,6 +104,36 @@ def test_single_leaf_product_layout(S, ctx, prec, bs):
 
 
 @pytest.mark.parametrize("prec", TC)
+@pytest.mark.parametrize("cols", ["odd", "even", "alternating", "all"])
+def test_steps_with_one_b_leaf(S, ctx, prec, cols):
+    """Quads of 64-leaves whose steps need only one of their two B leaves
+    (kept products in one output column) run half-width MMAs on that leaf:
+    B's leaf columns only odd (the second leaf of every pair), only even,
+    alternating with k (both kinds within one quad), and all present.
+    Integer entries: the BF16 splits are exact (C = AB bit for bit); FP16
+    within its derived bound."""
+    rng = np.random.default_rng(23)
+    bs, nl = 64, 6
+    n = bs * nl
+    A = rng.integers(-255, 256, (n, n)).astype(np.float64)
+    B = rng.integers(-255, 256, (n, n)).astype(np.float64)
+    for kb in range(nl):
+        for jb in range(nl):
+            keep = {"odd": jb % 2 == 1, "even": jb % 2 == 0, "alternating": jb % 2 == kb % 2, "all": True}[cols]
+            if not keep:
+                B[kb * bs:(kb + 1) * bs, jb * bs:(jb + 1) * bs] = 0.0
+    GA, GB = S.spamm_from_dense(ctx, A, bs), S.spamm_from_dense(ctx, B, bs)
+    C = S.spamm_to_dense(ctx, S.spamm_multiply(ctx, GA, GB, 0.0, "spamm", prec))
+    if prec != "fp16_scaled":
+        assert np.array_equal(C, A @ B)
+    else:
+        MA, MB = oracle.from_dense(A, bs), oracle.from_dense(B, bs)
+        ref, ikj = oracle.multiply(MA, MB, 0.0, oracle.SPAMM)
+        bnd = oracle.to_dense(oracle.LeafMatrix(n, bs, ref.bi, ref.bj, tcbound.bound(prec, MA, MB, ikj, ref)))
+        assert np.all(np.abs(C - A @ B) <= bnd)
+
+
+@pytest.mark.parametrize("prec", TC)
 @pytest.mark.parametrize("bs", [64, 128])
 def test_tensor_ragged_and_empty(S, ctx, prec, bs):
     rng = np.random.default_rng(5)
