@@ -40,10 +40,7 @@
 // whole tile, but its quadrant is discarded by the epilogue; an operand leaf no
 // kept product of the step needs is not loaded (its stale contents reach only
 // discarded quadrants: each output element depends on one A row and one B
-// column).  A step whose kept products all use one of the two B leaves
-// (both of its products in one output column, or one product) loads that
-// leaf first in the B region and runs N = 64 MMAs into the column's half of
-// the slot: half the tensor work of the step.  The 4-slice form stages each step in two K-halves (64 KB each,
+// column).  The 4-slice form stages each step in two K-halves (64 KB each,
 // three in flight) so that its 128 KB of operands per step still pipeline.
 // Accumulators are 128 x 128 FP32 slots of TMEM; four slots rotate, one per
 // accumulator of each step in order, so the MMAs of the next step start as
@@ -113,20 +110,6 @@ double quad_step_flops(spamm_prec prec) {
   return (double)(terms * (terms + 1) / 2) * 2.0 * 128.0 * 128.0 * 64.0;
 }
 
-// Term products (i, g - i) of index sums g = G down to GLO, i from g down,
-// each as KS MMAs of K = 16: compile-time operand offsets from the stage's
-// two base descriptors.
-template <class Lay, int G, int GLO, int I, int KS0>
-__device__ __forceinline__ void issue_terms(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accumulate) {
-  if constexpr (G >= GLO) {
-    umma_f16_at<(uint32_t)I * Lay::ATOM + 32u * KS0, (uint32_t)(G - I) * Lay::ATOM + 32u * KS0>(d, ad, bd, idesc,
-                                                                                               accumulate);
-    if constexpr (KS0 + 1 < Lay::KS) issue_terms<Lay, G, GLO, I, KS0 + 1>(d, ad, bd, idesc, 1u);
-    else if constexpr (I > 0) issue_terms<Lay, G, GLO, I - 1, 0>(d, ad, bd, idesc, 1u);
-    else issue_terms<Lay, G - 1, GLO, G - 1, 0>(d, ad, bd, idesc, 1u);
-  }
-}
-
 // The MMAs of accumulator `acc` for one stage: term products (i, g - i) with
 // index sum g = acc (g from acc to TERMS - 1 for the last accumulator, the
 // largest sums first so the smallest products are added first), the first
@@ -136,8 +119,19 @@ __device__ __forceinline__ void issue_acc(uint32_t d, uint32_t a_s, uint32_t b_s
   using Cfg = FormCfg<PREC>;
   using Lay = QuadLayout<PREC>;
   constexpr int GLO = ACC, GHI = ACC < Cfg::NACC - 1 ? ACC : Cfg::TERMS - 1;
-  const uint64_t ad = Lay::desc(a_s), bd = Lay::desc(b_s);
-  issue_terms<Lay, GHI, GLO, GHI, 0>(d, ad, bd, idesc, fresh ? 0u : 1u);
+  uint32_t accumulate = fresh ? 0u : 1u;
+#pragma unroll
+  for (int g = GHI; g >= GLO; --g) {
+#pragma unroll
+    for (int i = g; i >= 0; --i) {
+#pragma unroll
+      for (int ks = 0; ks < Lay::KS; ++ks) {
+        umma_f16(d, Lay::desc(a_s + (uint32_t)i * Lay::ATOM + 32 * ks),
+                 Lay::desc(b_s + (uint32_t)(g - i) * Lay::ATOM + 32 * ks), idesc, accumulate);
+        accumulate = 1u;
+      }
+    }
+  }
 }
 
 // (hi, lo) += x sc for two adjacent output elements at once, with an
@@ -257,9 +251,8 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
             const int64_t off = (int64_t)h * LP;
             if (ab.x >= 0) bulk_g2s(st, pl.termsA + (int64_t)ab.x * LEAF + off, LP, &full[s]);
             if (ab.y >= 0) bulk_g2s(st + LP, pl.termsA + (int64_t)ab.y * LEAF + off, LP, &full[s]);
-            // a step with one B leaf has it first in the B region (the MMAs then run N = 64)
             if (ab.z >= 0) bulk_g2s(st + BREG, pl.termsB + (int64_t)ab.z * LEAF + off, LP, &full[s]);
-            if (ab.w >= 0) bulk_g2s(st + BREG + (ab.z >= 0 ? LP : 0u), pl.termsB + (int64_t)ab.w * LEAF + off, LP, &full[s]);
+            if (ab.w >= 0) bulk_g2s(st + BREG + LP, pl.termsB + (int64_t)ab.w * LEAF + off, LP, &full[s]);
             ++t;
           }
         }
@@ -270,13 +263,8 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer: the accumulators of step number n are slots (NACC n + a) % NB
     if (lane == 0) {
-      // a step whose kept products all use one B leaf runs N = 64 MMAs on that
-      // leaf (the producer put it first in the B region) into its 64 columns
-      // of the slot (the epilogue reads only the columns of children with a
-      // kept product)
-      constexpr uint32_t idesc128 = umma_idesc_f16(Cfg::AB, 128, 128), idesc64 = umma_idesc_f16(Cfg::AB, 128, 64);
-      int64_t t = 0;   // stages consumed
-      uint32_t u = 0;  // accumulator units started: below 2^32 (a CTA's steps, 32 B each, would not fit in HBM)
+      constexpr uint32_t idesc = umma_idesc_f16(Cfg::AB, 128, 128);
+      int64_t t = 0, u = 0;  // stages consumed, accumulator units started
       bool stop = false;
       for (int64_t c = 0; !stop; ++c) {
         const int qs = (int)(c % kQuadQ);
@@ -291,14 +279,8 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
         const int r = plan_of(batch.ubegin, batch.nplans, un);
         const PlanDev& pl = batch.plans[r];
         const int64_t Qc = un - batch.ubegin[r], Q = pl.uorder ? pl.uorder[Qc] : pl.ufirst + Qc;
-        const int64_t j0 = pl.qstart[Q];
-        const int nstep = (int)(pl.qstart[Q + 1] - j0);  // a quad's k steps: at most the leaves per row
-        const int2* recb = reinterpret_cast<const int2*>(pl.qsteps + j0) + 1;  // b0, b1 of step j at 4j
-        for (int j = 0; j < nstep && !stop; ++j) {
-          const int2 bb = __ldg(recb + 4 * j);
-          const bool no_b0 = bb.x < 0, one_b = no_b0 || bb.y < 0;  // never both: a step has a kept product
-          const uint32_t idesc = one_b ? idesc64 : idesc128;
-          const uint32_t dstep = tmem_base + (no_b0 ? 64u : 0u);  // reread: one register fewer held
+        const int64_t nstep = pl.qstart[Q + 1] - pl.qstart[Q];
+        for (int64_t j = 0; j < nstep && !stop; ++j) {
 #pragma unroll
           for (int h = 0; h < SPS; ++h) {
             const int s = (int)(t % NS);
@@ -310,7 +292,7 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
             const uint32_t a_s = smem_u32(smem + s * STAGE), b_s = a_s + BREG;
 #pragma unroll
             for (int a = 0; a < NACC; ++a) {
-              const uint32_t un_a = u + (uint32_t)a;
+              const int64_t un_a = u + a;
               const int b = (int)(un_a % NB);
               if (h == 0 && un_a >= NB) {
                 if (!mbar_wait_or_abort(&tempty[b], (uint32_t)(((un_a / NB) - 1) & 1), abortp)) {
@@ -319,7 +301,7 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
                 }
                 tc_fence_after();
               }
-              const uint32_t d = dstep + (uint32_t)b * 128u;
+              const uint32_t d = tbase + (uint32_t)b * 128u;
               if (a == 0) issue_acc<PREC, 0>(d, a_s, b_s, idesc, h == 0);
               if constexpr (NACC > 1) if (a == 1) issue_acc<PREC, (NACC > 1 ? 1 : 0)>(d, a_s, b_s, idesc, h == 0);
               if constexpr (NACC > 2) if (a == 2) issue_acc<PREC, (NACC > 2 ? 2 : 0)>(d, a_s, b_s, idesc, h == 0);

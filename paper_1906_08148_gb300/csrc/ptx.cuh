@@ -99,25 +99,6 @@ __device__ __forceinline__ void umma_f16(uint32_t d_taddr, uint64_t adesc, uint6
       : "memory");
 }
 
-// The same with the operands at byte offsets AOFF and BOFF from the ones the
-// two descriptors address: the offsets (multiples of 16 bytes, the address
-// field staying below 2^18 bytes of shared memory) are added to the address
-// field inside the instruction sequence, so the base descriptors are the only
-// values the caller keeps in registers.
-template <uint32_t AOFF, uint32_t BOFF>
-__device__ __forceinline__ void umma_f16_at(uint32_t d_taddr, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                            uint32_t accumulate) {
-  static_assert(AOFF % 16 == 0 && BOFF % 16 == 0, "operand offsets are in 16-byte units");
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "add.s64 da, %1, %5;\n\t"
-      "add.s64 db, %2, %6;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %3, p;\n\t}" ::"r"(d_taddr),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate), "n"(AOFF >> 4), "n"(BOFF >> 4)
-      : "memory");
-}
-
 // Arrive (once) on `bar` when every tcgen05 operation this thread issued so far has completed.
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
