@@ -107,9 +107,11 @@ def test_single_leaf_product_layout(S, ctx, prec, bs):
 @pytest.mark.parametrize("cols", ["odd", "even", "alternating", "all"])
 def test_steps_with_one_b_leaf(S, ctx, prec, cols):
     """Quads of 64-leaves whose steps need only one of their two B leaves
-    (kept products in one output column) run half-width MMAs on that leaf:
-    B's leaf columns only odd (the second leaf of every pair), only even,
-    alternating with k (both kinds within one quad), and all present.
+    (kept products in one output column): the other leaf is not loaded, so
+    its half of the stage holds an earlier step's terms, which must reach
+    only discarded quadrants.  B's leaf columns only odd (the second leaf of
+    every pair), only even, alternating with k (both kinds within one quad),
+    and all present.
     Integer entries: the BF16 splits are exact (C = AB bit for bit); FP16
     within its derived bound."""
     rng = np.random.default_rng(23)
