@@ -1395,10 +1395,11 @@ def run_e2e(S, ctx, GA, GB, args, bs, torch, np):
         d2h = 8 * nc * e + 16 * nc
         for m in {id(C): C, id(A): A, id(B): B}.values():
             m.close()
+    held = reserve_bytes if reserve is not None else 0
     del reserve
     return {"value": flops / sum(times) / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": len(times), "ms_per_step": 1e3 * sum(times) / len(times),
-            "host_reserve_bytes": reserve_bytes if reserve is not None else 0,
+            "host_reserve_bytes": held,
             "phases_s_per_step": {k: v / len(times) for k, v in phase.items()}, "per_step": per_step}
 
 

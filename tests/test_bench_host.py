@@ -132,3 +132,67 @@ def test_sp2_footprint_estimate_admits_the_64_cubed_lattice_and_refuses_two_to_t
     # leaves per block row are about the same for both lattices (the decay sets them)
     per_row = {n: e["x0_leaves_est"] / (n // 64) for n, e in est.items()}
     assert 0.8 < per_row[262144] / per_row[1048576] < 1.25
+
+
+def test_end_to_end_leg_counts_copied_bytes_and_the_held_block(monkeypatch):
+    """run_e2e against a stand-in library and host allocator: the timed steps
+    (one untimed sizing pass first), the host-to-device bytes of both inputs'
+    leaves and coordinates, the device-to-host bytes of every C leaf with its
+    coordinates and norm, and the held pinned block reported when the host
+    has room for it (none when it has not)."""
+    import types
+
+    import numpy as np
+    import torch
+
+    class Torch:
+        int32, float64 = torch.int32, torch.float64
+
+        @staticmethod
+        def empty(shape, dtype=None, pin_memory=False):
+            return torch.empty(shape, dtype=dtype)
+
+        class cuda:
+            @staticmethod
+            def synchronize():
+                pass
+
+    class M:
+        def __init__(self, n):
+            self.n = n
+
+        def info(self):
+            return {"nleaves": self.n, "n": 512, "bs": 64}
+
+        def close(self):
+            pass
+
+    calls = {"from_blocks": 0}
+
+    class S:
+        @staticmethod
+        def spamm_to_blocks(ctx, m, out=None):
+            return out
+
+        @staticmethod
+        def spamm_trim(ctx):
+            pass
+
+        @staticmethod
+        def spamm_from_blocks(ctx, n, bs, bi, bj, pay):
+            calls["from_blocks"] += 1
+            return M(len(bi))
+
+        @staticmethod
+        def spamm_multiply(ctx, A, B, tau, mode, prec, stats=False):
+            return M(5), {"kept_flops": 1e9}
+
+    args = types.SimpleNamespace(e2e_steps=3, tau=1e-6, mode="combined", prec="fp64")
+    monkeypatch.setattr(bench, "host_available_bytes", lambda: 1 << 40)
+    r = bench.run_e2e(S, None, M(7), M(6), args, 64, Torch, np)
+    assert r["steps"] == 3 and calls["from_blocks"] == 2 * 4
+    assert r["h2d_bytes_per_step"] == (7 + 6) * (64 * 64 * 8 + 8)
+    assert r["d2h_bytes_per_step"] == 5 * (64 * 64 * 8 + 16)
+    assert r["host_reserve_bytes"] == 7 * 64 * 64 * 8
+    monkeypatch.setattr(bench, "host_available_bytes", lambda: 0)
+    assert bench.run_e2e(S, None, M(7), M(6), args, 64, Torch, np)["host_reserve_bytes"] == 0
