@@ -55,6 +55,9 @@ def parse_args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--latency-repeats", type=int, default=50,
+                    help="p50/p99 latency over at least this many warm multiplies: the timed steps, then "
+                         "untimed-for-throughput repeats up to this count")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="lattice65536", choices=sorted(CONFIGS))
     ap.add_argument("--mode", default="combined", choices=["truncate", "spamm", "combined"])
@@ -1035,9 +1038,23 @@ def main():
             ev_b[k].record(stream)
         barrier()
     per_step = sorted(ev_a[k].elapsed_time(ev_b[k]) for k in range(args.steps))
-    latency = {"p50_ms": per_step[(len(per_step) - 1) // 2],
-               "p99_ms": per_step[min(len(per_step) - 1, int(math.ceil(0.99 * len(per_step))) - 1)],
-               "steps": len(per_step)}
+    # latency percentiles over at least --latency-repeats warm multiplies: the
+    # timed steps plus further ones, each between its own events (not part of
+    # the throughput above)
+    lat = list(per_step)
+    extra = max(0, args.latency_repeats - args.steps) if rank == 0 else 0
+    if extra:
+        ex_a = [torch.cuda.Event(enable_timing=True) for _ in range(extra)]
+        ex_b = [torch.cuda.Event(enable_timing=True) for _ in range(extra)]
+        for k in range(extra):
+            if flush is not None:
+                flush.zero_()
+            ex_a[k].record(stream)
+            step()
+            ex_b[k].record(stream)
+        torch.cuda.synchronize()
+        lat += [ex_a[k].elapsed_time(ex_b[k]) for k in range(extra)]
+    latency = latency_summary(lat)
     ms_total, value, mults = aggregate_ranks(sum(per_step), sum(s["kept_flops"] for s in stats),
                                              sum(s["n_kept"] for s in stats), dist)
     clocks = clk.summary()
@@ -1304,6 +1321,13 @@ def load_traffic(kernel, kept):
     if hashlib.sha256(src).hexdigest()[:16] != d["source_sha256_16"]:
         return None
     return d["dram_bytes_per_product"] * kept
+
+
+def latency_summary(ms) -> dict:
+    """p50 and p99 (nearest rank) of per-multiply times in ms."""
+    v = sorted(ms)
+    return {"p50_ms": v[(len(v) - 1) // 2], "p99_ms": v[min(len(v) - 1, int(math.ceil(0.99 * len(v))) - 1)],
+            "steps": len(v)}
 
 
 def host_available_bytes() -> int:

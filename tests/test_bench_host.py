@@ -196,3 +196,16 @@ def test_end_to_end_leg_counts_copied_bytes_and_the_held_block(monkeypatch):
     assert r["host_reserve_bytes"] == 7 * 64 * 64 * 8
     monkeypatch.setattr(bench, "host_available_bytes", lambda: 0)
     assert bench.run_e2e(S, None, M(7), M(6), args, 64, Torch, np)["host_reserve_bytes"] == 0
+
+
+def test_latency_percentiles_are_nearest_rank():
+    ms = [float(v) for v in range(100, 0, -1)]  # 100 multiplies, 1..100 ms, unsorted
+    r = bench.latency_summary(ms)
+    assert r == {"p50_ms": 50.0, "p99_ms": 99.0, "steps": 100}
+    assert bench.latency_summary(ms[:50])["p99_ms"] == 100.0  # 50 repeats: p99 is the slowest
+    assert bench.latency_summary([3.0]) == {"p50_ms": 3.0, "p99_ms": 3.0, "steps": 1}
+
+
+def test_latency_repeats_default_to_fifty(monkeypatch):
+    monkeypatch.setattr("sys.argv", ["bench.py"])
+    assert bench.parse_args().latency_repeats == 50
