@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
     }
     for (int b = 0; b < NB; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 256);
+      mbar_init(&tempty[b], 8);  // the eight epilogue warps, one arrival each
     }
     for (int q = 0; q < kQuadQ; ++q) {
       mbar_init(&qfull[q], 1);
@@ -407,7 +407,8 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
 #pragma unroll
             for (int hh = 0; hh < 4; ++hh) tmem_wait16(buf[hh]);  // the first waits for all four
             tc_fence_before();
-            mbar_arrive(&tempty[b]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);  // one arrival per warp, after all its lanes' loads
             released = true;
 #pragma unroll
             for (int hh = 0; hh < 4; ++hh) {
@@ -426,7 +427,8 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
           }
           if (!released) {
             tc_fence_before();
-            mbar_arrive(&tempty[b]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
           }
         }
       }
