@@ -471,7 +471,7 @@ def run_served(args):
         prefix = {"requests": k, "arrivals": "all at t = 0 (the stream's first requests)",
                   "chosen_forms": serve(stream(0.0, count=k)), "fp64": serve(stream(0.0, forced="fp64", count=k))}
     line = {"metric": "requests/s (served stream)", "value": load["requests_per_s"], "unit": "req/s", "n_gpus": 1,
-            "higher_is_better": True, "dtype": args.prec, "data": "synthetic",
+            "higher_is_better": True, "dtype": compute_dtype(args.prec), "data": "synthetic",
             "config": {"workload": "served_stream", "requests": args.serve_requests, "inputs": args.serve_inputs,
                        "resident_inputs": [{"n": specs[i][0], "alpha": specs[i][1]} for i in live],
                        "dropped_inputs": dropped, "n_range": [4096, args.serve_nmax],
@@ -1088,7 +1088,7 @@ def main():
             "metric": "kept-block GFLOP/s", "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.prec == "fp64" else args.prec, "data": "synthetic",
+            "dtype": compute_dtype(args.prec), "data": "synthetic",
             "config": {"workload": args.config, "desc": cfg["desc"], "n": cfg["n"], "bs": bs, "method": args.mode,
                        "tau": args.tau, "precision": args.prec,
                        "sigma": args.sigma if args.headline else None, "l2": ("inputs (%.1f GB of leaves) larger than L2" % in_gb) if flush is None
@@ -1232,7 +1232,7 @@ def run_precision_config(args, cfg):
     line = {"metric": "kept-block GFLOP/s", "value": ch.get("kept_gflops"), "unit": "GFLOP/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ch.get("ms_per_step"),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if chosen == "fp64" else chosen, "data": "synthetic",
+            "dtype": compute_dtype(chosen), "data": "synthetic",
             "config": {"workload": "lattice262144", "desc": cfg["desc"], "n": cfg["n"], "bs": bs,
                        "method": "combined", "tau": min(args.pc_taus), "precision": chosen,
                        "l2": "inputs far larger than L2", "parallelism": "single"},
@@ -1321,6 +1321,13 @@ def load_traffic(kernel, kept):
     if hashlib.sha256(src).hexdigest()[:16] != d["source_sha256_16"]:
         return None
     return d["dram_bytes_per_product"] * kept
+
+
+def compute_dtype(prec) -> str:
+    """The arithmetic type a form's leaf products compute in (the form itself is
+    named in the line's config): FP64 leaves "f64", the BF16 slice splits "bf16",
+    the scaled FP16 form "f16"; the autotuned mix of the served stream "mixed"."""
+    return {"fp64": "f64", "bf16_split": "bf16", "bf16_split4": "bf16", "fp16_scaled": "f16"}.get(prec, "mixed")
 
 
 def latency_summary(ms) -> dict:

@@ -209,3 +209,8 @@ def test_latency_percentiles_are_nearest_rank():
 def test_latency_repeats_default_to_fifty(monkeypatch):
     monkeypatch.setattr("sys.argv", ["bench.py"])
     assert bench.parse_args().latency_repeats == 50
+
+
+def test_dtype_is_the_arithmetic_type_of_the_form():
+    assert [bench.compute_dtype(p) for p in ("fp64", "bf16_split", "bf16_split4", "fp16_scaled", "auto")] == \
+        ["f64", "bf16", "bf16", "f16", "mixed"]
